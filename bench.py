@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the coherent F-statistic template loop on one GB300 (or N).
+
+One step = one pass of the whole path over one segment: segment preparation
+(time/ephemeris tables, Fourier x2 upsampling, spline) followed by the coarse
+search of every template (resample/demodulate per sky, two-pass zero-padded
+transform per template, F on every bin up to Nyquist, candidate compaction).
+Workload "grid_2d": 2 sidereal days at dt = 2 s (N = 86,164 float32 samples),
+Nfft = 2^18, 256 sky positions x 16 spindowns in [-1e-8, 0] Hz/s, F written
+for all 2^17 bins (4096 x 512 KiB), candidates above F = 20; seeded white
+noise with 4 simulated signals.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1003_0844_gb300 import workloads as W  # noqa: E402
+
+METRIC = "F-stat templates/s (N=86,164, 2^18 FFT) on 1 GB300; % HBM roofline; max rel dF vs FP64"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="grid_2d")
+    p.add_argument("--cpu-templates", type=int, default=48, help="oracle sample size (templates)")
+    p.add_argument("--fp64-skies", type=int, default=2, help="skies of the plain FP64 form comparison")
+    p.add_argument("--quick", action="store_true", help="skip the CPU baseline and FP64 comparison")
+    p.add_argument("--nsky", type=int, default=None, help="override the sky count (profiling runs)")
+    return p.parse_args()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(x, wl, det, alpha, delta, f1, ntempl):
+    """Oracle (as it stands) on a bounded sample: segment preparation + ntempl templates, FFT mode."""
+    from oracle import fstat as ofs, resample as ors
+    t0 = time.perf_counter()
+    seg = ors.Segment(np.asarray(x, dtype=np.float64), wl.dt)
+    done = 0
+    for s in range(len(alpha)):
+        for m in range(len(f1)):
+            if done >= ntempl:
+                break
+            ofs.fstat(seg, alpha[s], delta[s], f1[m], wl.fl, det, wl.S0, wl.nfft)
+            done += 1
+        if done >= ntempl:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, dt, done
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import response as orsp
+    wl = W.WORKLOADS[args.workload]
+    det = W.detector_for(wl)
+    x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float32)
+    alpha, delta = W.sky_grid(wl.nsky)
+    f1 = W.spin_grid(wl.nspin, *wl.f1_range)
+    per_step = 4  # templates per step: each step is a bounded sample of the workload
+    for _ in range(args.warmup):
+        cpu_oracle_rate(x, wl, det, alpha, delta, f1, per_step)
+    rates, secs = [], 0.0
+    t0 = time.perf_counter()
+    total = 0
+    for _ in range(args.steps):
+        r, dt, n = cpu_oracle_rate(x, wl, det, alpha, delta, f1, per_step)
+        total += n
+    wall = time.perf_counter() - t0
+    value = total / wall
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "templates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": wl.n, "nfft": wl.nfft, "templates": wl.nsky * wl.nspin,
+                   "sample_templates_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "templates/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d templates per step (oracle segment preparation + FFT-mode F), %d steps"
+                                   % (per_step, args.steps)},
+        "e2e": {"value": value, "unit": "templates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_1003_0844_gb300 import build, fstat as fs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    wl = W.WORKLOADS[args.workload]
+    if args.nsky:
+        import dataclasses
+        wl = dataclasses.replace(wl, nsky=args.nsky)
+    det = W.detector_for(wl)
+    ctx = fs.Context(det, device=local)
+    # inputs: seeded noise plus simulated signals (fs_inject, FP64), stored as float32 data
+    x64 = torch.as_tensor(W.noise(wl), device="cuda")
+    fs.inject(ctx, x64, wl.dt, wl.fl, wl.sigma, W.injections(wl))
+    x32 = x64.float().contiguous()
+    # weak scaling: rank r searches its own 256-sky shard of a lattice of 256 x world points
+    a_all, d_all = W.sky_grid(wl.nsky * world)
+    alpha = torch.as_tensor(np.ascontiguousarray(a_all[rank::world]), device="cuda")
+    delta = torch.as_tensor(np.ascontiguousarray(d_all[rank::world]), device="cuda")
+    f1 = torch.as_tensor(W.spin_grid(wl.nspin, *wl.f1_range), device="cuda")
+    nsky, nspin, nbins = alpha.numel(), f1.numel(), wl.nbins
+    ntempl = nsky * nspin
+    seg = fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0)
+    F_out = torch.empty((ntempl, nbins), dtype=torch.float32, device="cuda")
+    cap = 1 << 16
+    cand = torch.empty((cap, 4), dtype=torch.int32, device="cuda")
+    ncand = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+
+    def step():
+        seg.load(x32)
+        fs.search(ctx, seg, alpha, delta, f1, wl.F_thr, F_out=F_out, cand=cand, n_cand=ncand, cand_cap=cap)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    ctx.check()
+    ctx.stats(reset=True)
+    ctx.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flushed between timed steps (outside the events)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    stats = ctx.stats(reset=True)
+    ctx.set_profiling(False)
+    ctx.check()
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ntempl * world / (ms_per_step / 1e3)
+
+    # dominant kernel and its roofline: FFT flops 5 Nfft log2(Nfft) per complex transform,
+    # two transforms (a, b) per template, split between the passes by log2 N1 : log2 N2
+    p = int(round(math.log2(wl.nfft)))
+    lg1, lg2 = (p + 1) // 2, p // 2
+    kinds = {k: (stats["ms"][k], stats["count"][k]) for k in ("prepare", "demodulate", "pass1", "pass2")}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    tmpl_per_launch = {"pass1": ntempl * args.steps / max(kinds["pass1"][1], 1),
+                       "pass2": ntempl * args.steps / max(kinds["pass2"][1], 1)}
+    flops_tmpl = {"pass1": 2 * 5 * wl.nfft * lg1, "pass2": 2 * 5 * wl.nfft * lg2}
+    roof = None
+    if dom in flops_tmpl and dom_n:
+        per_launch_ms = dom_ms / dom_n
+        achieved = flops_tmpl[dom] * tmpl_per_launch[dom] / (per_launch_ms / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_kind": "FP32 CUDA-core peak from unit counts and max clock (152 SM x 128 x 2 x 2070 MHz)",
+                "per_launch_ms": per_launch_ms, "templates_per_launch": tmpl_per_launch[dom]}
+    hbm_gbs, hbm_kind = _peaks()
+    # whole-path HBM view: algorithmic bytes = F written (4 B per bin) per template
+    hbm_alg = ntempl * nbins * 4 / (ms_per_step / 1e3) / 1e9
+    shares = {k: round(v[0] / max(sum(x[0] for x in kinds.values()), 1e-9), 4) for k, v in kinds.items()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "templates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (FP64/double-float phases)", "data": "synthetic",
+        "config": {"workload": args.workload, "n": wl.n, "nfft": wl.nfft, "nsky": nsky, "nspin": nspin,
+                   "templates_per_gpu": ntempl, "nbins": nbins, "F_thr": wl.F_thr, "F_written": True,
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky shards x%d" % world},
+        "roofline": roof,
+        "hbm_alg_gbs": hbm_alg, "hbm_peak_gbs": hbm_gbs, "hbm_peak_kind": hbm_kind,
+        "kernel_ms_share": shares,
+        "gpu_launches": int(stats["launches"]),
+        "clocks": ck,
+    }
+    if rank == 0 and not args.quick:
+        # plain FP64 form on a sample of skies (same GPU), and the FP32 path's error against it
+        nsk = min(args.fp64_skies, nsky)
+        seg64 = fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0, precision="f64")
+        fs.search(ctx, seg64, alpha[:nsk].contiguous(), delta[:nsk].contiguous(), f1, wl.F_thr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r64 = fs.search(ctx, seg64, alpha[:nsk].contiguous(), delta[:nsk].contiguous(), f1, wl.F_thr)
+        e1.record()
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        F64 = r64.F
+        F32 = F_out[: nsk * nspin].double()
+        drel = float(((F32 - F64).abs() / torch.clamp(F64, min=1.0)).max().item())
+        line["fp64_form"] = {"value": nsk * nspin / t64, "unit": "templates/s", "templates": nsk * nspin,
+                             "note": "plain all-FP64 path (radix-2 FP64 FFT), search only"}
+        line["max_rel_dF_vs_fp64"] = drel
+        seg64.close()
+        # the oracle on the host cores, bounded sample
+        xh = x32.cpu().numpy()
+        rate, secs, done = cpu_oracle_rate(xh, wl, det, a_all[rank::world], d_all[rank::world],
+                                           W.spin_grid(wl.nspin, *wl.f1_range), args.cpu_templates)
+        line["cpu_baseline"] = {"value": rate, "unit": "templates/s", "cores": 1, "kind": "oracle",
+                                "sample": "segment preparation + %d templates (FFT mode), %.1f s" % (done, secs)}
+        # end to end through the public API with host buffers: pinned x -> device,
+        # prepare + search, candidates and their count -> host, every step
+        xh_pin = torch.empty(wl.n, dtype=torch.float32).pin_memory()
+        xh_pin.copy_(x32.cpu())
+        cand_h = torch.empty((cap, 4), dtype=torch.int32).pin_memory()
+        nc_h = torch.empty(1, dtype=torch.int64).pin_memory()
+        xd = torch.empty_like(x32)
+        ke = max(5, args.steps // 5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            xd.copy_(xh_pin, non_blocking=True)
+            seg.load(xd)
+            fs.search(ctx, seg, alpha, delta, f1, wl.F_thr, F_out=F_out, cand=cand, n_cand=ncand, cand_cap=cap)
+            nc_h.copy_(ncand, non_blocking=True)
+            cand_h.copy_(cand, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / ke
+        line["e2e"] = {"value": ntempl / e2e_s, "unit": "templates/s", "h2d_bytes_per_step": wl.n * 4,
+                       "d2h_bytes_per_step": cap * 16 + 8}
+    else:
+        line.setdefault("e2e", None)
+        line.setdefault("cpu_baseline", None)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    seg.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * fstat.h -- C ABI of the GB300 coherent F-statistic template loop.
+ *
+ * The library evaluates, for every template (sky position alpha, delta and
+ * spindown f1) of a search grid, the F-statistic of Eq. (OS)
+ *
+ *     F_k = 2 / (S0 To) * ( |Fa_k|^2 / <a^2> + |Fb_k|^2 / <b^2> )
+ *
+ * on the Fourier bins k of a zero-padded transform, where Fa, Fb are the
+ * integrals of Eqs. (Fab) written as Fourier transforms in barycentric time
+ * (Eq. ia, Sec. VI.A):
+ *
+ *     Fa_k = dt * sum_{j<N} x~_j a_j exp(-2 pi i Phi_j) exp(-2 pi i j k / Nfft)
+ *
+ * with x~_j the data resampled to the source time t_j that solves
+ * t_j + phi_m(t_j) = j dt (Eq. eq:Bt, phi_m of Eq. pham), a_j, b_j the
+ * amplitude modulation functions at t_j (Sec. II), and
+ * Phi_j = fl phi_m(t_j) + f1 (t_j^2/2 + t_j phi_m(t_j)) the
+ * frequency-independent phase (Eq. phas with one spindown, plus the
+ * heterodyne term of a narrow band starting at fl).  Threshold crossings
+ * F_k > F_thr are compacted into a candidate list (Sec. VII, coarse search).
+ *
+ * Conventions shared by every entry point:
+ *  - Array arguments named *_dev are device pointers on the context's
+ *    device, owned by the caller; the library only reads inputs and writes
+ *    outputs through them.  Arguments named *_host are host pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless stated.
+ *  - Argument errors are returned immediately and nothing is launched.
+ *    Errors found on the device (candidate overflow, non-finite input,
+ *    exhausted wait) are latched in the context and returned by
+ *    fs_sync_status().
+ *  - A context is not thread-safe; use one context per host thread.
+ *  - No C++ exception crosses this boundary.
+ */
+#ifndef FSTAT_H
+#define FSTAT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FS_API __attribute__((visibility("default")))
+#else
+#define FS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FS_OK = 0,
+  FS_ERR_ARG = 1,         /* null pointer, bad enum value, bad sizes         */
+  FS_ERR_SHAPE = 2,       /* unsupported n / nfft / nbins combination        */
+  FS_ERR_CAPACITY = 3,    /* more candidates than cand_cap (count is exact)  */
+  FS_ERR_NONFINITE = 4,   /* NaN or Inf in the data series                   */
+  FS_ERR_CUDA = 5,        /* a CUDA runtime call failed                      */
+  FS_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out              */
+  FS_ERR_UNSUPPORTED = 7, /* valid request this build does not implement     */
+  FS_ERR_NOMEM = 8        /* device allocation failed                        */
+} fs_status;
+
+/* Detector site and analytic-Earth parameters, radians.
+ * lat, lon: geodetic latitude and east longitude of the site on the
+ *   reference ellipsoid (a = 6378.140 km, flattening 0.00335281, Sec. V);
+ * gamma: orientation of the arms' bisector, counter-clockwise from local
+ *   East (the gamma of the amplitude modulation functions, Sec. II);
+ * eps: obliquity of the ecliptic (Eq. pha4);
+ * lambda_e0: ecliptic longitude of the Earth seen from the SSB at t = 0 on
+ *   a circular orbit of 1 AU (R_ES of Eq. pha5);
+ * theta_g0: Greenwich sidereal angle at t = 0; the local sidereal angle is
+ *   theta(t) = theta_g0 + lon + Omega_r t, Omega_r = 7.2921151467e-5 rad/s.
+ */
+typedef struct {
+  double lat, lon, gamma, eps, lambda_e0, theta_g0;
+} fs_detector;
+
+enum { FS_PREC_F32 = 0, /* FP32 samples, spline and FFT; compensated (double-float) phases */
+       FS_PREC_F64 = 1  /* plain FP64 throughout                                           */ };
+enum { FS_INTERP_SPLINE2X = 0, /* Fourier x2 + natural cubic spline (Sec. VI.A) */
+       FS_INTERP_NEAREST = 1   /* nearest neighbour, "stroboscopic" (Sec. VI.A)  */ };
+enum { FS_X_F32 = 0, FS_X_F64 = 1 };
+
+/* One data segment: x_k = x(k dt), k < n, t = 0 at the first sample.
+ * nfft: zero-padded transform length, a power of two with nfft >= n and
+ *   4096 <= nfft <= 2^20;
+ * fl: lower edge of the band [Hz] (heterodyne reference);
+ * S0: one-sided noise spectral density (2 sigma^2 dt for white noise). */
+typedef struct {
+  int64_t n;
+  int64_t nfft;
+  double dt;
+  double fl;
+  double S0;
+  int32_t precision; /* FS_PREC_* */
+  int32_t interp;    /* FS_INTERP_* */
+  int32_t x_dtype;   /* FS_X_F32 or FS_X_F64: element type of x_dev */
+  int32_t reserved;
+} fs_segment_desc;
+
+/* A threshold crossing: template (sky index, spindown index), bin k, F_k. */
+typedef struct {
+  uint32_t sky, spin, bin;
+  float F;
+} fs_candidate;
+
+typedef struct fs_ctx fs_ctx;
+typedef struct fs_seg fs_seg;
+
+/* Create a context on CUDA device `device` for detector `det`.
+ * Allocates the context's small device state (error flag, counters).
+ * Returns FS_ERR_ARG for null pointers, FS_ERR_CUDA if the device cannot be
+ * used.  On success *ctx must be released with fs_destroy. */
+FS_API fs_status fs_create(fs_ctx **ctx, const fs_detector *det, int32_t device);
+FS_API void fs_destroy(fs_ctx *ctx);
+
+/* Prepare the template-independent part of the resampler for one segment
+ * (Sec. VI.A): time/ephemeris tables on the grid t_m = m dt (analytic Earth,
+ * Eqs. pha4-pha5, Sec. V), the Fourier x2 upsampled series and its natural
+ * cubic spline.  x_dev holds n samples of type desc->x_dtype.  The segment
+ * keeps its own device copies (about 40 bytes per sample) and may be reused
+ * by any number of fs_search calls.  Non-finite samples latch
+ * FS_ERR_NONFINITE.  Release with fs_seg_destroy. */
+FS_API fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *desc,
+                             const void *x_dev, void *stream);
+FS_API void fs_seg_destroy(fs_seg *seg);
+
+/* Coarse search over nsky x nspin templates (Eq. OS on every bin).
+ * alpha_dev, delta_dev: nsky doubles (radians); f1_dev: nspin doubles
+ *   [Hz/s]; template (s, m) is (alpha[s], delta[s], f1[m]).
+ * F_out_dev: NULL (candidates only) or [nsky*nspin][nbins] values, template
+ *   index s*nspin + m, bins k = 0..nbins-1 (float for FS_PREC_F32, double
+ *   for FS_PREC_F64); nbins is nfft/2 (bins up to Nyquist) or nfft.
+ * cand_dev: capacity cand_cap; n_cand_dev: one device int64 that receives
+ *   the number of crossings F_k > F_thr (it may exceed cand_cap; then only
+ *   cand_cap are stored, in no particular order, and FS_ERR_CAPACITY is
+ *   latched).  n_cand_dev is overwritten, not accumulated.
+ * The call uses the context workspace, which it grows on first use for the
+ * segment's shape; it allocates nothing on later calls of the same shape. */
+FS_API fs_status fs_search(fs_ctx *ctx, fs_seg *seg,
+                    const double *alpha_dev, const double *delta_dev, int32_t nsky,
+                    const double *f1_dev, int32_t nspin, float F_thr,
+                    void *F_out_dev, int64_t nbins,
+                    fs_candidate *cand_dev, int64_t cand_cap, int64_t *n_cand_dev,
+                    void *stream);
+
+/* Re-run the segment preparation on new data of the same shape (n samples
+ * of desc->x_dtype at x_dev), reusing the segment's buffers: no allocation.
+ * Same work and errors as fs_prepare_segment. */
+FS_API fs_status fs_seg_load(fs_seg *seg, const void *x_dev, void *stream);
+
+/* Synchronise `stream` and return (and clear) the first device-side error
+ * latched since the last call, or FS_OK. */
+FS_API fs_status fs_sync_status(fs_ctx *ctx, void *stream);
+
+/* Launch accounting and optional per-kernel timing.
+ * launches: kernels launched by this context since the last reset.
+ * With profiling on, every launch of the kinds below is bracketed by CUDA
+ * events on its stream; ms[k] / count[k] are their summed durations and
+ * launch counts (read after the work completes; fs_get_stats synchronises
+ * the device).  Kinds: 0 segment preparation (all of it), 1 per-sky
+ * demodulation, 2 transform pass 1, 3 transform pass 2 + F epilogue,
+ * 4 other. */
+#define FS_PROF_KINDS 5
+typedef struct {
+  int64_t launches;
+  double ms[FS_PROF_KINDS];
+  int64_t count[FS_PROF_KINDS];
+} fs_stats;
+FS_API fs_status fs_set_profiling(fs_ctx *ctx, int32_t on);
+FS_API fs_status fs_get_stats(fs_ctx *ctx, fs_stats *out, int32_t reset);
+
+/* Human-readable name of a status code (static storage). */
+FS_API const char *fs_strerror(fs_status s);
+
+/* ---- stage access, for verification of each step against a reference ---- */
+
+/* Copy the segment's Fourier x2 upsampled series (2n doubles, Sec. VI.A)
+ * into x2_dev. */
+FS_API fs_status fs_seg_upsampled(const fs_seg *seg, double *x2_dev, void *stream);
+
+/* Resample and demodulate one sky position (the per-sky half of Sec. VI.A):
+ * for j < n writes y^a_j = x~_j a_j exp(-2 pi i fl phi_m(t_j)) and y^b_j
+ * (interleaved re, im: 2n doubles each), t_j (n doubles), and
+ * ab2_dev[0..1] = <a^2>, <b^2> (means over the n output samples).
+ * Values are computed by the segment's precision path and widened to double. */
+FS_API fs_status fs_demodulate(fs_ctx *ctx, fs_seg *seg, double alpha, double delta,
+                        double *ya_dev, double *yb_dev, double *tsrc_dev,
+                        double *ab2_dev, void *stream);
+
+/* Signal injection (software simulation of Eqs. resp-hphc, sig-eq:ampone):
+ * adds to x_dev (n doubles, t_k = k dt) the response to each injection,
+ * scaled so that its optimal SNR (Eq. snr-def with Eq. approx1,
+ * S0 = 2 sigma^2 dt) is inj[i].snr.  Host array of n_inj records. FP64. */
+typedef struct {
+  double f0, f1, alpha, delta, psi, cos_iota, phi0, snr;
+} fs_injection;
+FS_API fs_status fs_inject(fs_ctx *ctx, double *x_dev, int64_t n, double dt, double fl, double sigma,
+                    const fs_injection *inj_host, int32_t n_inj, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSTAT_H */

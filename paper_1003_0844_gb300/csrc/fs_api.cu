@@ -1,0 +1,246 @@
+// C ABI of the library (include/fstat.h): argument checks, ownership of
+// segment buffers and workspaces, dispatch to the FP32 or FP64 path.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <new>
+#include "fs_internal.h"
+#include "fs_model.cuh"
+
+using namespace fs;
+
+namespace fs {
+fs_status ensure_buffer(void **buf, size_t *cur, size_t bytes, cudaStream_t st) {
+  if (*cur >= bytes && *buf) return FS_OK;
+  if (*buf) {
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FS_ERR_CUDA;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cur = 0;
+  }
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return FS_ERR_NOMEM;
+  }
+  *buf = p;
+  *cur = bytes;
+  return FS_OK;
+}
+}  // namespace fs
+
+static inline cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+extern "C" {
+
+const char *fs_strerror(fs_status s) {
+  switch (s) {
+    case FS_OK: return "ok";
+    case FS_ERR_ARG: return "invalid argument";
+    case FS_ERR_SHAPE: return "unsupported shape (n, nfft, nbins)";
+    case FS_ERR_CAPACITY: return "candidate buffer overflow";
+    case FS_ERR_NONFINITE: return "non-finite value in the data";
+    case FS_ERR_CUDA: return "CUDA runtime error";
+    case FS_ERR_TIMEOUT: return "device-side wait timed out";
+    case FS_ERR_UNSUPPORTED: return "unsupported request";
+    case FS_ERR_NOMEM: return "device allocation failed";
+  }
+  return "unknown status";
+}
+
+fs_status fs_create(fs_ctx **ctx, const fs_detector *det, int32_t device) {
+  if (!ctx || !det) return FS_ERR_ARG;
+  *ctx = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return FS_ERR_CUDA; }
+  fs_ctx *c = new (std::nothrow) fs_ctx();
+  if (!c) return FS_ERR_NOMEM;
+  c->device = device;
+  c->det = *det;
+  if (cudaMalloc(&c->d_flags, sizeof(uint32_t)) != cudaSuccess) { delete c; cudaGetLastError(); return FS_ERR_NOMEM; }
+  if (cudaMemset(c->d_flags, 0, sizeof(uint32_t)) != cudaSuccess) { cudaFree(c->d_flags); delete c; return FS_ERR_CUDA; }
+  const char *bt = getenv("FSTAT_BATCH_TEMPLATES");
+  if (bt && atoi(bt) > 0) c->batch_templates = atoi(bt);
+  const char *gs = getenv("FSTAT_GROUP_SKIES");
+  if (gs && atoi(gs) > 0) c->group_skies = atoi(gs);
+  *ctx = c;
+  return FS_OK;
+}
+
+void fs_destroy(fs_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->d_flags);
+  cudaFree(ctx->ws);
+  cudaFree(ctx->ws64);
+  cudaFree(ctx->scratch);
+  for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d, const void *x_dev,
+                             void *stream) {
+  if (!ctx || !seg || !d || !x_dev) return FS_ERR_ARG;
+  *seg = nullptr;
+  if (d->n < 16 || !(d->dt > 0.0) || !(d->S0 > 0.0) || !isfinite(d->fl) || !isfinite(d->dt)) return FS_ERR_ARG;
+  if (d->precision != FS_PREC_F32 && d->precision != FS_PREC_F64) return FS_ERR_ARG;
+  if (d->interp != FS_INTERP_SPLINE2X && d->interp != FS_INTERP_NEAREST) return FS_ERR_ARG;
+  if (d->x_dtype != FS_X_F32 && d->x_dtype != FS_X_F64) return FS_ERR_ARG;
+  if (!is_pow2(d->nfft) || d->nfft < d->n || d->nfft < 4096 || d->nfft > (int64_t(1) << 20)) return FS_ERR_SHAPE;
+  if (d->precision == FS_PREC_F32 && d->nfft > (int64_t(1) << 18)) return FS_ERR_UNSUPPORTED;
+  if (d->n > (int64_t(1) << 28)) return FS_ERR_SHAPE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  cudaStream_t st = as_stream(stream);
+
+  fs_seg *s = new (std::nothrow) fs_seg();
+  if (!s) return FS_ERR_NOMEM;
+  s->ctx = ctx;
+  s->d = *d;
+  SegGeom &g = s->g;
+  g.n = d->n;
+  g.nfft = d->nfft;
+  g.dt = d->dt;
+  g.fl = d->fl;
+  g.S0 = d->S0;
+  g.margin = (int64_t)ceil(kMaxDelay / d->dt) + 4;
+  g.ngrid = g.n + 2 * g.margin;
+  g.theta0 = ctx->det.theta_g0 + ctx->det.lon;
+  g.lambda0 = ctx->det.lambda_e0;
+  double re, z;
+  site_radius(ctx->det.lat, &re, &z);
+  g.re_c = re / kC;
+  g.z_c = z / kC;
+
+  const int64_t n = g.n;
+  bool ok = cudaMalloc(&s->x64, sizeof(double) * n) == cudaSuccess &&
+            cudaMalloc(&s->x32, sizeof(float) * n) == cudaSuccess &&
+            cudaMalloc(&s->x2, sizeof(double) * 2 * n) == cudaSuccess;
+  if (ok && d->precision == FS_PREC_F32) {
+    ok = cudaMalloc(&s->tab0, sizeof(float4) * g.ngrid) == cudaSuccess &&
+         cudaMalloc(&s->tab1, sizeof(float4) * g.ngrid) == cudaSuccess &&
+         cudaMalloc(&s->coef, sizeof(float4) * 2 * n) == cudaSuccess;
+  } else if (ok) {
+    ok = cudaMalloc(&s->coef, sizeof(dcoef4) * 2 * n) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    fs_seg_destroy(s);
+    return FS_ERR_NOMEM;
+  }
+  fs_status r = fs_seg_load(s, x_dev, stream);
+  if (r != FS_OK) {
+    fs_seg_destroy(s);
+    return r;
+  }
+  *seg = s;
+  return FS_OK;
+}
+
+fs_status fs_seg_load(fs_seg *s, const void *x_dev, void *stream) {
+  if (!s || !x_dev) return FS_ERR_ARG;
+  if (cudaSetDevice(s->ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  cudaStream_t st = as_stream(stream);
+  ProfScope ps(s->ctx, PROF_PREP, st);
+  fs_status r = FS_OK;
+  if (s->d.precision == FS_PREC_F32) r = prepare_tables(s, st);
+  if (r == FS_OK) r = prepare_upsample(s, x_dev, st);
+  if (r == FS_OK) r = prepare_spline(s, st);
+  return r;
+}
+
+void fs_seg_destroy(fs_seg *s) {
+  if (!s) return;
+  cudaSetDevice(s->ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(s->tab0);
+  cudaFree(s->tab1);
+  cudaFree(s->x64);
+  cudaFree(s->x32);
+  cudaFree(s->x2);
+  cudaFree(s->coef);
+  delete s;
+}
+
+fs_status fs_search(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const double *delta_dev, int32_t nsky,
+                    const double *f1_dev, int32_t nspin, float F_thr, void *F_out_dev, int64_t nbins,
+                    fs_candidate *cand_dev, int64_t cand_cap, int64_t *n_cand_dev, void *stream) {
+  if (!ctx || !seg || !alpha_dev || !delta_dev || !f1_dev || !n_cand_dev) return FS_ERR_ARG;
+  if (seg->ctx != ctx) return FS_ERR_ARG;
+  if (nsky < 1 || nspin < 1 || cand_cap < 0 || (cand_cap > 0 && !cand_dev)) return FS_ERR_ARG;
+  if (!(nbins == seg->g.nfft / 2 || nbins == seg->g.nfft)) return FS_ERR_SHAPE;
+  if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  cudaStream_t st = as_stream(stream);
+  if (seg->d.precision == FS_PREC_F32)
+    return search32(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, (float *)F_out_dev, nbins,
+                    cand_dev, cand_cap, n_cand_dev, st);
+  return search64(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, (double *)F_out_dev, nbins,
+                  cand_dev, cand_cap, n_cand_dev, st);
+}
+
+fs_status fs_sync_status(fs_ctx *ctx, void *stream) {
+  if (!ctx) return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) { cudaGetLastError(); return FS_ERR_CUDA; }
+  if (cudaGetLastError() != cudaSuccess) return FS_ERR_CUDA;
+  uint32_t f = 0;
+  if (cudaMemcpy(&f, ctx->d_flags, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess) return FS_ERR_CUDA;
+  if (f) cudaMemset(ctx->d_flags, 0, sizeof(uint32_t));
+  if (f & ERRF_TIMEOUT) return FS_ERR_TIMEOUT;
+  if (f & ERRF_NONFINITE) return FS_ERR_NONFINITE;
+  if (f & ERRF_CAPACITY) return FS_ERR_CAPACITY;
+  return FS_OK;
+}
+
+fs_status fs_set_profiling(fs_ctx *ctx, int32_t on) {
+  if (!ctx) return FS_ERR_ARG;
+  ctx->prof = on != 0;
+  return FS_OK;
+}
+
+fs_status fs_get_stats(fs_ctx *ctx, fs_stats *out, int32_t reset) {
+  if (!ctx || !out) return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FS_ERR_CUDA;
+  memset(out, 0, sizeof(*out));
+  out->launches = ctx->launches;
+  for (const auto &r : ctx->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return FS_ERR_CUDA;
+    out->ms[r.kind] += ms;
+    out->count[r.kind] += 1;
+  }
+  if (reset) {
+    ctx->launches = 0;
+    ctx->recs.clear();
+    ctx->ev_used = 0;
+  }
+  return FS_OK;
+}
+
+fs_status fs_seg_upsampled(const fs_seg *seg, double *x2_dev, void *stream) {
+  if (!seg || !x2_dev) return FS_ERR_ARG;
+  return cuda_status(cudaMemcpyAsync(x2_dev, seg->x2, sizeof(double) * 2 * seg->g.n, cudaMemcpyDeviceToDevice,
+                                     as_stream(stream)));
+}
+
+fs_status fs_demodulate(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, double *ya_dev, double *yb_dev,
+                        double *tsrc_dev, double *ab2_dev, void *stream) {
+  if (!ctx || !seg || !ya_dev || !yb_dev || !tsrc_dev || !ab2_dev) return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  if (seg->d.precision == FS_PREC_F32)
+    return demod32_debug(ctx, seg, alpha, delta, ya_dev, yb_dev, tsrc_dev, ab2_dev, as_stream(stream));
+  return demod64_debug(ctx, seg, alpha, delta, ya_dev, yb_dev, tsrc_dev, ab2_dev, as_stream(stream));
+}
+
+fs_status fs_inject(fs_ctx *ctx, double *x_dev, int64_t n, double dt, double fl, double sigma,
+                    const fs_injection *inj_host, int32_t n_inj, void *stream) {
+  if (!ctx || !x_dev || n < 1 || !(dt > 0.0) || !(sigma > 0.0) || n_inj < 0 || (n_inj > 0 && !inj_host))
+    return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  return inject64(ctx, x_dev, n, dt, fl, sigma, inj_host, n_inj, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// Host-side internals shared by the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+
+#include "fs_common.cuh"
+
+struct fs_ctx {
+  int device = 0;
+  fs_detector det{};
+  uint32_t *d_flags = nullptr;       // latched device error bits
+  // FP32 search workspace (grown on demand)
+  size_t ws_bytes = 0;
+  void *ws = nullptr;
+  // FP64 search workspace
+  size_t ws64_bytes = 0;
+  void *ws64 = nullptr;
+  // scratch for stage access / injection
+  size_t scratch_bytes = 0;
+  void *scratch = nullptr;
+  // tuning knobs (templates per batch, skies per group)
+  int batch_templates = 16;
+  int group_skies = 1;
+  // launch accounting and optional event profiling
+  int64_t launches = 0;
+  bool prof = false;
+  std::vector<cudaEvent_t> evpool;
+  size_t ev_used = 0;
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+};
+
+struct fs_seg {
+  fs_ctx *ctx = nullptr;
+  fs_segment_desc d{};
+  fs::SegGeom g{};
+  // FP32 path tables on the grid t_m = m dt, m in [-margin, n + margin):
+  //   tab0[m] = (C.hi, C.lo, S.hi, S.lo) with C, S = (AU/c) (cos, sin) lambda_E(t_m)
+  //   tab1[m] = (cos theta_m, sin theta_m, t_m.hi, t_m.lo)
+  float4 *tab0 = nullptr, *tab1 = nullptr;
+  double *x64 = nullptr;    // input as double [n]
+  float *x32 = nullptr;     // input as float [n] (nearest-neighbour path)
+  double *x2 = nullptr;     // Fourier x2 upsampled [2n]
+  void *coef = nullptr;     // spline coefficients per interval: float4 or double[4] x [2n]
+};
+
+// ---- launchers implemented in the .cu files (all asynchronous on `st`) ----
+namespace fs {
+
+inline fs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FS_OK : FS_ERR_CUDA; }
+
+// FP64 radix-2 Stockham FFT of `batch` contiguous sequences of length n
+// (power of two) in place in `buf` using `tmp` as ping-pong space.
+// sign = -1 forward (exp(-2 pi i ...)), +1 inverse (unnormalised).
+cudaError_t fft64(double2 *buf, double2 *tmp, const double2 *twiddle, int64_t n, int batch,
+                  int sign, cudaStream_t st, int64_t *launches);
+// twiddle[q] = exp(-2 pi i q / n), q < n/2
+cudaError_t fft64_twiddles(double2 *tw, int64_t n, cudaStream_t st);
+
+// Segment preparation (P0 tables, P1 upsampling, P2 spline).
+fs_status prepare_tables(fs_seg *seg, cudaStream_t st);
+fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st);
+fs_status prepare_spline(fs_seg *seg, cudaStream_t st);
+
+// Per-sky constants from alpha/delta device arrays.
+cudaError_t sky_constants32(const double *alpha, const double *delta, int nsky, const fs::SegGeom &g,
+                            const fs_detector &det, SkyConst32 *out, cudaStream_t st);
+cudaError_t sky_constants64(const double *alpha, const double *delta, int nsky, const fs::SegGeom &g,
+                            const fs_detector &det, SkyConst64 *out, cudaStream_t st);
+
+// Searches.
+fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
+                   const double *f1, int nspin, float thr, float *F, int64_t nbins,
+                   fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st);
+fs_status search64(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
+                   const double *f1, int nspin, float thr, double *F, int64_t nbins,
+                   fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st);
+fs_status demod32_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, double *ya, double *yb,
+                        double *tsrc, double *ab2, cudaStream_t st);
+fs_status demod64_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, double *ya, double *yb,
+                        double *tsrc, double *ab2, cudaStream_t st);
+fs_status inject64(fs_ctx *ctx, double *x, int64_t n, double dt, double fl, double sigma,
+                   const fs_injection *inj, int n_inj, cudaStream_t st);
+
+// Event profiling of one launch (or group of launches) of a given kind.
+enum { PROF_PREP = 0, PROF_DEMOD = 1, PROF_PASS1 = 2, PROF_PASS2 = 3, PROF_OTHER = 4 };
+inline cudaEvent_t prof_event(fs_ctx *c) {
+  if (c->ev_used == c->evpool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->evpool.push_back(e);
+  }
+  return c->evpool[c->ev_used++];
+}
+struct ProfScope {
+  fs_ctx *c;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  ProfScope(fs_ctx *c_, int k, cudaStream_t s) : c(c_), kind(k), st(s) {
+    if (c->prof) { a = prof_event(c); cudaEventRecord(a, st); }
+  }
+  ~ProfScope() {
+    if (c->prof) {
+      cudaEvent_t b = prof_event(c);
+      cudaEventRecord(b, st);
+      c->recs.push_back({kind, a, b});
+    }
+  }
+};
+
+// Workspace helper: grow *buf to at least `bytes` (synchronising `st` first).
+fs_status ensure_buffer(void **buf, size_t *cur, size_t bytes, cudaStream_t st);
+
+}  // namespace fs

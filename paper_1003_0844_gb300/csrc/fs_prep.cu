@@ -1,0 +1,368 @@
+// Segment preparation (template independent), Sec. VI.A and Sec. V.
+//
+//  P0  time/ephemeris tables on the grid t_m = m dt (analytic Earth, FP64
+//      computed, stored as double-float for the FP32 path);
+//  P1  Fourier x2 upsampling of the data (FP64).  With X = DFT_N(x), the
+//      2N-point series of Sec. VI.A (DFT padded with N zeros, inverse DFT)
+//      has x2[2m] = x[m] and x2[2m+1] = IDFT_N(Z)[m] with
+//      Z_k = X_k exp(i pi k'/N), k' the signed frequency of bin k and the
+//      Nyquist bin of even N set to zero (its split halves cancel on the odd
+//      samples).  Both length-N transforms use Bluestein's chirp-z identity
+//      on power-of-two FP64 FFTs, so any N is accepted;
+//  P2  natural cubic spline through x2 at unit spacing: second derivatives
+//      from the [1 4 1] tridiagonal system by the Thomas recurrences, run in
+//      parallel chunks whose start and end are warmed up over 40 points
+//      (errors of the truncated recurrences shrink by (2 - sqrt 3)^40 ~ 1e-23),
+//      then per-interval polynomial coefficients.
+#include <stdio.h>
+#include <algorithm>
+#include "fs_internal.h"
+#include "fs_model.cuh"
+
+namespace fs {
+
+// ------------------------------------------------------------------ P0 tables
+__global__ void k_tables32(SegGeom g, float4 *tab0, float4 *tab1) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.ngrid) return;
+  double t = (double)(i - g.margin) * g.dt;
+  double sl, cl, sth, cth;
+  sincos(g.lambda0 + kOmegaO * t, &sl, &cl);
+  sincos(g.theta0 + kOmegaR * t, &sth, &cth);
+  df32 C = df_from_double(kAUls * cl), S = df_from_double(kAUls * sl), T = df_from_double(t);
+  tab0[i] = make_float4(C.hi, C.lo, S.hi, S.lo);
+  tab1[i] = make_float4((float)cth, (float)sth, T.hi, T.lo);
+}
+
+fs_status prepare_tables(fs_seg *seg, cudaStream_t st) {
+  const SegGeom &g = seg->g;
+  k_tables32<<<(unsigned)((g.ngrid + 255) / 256), 256, 0, st>>>(g, seg->tab0, seg->tab1);
+  seg->ctx->launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ P1 upsampling
+template <typename T>
+__global__ void k_load_x(const T *x, double *x64, float *x32, int64_t n, uint32_t *flags) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = (double)x[i];
+  if (!isfinite(v)) { atomicOr(flags, ERRF_NONFINITE); v = 0.0; }
+  x64[i] = v;
+  x32[i] = (float)v;
+}
+
+// Bluestein chirp c_m = exp(sign * i pi m^2 / N) with m^2 reduced mod 2N exactly.
+__device__ inline double2 bluestein_chirp(int64_t m, int64_t N, int sign) {
+  unsigned long long q = ((unsigned long long)m * (unsigned long long)m) % (unsigned long long)(2 * N);
+  double s, c;
+  sincospi((double)q / (double)N, &s, &c);
+  return make_double2(c, sign * s);
+}
+
+// b[m] = exp(+i pi m^2/N) for |m| < N placed circularly in a length-M buffer.
+__global__ void k_bluestein_b(double2 *b, int64_t N, int64_t M) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double2 v = make_double2(0.0, 0.0);
+  if (i < N) v = bluestein_chirp(i, N, +1);
+  else if (i > M - N) v = bluestein_chirp(M - i, N, +1);
+  b[i] = v;
+}
+
+// a[n] = in[n] * exp(-i pi n^2/N) for n < N (in real or complex, optionally conjugated), 0 beyond.
+__global__ void k_bluestein_a(double2 *a, const double *in_real, const double2 *in_cplx, int conj_in,
+                              int64_t N, int64_t M) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double2 v = make_double2(0.0, 0.0);
+  if (i < N) {
+    double2 u = in_cplx ? in_cplx[i] : make_double2(in_real[i], 0.0);
+    if (conj_in) u.y = -u.y;
+    v = cmul(u, bluestein_chirp(i, N, -1));
+  }
+  a[i] = v;
+}
+
+__global__ void k_pointwise_mul(double2 *a, const double2 *b, int64_t M) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < M) a[i] = cmul(a[i], b[i]);
+}
+
+// out[k] = exp(-i pi k^2/N) conv[k] / M   (k < N)
+__global__ void k_bluestein_out(double2 *out, const double2 *conv, int64_t N, int64_t M) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  double2 v = conv[k];
+  v.x /= (double)M;
+  v.y /= (double)M;
+  out[k] = cmul(v, bluestein_chirp(k, N, -1));
+}
+
+// Z_k = X_k exp(i pi k'/N), Nyquist bin of even N zeroed.
+__global__ void k_halfshift(double2 *Z, const double2 *X, int64_t N) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  if ((N % 2 == 0) && k == N / 2) { Z[k] = make_double2(0.0, 0.0); return; }
+  int64_t kp = (2 * k < N) ? k : k - N;  // signed frequency
+  double s, c;
+  sincospi((double)kp / (double)N, &s, &c);
+  Z[k] = cmul(X[k], make_double2(c, s));
+}
+
+// x2[2m] = x[m]; x2[2m+1] = Re(IDFT_N(Z))[m] = Re(conj(DFT_N(conj Z)))[m] / N
+__global__ void k_interleave(double *x2, const double *x, const double2 *dft_conjZ, int64_t N) {
+  int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= N) return;
+  x2[2 * m] = x[m];
+  x2[2 * m + 1] = dft_conjZ[m].x / (double)N;
+}
+
+static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// DFT of length N of `in` (real or complex, optionally conjugated) into out, by Bluestein.
+static cudaError_t bluestein_dft(double2 *out, const double *in_real, const double2 *in_cplx, int conj_in,
+                                 int64_t N, int64_t M, const double2 *Bhat, double2 *a, double2 *tmp,
+                                 const double2 *tw, cudaStream_t st, int64_t *launches) {
+  k_bluestein_a<<<nblk(M), 256, 0, st>>>(a, in_real, in_cplx, conj_in, N, M);
+  cudaError_t e = fft64(a, tmp, tw, M, 1, -1, st, launches);
+  if (e != cudaSuccess) return e;
+  k_pointwise_mul<<<nblk(M), 256, 0, st>>>(a, Bhat, M);
+  e = fft64(a, tmp, tw, M, 1, +1, st, launches);
+  if (e != cudaSuccess) return e;
+  k_bluestein_out<<<nblk(N), 256, 0, st>>>(out, a, N, M);
+  *launches += 3;
+  return cudaGetLastError();
+}
+
+fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st) {
+  int64_t N = seg->g.n;
+  int64_t M = 1;
+  while (M < 2 * N - 1) M <<= 1;
+  // scratch: Bhat, a, tmp, X (M each) + twiddles (M/2)
+  size_t need = sizeof(double2) * (4 * (size_t)M + (size_t)M / 2 + 1);
+  fs_status s = ensure_buffer(&seg->ctx->scratch, &seg->ctx->scratch_bytes, need, st);
+  if (s != FS_OK) return s;
+  double2 *Bhat = (double2 *)seg->ctx->scratch;
+  double2 *a = Bhat + M, *tmp = a + M, *X = tmp + M, *tw = X + M;
+
+  if (seg->d.x_dtype == FS_X_F32)
+    k_load_x<float><<<nblk(N), 256, 0, st>>>((const float *)x_dev, seg->x64, seg->x32, N, seg->ctx->d_flags);
+  else
+    k_load_x<double><<<nblk(N), 256, 0, st>>>((const double *)x_dev, seg->x64, seg->x32, N, seg->ctx->d_flags);
+  int64_t *L = &seg->ctx->launches;
+  cudaError_t e = fft64_twiddles(tw, M, st);
+  if (e != cudaSuccess) return FS_ERR_CUDA;
+  k_bluestein_b<<<nblk(M), 256, 0, st>>>(Bhat, N, M);
+  *L += 3;
+  e = fft64(Bhat, tmp, tw, M, 1, -1, st, L);
+  if (e != cudaSuccess) return FS_ERR_CUDA;
+  // X = DFT_N(x)
+  e = bluestein_dft(X, seg->x64, nullptr, 0, N, M, Bhat, a, tmp, tw, st, L);
+  if (e != cudaSuccess) return FS_ERR_CUDA;
+  // Z = half-sample shift; odd samples = Re IDFT_N(Z) = Re conj(DFT_N(conj Z)) / N
+  k_halfshift<<<nblk(N), 256, 0, st>>>(X, X, N);
+  *L += 1;
+  // the result overwrites X: the transform reads its whole input before writing
+  e = bluestein_dft(X, nullptr, X, 1, N, M, Bhat, a, tmp, tw, st, L);
+  if (e != cudaSuccess) return FS_ERR_CUDA;
+  k_interleave<<<nblk(N), 256, 0, st>>>(seg->x2, seg->x64, X, N);
+  *L += 1;
+  return cuda_status(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ P2 spline
+// Thomas recurrences for M_{i-1} + 4 M_i + M_{i+1} = r_i (i = 1..n2-2), M_0 = M_{n2-1} = 0:
+//   c'_1 = 1/4, c'_i = 1/(4 - c'_{i-1});  d'_1 = r_1 c'_1, d'_i = (r_i - d'_{i-1}) c'_i
+//   M_{n2-2} = d'_{n2-2},  M_i = d'_i - c'_i M_{i+1}
+constexpr int kSplChunk = 128;
+constexpr int kSplWarm = 40;
+constexpr int kSplCExact = 64;  // c'_i follows the recurrence up to here, then stays at its limit
+
+__device__ inline double spline_cprime(int64_t i) {
+  double c = 0.25;
+  int64_t lim = i < kSplCExact ? i : kSplCExact;
+  for (int64_t k = 2; k <= lim; k++) c = 1.0 / (4.0 - c);
+  return c;
+}
+
+__device__ inline double spline_rhs(const double *y, int64_t i) {
+  return 6.0 * (y[i + 1] - 2.0 * y[i] + y[i - 1]);
+}
+
+__global__ void k_spline_forward(const double *y, double *dp, int64_t n2) {
+  int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t lo = 1 + h * kSplChunk;
+  int64_t last = n2 - 2;
+  if (lo > last) return;
+  int64_t hi = lo + kSplChunk - 1;
+  if (hi > last) hi = last;
+  int64_t i0 = lo - kSplWarm;
+  if (i0 < 1) i0 = 1;
+  const double cinf = spline_cprime(kSplCExact);
+  double d = 0.0;  // d'_{i0-1}: exact (no term) at the true start, a warm-up guess otherwise
+  for (int64_t i = i0; i <= hi; i++) {
+    double c = (i < kSplCExact) ? spline_cprime(i) : cinf;
+    d = (spline_rhs(y, i) - d) * c;
+    if (i >= lo) dp[i] = d;
+  }
+}
+
+// Back substitution over one chunk, started kSplWarm points beyond its end from
+// M = 0 (exact at the true end); reads the complete d' array of the forward pass.
+__global__ void k_spline_backward(const double *dp, double *Mout, int64_t n2) {
+  int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t lo = 1 + h * kSplChunk;
+  int64_t last = n2 - 2;
+  if (lo > last) return;
+  int64_t hi = lo + kSplChunk - 1;
+  if (hi > last) hi = last;
+  int64_t i1 = hi + kSplWarm;
+  if (i1 > last) i1 = last;
+  const double cinf = spline_cprime(kSplCExact);
+  double Mnext = 0.0;  // M_{i1+1}
+  for (int64_t i = i1; i >= lo; i--) {
+    double c = (i < kSplCExact) ? spline_cprime(i) : cinf;
+    double m = dp[i] - c * Mnext;
+    if (i <= hi) Mout[i] = m;
+    Mnext = m;
+  }
+}
+
+// coef[i] for u = i + f, f in [0,1):
+//   S = y_i + f (y_{i+1} - y_i - (2 M_i + M_{i+1})/6) + f^2 M_i/2 + f^3 (M_{i+1} - M_i)/6
+template <typename C>
+__global__ void k_spline_coef(const double *y, const double *Msd, C *coef, int64_t n2);
+
+template <>
+__global__ void k_spline_coef<float4>(const double *y, const double *Msd, float4 *coef, int64_t n2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n2) return;
+  if (i == n2 - 1) { coef[i] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
+  double Mi = (i == 0) ? 0.0 : Msd[i];
+  double Mj = (i + 1 == n2 - 1) ? 0.0 : Msd[i + 1];
+  double c1 = y[i + 1] - y[i] - (2.0 * Mi + Mj) / 6.0;
+  coef[i] = make_float4((float)y[i], (float)c1, (float)(0.5 * Mi), (float)((Mj - Mi) / 6.0));
+}
+
+template <>
+__global__ void k_spline_coef<dcoef4>(const double *y, const double *Msd, dcoef4 *coef, int64_t n2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n2) return;
+  if (i == n2 - 1) { coef[i] = dcoef4{0.0, 0.0, 0.0, 0.0}; return; }
+  double Mi = (i == 0) ? 0.0 : Msd[i];
+  double Mj = (i + 1 == n2 - 1) ? 0.0 : Msd[i + 1];
+  double c1 = y[i + 1] - y[i] - (2.0 * Mi + Mj) / 6.0;
+  coef[i] = dcoef4{y[i], c1, 0.5 * Mi, (Mj - Mi) / 6.0};
+}
+
+fs_status prepare_spline(fs_seg *seg, cudaStream_t st) {
+  int64_t n2 = 2 * seg->g.n;
+  size_t need = sizeof(double) * 2 * (size_t)n2;
+  fs_status s = ensure_buffer(&seg->ctx->scratch, &seg->ctx->scratch_bytes, need, st);
+  if (s != FS_OK) return s;
+  double *dp = (double *)seg->ctx->scratch;
+  double *Msd = dp + n2;
+  int64_t chunks = (n2 - 2 + kSplChunk - 1) / kSplChunk;
+  seg->ctx->launches += (chunks > 0 ? 3 : 1);
+  if (chunks > 0) {
+    k_spline_forward<<<nblk(chunks, 128), 128, 0, st>>>(seg->x2, dp, n2);
+    k_spline_backward<<<nblk(chunks, 128), 128, 0, st>>>(dp, Msd, n2);
+  }
+  if (seg->d.precision == FS_PREC_F32)
+    k_spline_coef<float4><<<nblk(n2), 256, 0, st>>>(seg->x2, Msd, (float4 *)seg->coef, n2);
+  else
+    k_spline_coef<dcoef4><<<nblk(n2), 256, 0, st>>>(seg->x2, Msd, (dcoef4 *)seg->coef, n2);
+  return cuda_status(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ injections (FP64)
+struct InjConst {
+  SkyConst64 K;
+  double A[4];
+  double f0, f1, fl;
+};
+
+// Unit-amplitude response of one injection at t_k = k dt (Eqs. sig, eq:ab), and
+// per-block partial sums of h^2.
+__global__ void k_inject_unit(InjConst c, SegGeom g, double *h, double *partial, int64_t n) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (k < n) {
+    double t = (double)k * g.dt;
+    Geo64 q = geometry64(t, c.K, g);
+    double a, b;
+    ab_eval64(c.K, q.cx, q.sx, &a, &b);
+    double cyc = c.f0 * (t + q.phi) + c.fl * q.phi + c.f1 * (0.5 * t * t + t * q.phi);
+    cyc -= floor(cyc);
+    double sp, cp;
+    sincospi(2.0 * cyc, &sp, &cp);
+    v = c.A[0] * a * cp + c.A[1] * b * cp + c.A[2] * a * sp + c.A[3] * b * sp;
+    h[k] = v;
+  }
+  double sq = v * v;
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += ws[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
+// x += h * snr / rho_unit with rho_unit^2 = (2/S0) dt sum h^2 = sum h^2 / sigma^2.
+__global__ void k_inject_add(double *x, const double *h, const double *partial, int nb, double snr,
+                             double sigma, int64_t n) {
+  __shared__ double scale;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nb; i++) s += partial[i];
+    scale = (s > 0.0) ? snr * sigma / sqrt(s) : 0.0;
+  }
+  __syncthreads();
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) x[k] += h[k] * scale;
+}
+
+fs_status inject64(fs_ctx *ctx, double *x, int64_t n, double dt, double fl, double sigma,
+                   const fs_injection *inj, int n_inj, cudaStream_t st) {
+  int nb = (int)nblk(n);
+  size_t need = sizeof(double) * ((size_t)n + (size_t)nb);
+  fs_status s = ensure_buffer(&ctx->scratch, &ctx->scratch_bytes, need, st);
+  if (s != FS_OK) return s;
+  double *h = (double *)ctx->scratch;
+  double *partial = h + n;
+  SegGeom g{};
+  g.n = n;
+  g.dt = dt;
+  g.fl = fl;
+  g.theta0 = ctx->det.theta_g0 + ctx->det.lon;
+  g.lambda0 = ctx->det.lambda_e0;
+  double re, z;
+  site_radius(ctx->det.lat, &re, &z);
+  g.re_c = re / kC;
+  g.z_c = z / kC;
+  for (int i = 0; i < n_inj; i++) {
+    InjConst c{};
+    sky_constants(inj[i].alpha, inj[i].delta, ctx->det.eps, ctx->det.lat, ctx->det.gamma, g, &c.K);
+    // A_i of Eq. eq:ampone with h0+ = (1 + cos^2 iota)/2, h0x = cos iota (Eq. h0iota, h0 = 1)
+    double hp = 0.5 * (1.0 + inj[i].cos_iota * inj[i].cos_iota), hc = inj[i].cos_iota;
+    double c2p = cos(2 * inj[i].psi), s2p = sin(2 * inj[i].psi);
+    double cp = cos(inj[i].phi0), sp = sin(inj[i].phi0);
+    c.A[0] = hp * c2p * cp - hc * s2p * sp;
+    c.A[1] = hp * s2p * cp + hc * c2p * sp;
+    c.A[2] = -hp * c2p * sp - hc * s2p * cp;
+    c.A[3] = -hp * s2p * sp + hc * c2p * cp;
+    c.f0 = inj[i].f0;
+    c.f1 = inj[i].f1;
+    c.fl = fl;
+    k_inject_unit<<<nb, 256, 0, st>>>(c, g, h, partial, n);
+    k_inject_add<<<nb, 256, 0, st>>>(x, h, partial, nb, inj[i].snr, sigma, n);
+    ctx->launches += 2;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace fs

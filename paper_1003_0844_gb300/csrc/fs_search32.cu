@@ -1,0 +1,622 @@
+// FP32 search path with compensated (double-float) phases.
+//
+// Per sky (A1, k_demod32): source times t_j of Eq. (eq:Bt) by one Newton
+// step from a first delay estimate, the spline value x~_j (Sec. VI.A),
+// a_j, b_j (Sec. II), the heterodyne factor exp(-2 pi i fl phi_m(t_j)) and
+// the spindown phase argument Q_j = t_j^2/2 + t_j phi_m(t_j) (Eq. phas) kept
+// as a double-float.  Output per sky: y^a_j, y^b_j (float2) and Q_j.
+//
+// Per template (sky, f1), the zero-padded transform of length
+// Nfft = N1 * N2 runs in two passes (index n = N2 n1 + n2, bin k = k1 + N1 k2):
+//  pass 1 (k_pass1): multiply by the chirp exp(-2 pi i f1 Q_j), DFTs of
+//    length N1 over n1 for a tile of 16 columns n2 (both signals a and b),
+//    twiddle exp(-2 pi i n2 k1 / Nfft), write Z[k1][n2];
+//  pass 2 (k_pass2): DFTs of length N2 over n2 for 16 or 32 rows k1, then
+//    F_k = 2/(S0 To) (|Fa_k|^2/<a^2> + |Fb_k|^2/<b^2>) (Eq. OS), threshold
+//    compaction, and a transposed store of F in natural bin order.
+// Each length-L DFT (L = P Q) is itself two register stages (DFT_P over the
+// stride-Q samples, twiddle exp(-2 pi i b c / L), DFT_Q) with one exchange
+// through shared memory.
+#include <stdio.h>
+#include "fs_internal.h"
+#include "fs_model.cuh"
+#include "fs_dft.cuh"
+
+namespace fs {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------ per-sky constants
+__global__ void k_skyconst(const double *alpha, const double *delta, int nsky, SegGeom g, double eps,
+                           double lat, double gamma, SkyConst32 *out32, SkyConst64 *out64) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsky) return;
+  SkyConst64 k;
+  sky_constants(alpha[s], delta[s], eps, lat, gamma, g, &k);
+  if (out64) out64[s] = k;
+  if (out32) {
+    SkyConst32 c;
+    c.nx = df_from_double(k.nx);  // the tables carry the factor AU/c
+    c.nyp = df_from_double(k.nyp);
+    c.ca = (float)k.ca;
+    c.sa = (float)k.sa;
+    c.rcd = (float)k.rcd;
+    c.zsd = (float)k.zsd;
+    for (int i = 0; i < 5; i++) c.ea[i] = (float)k.ea[i];
+    for (int i = 0; i < 4; i++) c.eb[i] = (float)k.eb[i];
+    out32[s] = c;
+  }
+}
+
+cudaError_t sky_constants32(const double *alpha, const double *delta, int nsky, const SegGeom &g,
+                            const fs_detector &det, SkyConst32 *out, cudaStream_t st) {
+  k_skyconst<<<(nsky + 127) / 128, 128, 0, st>>>(alpha, delta, nsky, g, det.eps, det.lat, det.gamma, out,
+                                                  nullptr);
+  return cudaGetLastError();
+}
+cudaError_t sky_constants64(const double *alpha, const double *delta, int nsky, const SegGeom &g,
+                            const fs_detector &det, SkyConst64 *out, cudaStream_t st) {
+  k_skyconst<<<(nsky + 127) / 128, 128, 0, st>>>(alpha, delta, nsky, g, det.eps, det.lat, det.gamma,
+                                                  nullptr, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ A1: resample + demodulate one sky
+struct DemodArgs {
+  SegGeom g;
+  df32 dt2;            // dt as double-float
+  float dt, inv_dt, two_over_dt;
+  df32 fl;
+  const SkyConst32 *sky;
+  const float4 *tab0, *tab1;  // indexed by m + margin
+  const float4 *coef;         // spline intervals [2n]
+  const float *x32;           // data, nearest-neighbour path
+  float2 *ya, *yb, *qq;       // [nsky][stride]
+  int64_t stride, npad;
+  double *partial;            // [nsky][gridDim.x][2]
+  double *tsrc;               // optional [n] (first sky only)
+};
+
+template <int INTERP>
+__global__ void __launch_bounds__(256) k_demod32(DemodArgs A) {
+  const int s = blockIdx.y;
+  const SkyConst32 K = A.sky[s];
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float a2 = 0.f, b2 = 0.f;
+  if (j < A.npad) {
+    float2 oa = make_float2(0.f, 0.f), ob = oa, oq = oa;
+    if (j < A.g.n) {
+      const int64_t M = A.g.margin;
+      // 1) delay at the output time t_b = j dt, plain FP32 (only seeds the solve)
+      const float4 T0 = A.tab0[j + M], T1 = A.tab1[j + M];
+      const float phi0 = fmaf(K.nx.hi, T0.x, K.nyp.hi * T0.z) + fmaf(K.rcd, K.ca * T1.x + K.sa * T1.y, K.zsd);
+      // 2) first source time t1 = m1 dt + tau1 with t1 - t_b = -phi0 (up to rounding)
+      const float kf = rintf(-phi0 * A.inv_dt);
+      const int k1 = (int)kf;
+      const df32 kd = two_prod(kf, A.dt2.hi);  // k1 dt as an exact pair (plus kf * dt.lo)
+      const float kdlo = fmaf(kf, A.dt2.lo, kd.lo);
+      const float tau1 = (-phi0 - kd.hi) - kdlo;
+      const int64_t m1 = j + k1;
+      const float4 U0 = A.tab0[m1 + M], U1 = A.tab1[m1 + M];
+      // 3) delay at t1: orbit term as double-float at the grid point, rotated by Omega_o tau1
+      df32 P = df_add(df_mul(K.nx, df32{U0.x, U0.y}), df_mul(K.nyp, df32{U0.z, U0.w}));
+      const float eo = (float)kOmegaO * tau1;
+      const float Qo = fmaf(-K.nx.hi, U0.z, K.nyp.hi * U0.x);  // d(orbit)/d(lambda)
+      const float orb = fmaf(eo, Qo, -0.5f * eo * eo * P.hi);
+      const float er = (float)kOmegaR * tau1;
+      const float ce = 1.f - 0.5f * er * er, se = er - er * er * er * (1.f / 6.f);
+      const float cth = fmaf(U1.x, ce, -U1.y * se), sth = fmaf(U1.y, ce, U1.x * se);
+      float cx = fmaf(K.ca, cth, K.sa * sth);   // cos(alpha - theta(t1))
+      float sx = fmaf(K.sa, cth, -K.ca * sth);  // sin(alpha - theta(t1))
+      const float rot = fmaf(K.rcd, cx, K.zsd);
+      const float phidot = fmaf((float)kOmegaO, Qo, K.rcd * (float)kOmegaR * sx);
+      // 4) Newton step on g(t) = t + phi_m(t) - t_b at t1
+      const df32 Ah = two_sum(kd.hi, P.hi);
+      const float gres = ((Ah.hi + tau1) + (Ah.lo + kdlo)) + ((P.lo + orb) + rot);
+      const float delta = -gres / (1.f + phidot);
+      const float tau = tau1 + delta;  // t_j = m1 dt + tau
+      const float small = ((P.lo + orb) + rot) + phidot * delta;
+      const df32 phim = quick_two_sum(P.hi, small);  // phi_m(t_j)
+      const float eta = (float)kOmegaR * delta;
+      const float cxj = fmaf(sx, eta, cx), sxj = fmaf(-cx, eta, sx);
+      cx = cxj;
+      sx = sxj;
+      // 5) data at the source time
+      float xr = 0.f;
+      if (INTERP == FS_INTERP_SPLINE2X) {
+        const float v = tau * A.two_over_dt;
+        const float fv = floorf(v);
+        const int64_t i = 2 * m1 + (int64_t)fv;
+        const float f = v - fv;
+        const int64_t ilast = 2 * A.g.n - 2;
+        if ((i >= 0 && i < ilast) || (i == ilast && f == 0.f)) {
+          const float4 c = A.coef[i];
+          xr = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
+        }
+      } else {
+        const int64_t kk = m1 + (int64_t)rintf(tau * A.inv_dt);
+        if (kk >= 0 && kk < A.g.n) xr = A.x32[kk];
+      }
+      // 6) amplitude modulation at t_j
+      const float c2 = fmaf(cx, cx, -sx * sx), s2 = 2.f * sx * cx;
+      const float av = fmaf(K.ea[0], c2, fmaf(K.ea[1], s2, fmaf(K.ea[2], cx, fmaf(K.ea[3], sx, K.ea[4]))));
+      const float bv = fmaf(K.eb[0], c2, fmaf(K.eb[1], s2, fmaf(K.eb[2], cx, K.eb[3] * sx)));
+      a2 = av * av;
+      b2 = bv * bv;
+      // 7) heterodyne exp(-2 pi i fl phi_m(t_j))
+      const float2 h = expm2pi(df_mul_frac(A.fl, phim));
+      oa = make_float2(xr * av * h.x, xr * av * h.y);
+      ob = make_float2(xr * bv * h.x, xr * bv * h.y);
+      // 8) Q_j = t_j (t_j/2 + phi_m(t_j)) as double-float
+      const df32 tj = df_add_f(df32{U1.z, U1.w}, tau);
+      const df32 U = df_add(df32{0.5f * tj.hi, 0.5f * tj.lo}, phim);
+      const df32 Q = df_mul(tj, U);
+      oq = make_float2(Q.hi, Q.lo);
+      if (A.tsrc && s == 0) A.tsrc[j] = (double)m1 * A.g.dt + (double)tau;
+    }
+    A.ya[s * A.stride + j] = oa;
+    A.yb[s * A.stride + j] = ob;
+    A.qq[s * A.stride + j] = oq;
+  }
+  // deterministic block sums of a^2, b^2 in FP64
+  double da = a2, db = b2;
+  for (int o = 16; o > 0; o >>= 1) {
+    da += __shfl_down_sync(kFull, da, o);
+    db += __shfl_down_sync(kFull, db, o);
+  }
+  __shared__ double wa[8], wb[8];
+  if ((threadIdx.x & 31) == 0) { wa[threadIdx.x >> 5] = da; wb[threadIdx.x >> 5] = db; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < 8; w++) { sa += wa[w]; sb += wb[w]; }
+    double *p = A.partial + ((int64_t)s * gridDim.x + blockIdx.x) * 2;
+    p[0] = sa;
+    p[1] = sb;
+  }
+}
+
+// <a^2>, <b^2> over the n output samples and the per-sky F normalisation
+// (cF / <a^2>, cF / <b^2>) with cF = 2 dt^2 / (S0 To) = 2 dt / (S0 n).
+__global__ void k_demod_finalize(const double *partial, int nb, int64_t n, double dt, double S0, float2 *norm,
+                                 double2 *ab2) {
+  const int s = blockIdx.x;
+  double sa = 0.0, sb = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    sa += partial[((int64_t)s * nb + i) * 2];
+    sb += partial[((int64_t)s * nb + i) * 2 + 1];
+  }
+  __shared__ double ra[256], rb[256];
+  ra[threadIdx.x] = sa;
+  rb[threadIdx.x] = sb;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) { ra[threadIdx.x] += ra[threadIdx.x + o]; rb[threadIdx.x] += rb[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double ma = ra[0] / (double)n, mb = rb[0] / (double)n;
+    double cF = 2.0 * dt / (S0 * (double)n);
+    if (norm) norm[s] = make_float2((float)(cF / ma), (float)(cF / mb));
+    if (ab2) ab2[s] = make_double2(ma, mb);
+  }
+}
+
+// ------------------------------------------------------------------ pass 1
+struct Pass1Args {
+  const float2 *ya, *yb, *qq;
+  int64_t sky_stride;
+  const double *f1;
+  int nspin, tmpl0;
+  int N2, n1max;
+  int64_t nfft;
+  float2 *Z;  // [batch][2][N1][N2]
+};
+
+template <int P, int Q>
+__global__ void __launch_bounds__(32 * P, 1) k_pass1(Pass1Args A) {
+  constexpr int L = P * Q;
+  constexpr int S = Q / P;
+  extern __shared__ float2 smem[];
+  float2 *xch = smem;           // [Q][P][32]
+  float2 *twL = smem + L * 32;  // W_L^q
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  const int col = lane & 15, sig = lane >> 4;
+  const int tiles = A.N2 >> 4;
+  const int bt = blockIdx.x / tiles, tile = blockIdx.x - bt * tiles;
+  const int tm = A.tmpl0 + bt;
+  const int sky = tm / A.nspin, spin = tm - sky * A.nspin;
+  const int n2 = tile * 16 + col;
+  for (int q = threadIdx.x; q < L; q += blockDim.x) twL[q] = expm2pi((float)q * (1.0f / L));
+  const float2 *y = (sig ? A.yb : A.ya) + sky * A.sky_stride;
+  const float2 *qq = A.qq + sky * A.sky_stride;
+  const df32 f1 = df_from_double(A.f1[spin]);
+  const int n1max = A.n1max;
+  const int64_t N2 = A.N2;
+
+  float2 v[Q];
+  // load y_j and the chirp exp(-2 pi i f1 Q_j); the two signal lanes of a
+  // column share the chirp: each computes every other one and swaps.
+  sfor<0, S>([&](auto s) {
+    const int b = t + P * s;
+    sfor<0, P / 2>([&](auto ap) {
+      constexpr int a0 = 2 * ap, a1 = 2 * ap + 1;
+      const int my = Q * (a0 + sig) + b;
+      float2 cm = make_float2(0.f, 0.f);
+      if (my < n1max) {
+        const float2 qv = qq[my * N2 + n2];
+        cm = expm2pi(df_mul_frac(f1, df32{qv.x, qv.y}));
+      }
+      float2 cp;
+      cp.x = __shfl_xor_sync(kFull, cm.x, 16);
+      cp.y = __shfl_xor_sync(kFull, cm.y, 16);
+      const float2 c0 = sig ? cp : cm, c1 = sig ? cm : cp;
+      const int na = Q * a0 + b, nb = Q * a1 + b;
+      v[s * P + a0] = (na < n1max) ? cmul(y[na * N2 + n2], c0) : make_float2(0.f, 0.f);
+      v[s * P + a1] = (nb < n1max) ? cmul(y[nb * N2 + n2], c1) : make_float2(0.f, 0.f);
+    });
+  });
+  __syncthreads();  // twL ready
+  sfor<0, S>([&](auto s) {
+    const int b = t + P * s;
+    dft_inplace<P>(v + s * P);
+    sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twL[(b * c) & (L - 1)]); });
+    sfor<0, P>([&](auto c) { xch[(b * P + c) * 32 + lane] = v[s * P + c]; });
+  });
+  __syncthreads();
+  sfor<0, Q>([&](auto bb) { v[bb] = xch[(bb * P + t) * 32 + lane]; });
+  dft_inplace<Q>(v);  // v[d] = X[k1 = t + P d] of column n2
+  // inter-pass twiddle exp(-2 pi i n2 k1 / Nfft): exact anchors every 16 d, recurrence between
+  const int64_t nf = A.nfft;
+  const float inv_nf = 1.0f / (float)nf;
+  const float2 step = expm2pi((float)(((int64_t)n2 * P) & (nf - 1)) * inv_nf);
+  float2 w = make_float2(1.f, 0.f);
+  sfor<0, Q>([&](auto d) {
+    if constexpr (d % 16 == 0) {
+      w = expm2pi((float)(((int64_t)n2 * (t + P * d)) & (nf - 1)) * inv_nf);
+    } else {
+      w = cmul(w, step);
+    }
+    v[d] = cmul(v[d], w);
+  });
+  float2 *Zs = A.Z + ((int64_t)bt * 2 + sig) * nf;
+  sfor<0, Q>([&](auto d) { Zs[(int64_t)(t + P * d) * N2 + n2] = v[d]; });
+}
+
+// ------------------------------------------------------------------ pass 2 + F epilogue
+struct Pass2Args {
+  const float2 *Z;
+  int N1, N2;
+  int64_t nfft;
+  const float2 *norm;  // per sky of the group
+  int nspin, tmpl0;
+  int sky_base;        // global index of the group's first sky
+  float *F;            // NULL or F_out + (global template of the group's first template) * nbins
+  int64_t nbins;
+  float thr;
+  fs_candidate *cand;
+  int64_t cap;
+  unsigned long long *ncand;
+  uint32_t *flags;
+};
+
+template <int P, int Q, int WARPS, bool FULLBINS>
+__global__ void __launch_bounds__(32 * WARPS, 1) k_pass2(Pass2Args A) {
+  constexpr int L = P * Q, T = P, G = 16 / T, R = WARPS * G, S = Q / P;
+  constexpr int D = FULLBINS ? Q : Q / 2;  // d values with k2 = t + P d in the output band
+  constexpr int XW = P * (Q + 1);          // exchange floats2 per sub-DFT
+  extern __shared__ float2 smem[];
+  float2 *twL = smem + WARPS * 2 * G * XW;
+  float *Fs = (float *)(twL + L);  // [D*P][R+1]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = lane % T, sig = (lane / T) & 1, gr = lane / (2 * T);
+  const int row = w * G + gr;
+  const int rtiles = A.N1 / R;
+  const int bt = blockIdx.x / rtiles, rt = blockIdx.x - bt * rtiles;
+  const int k1 = rt * R + row;
+  const int tm = A.tmpl0 + bt;
+  const int sky = tm / A.nspin, spin = tm - sky * A.nspin;
+  for (int q = threadIdx.x; q < L; q += blockDim.x) twL[q] = expm2pi((float)q * (1.0f / L));
+  const float2 *z = A.Z + ((int64_t)bt * 2 + sig) * A.nfft + (int64_t)k1 * A.N2;
+  float2 v[Q];
+  sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = z[Q * a + t + P * s]; }); });
+  __syncthreads();  // twL ready
+  float2 *xw = smem + (w * 2 * G + (sig + 2 * gr)) * XW;
+  sfor<0, S>([&](auto s) {
+    const int b = t + P * s;
+    dft_inplace<P>(v + s * P);
+    sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twL[(b * c) & (L - 1)]); });
+    sfor<0, P>([&](auto c) { xw[c * (Q + 1) + b] = v[s * P + c]; });
+  });
+  __syncwarp();
+  sfor<0, Q>([&](auto bb) { v[bb] = xw[t * (Q + 1) + bb]; });
+  dft_inplace<Q>(v);  // v[d] = X[k2 = t + P d] of row k1
+  const float2 nrm = A.norm[sky];
+  const float myn = sig ? nrm.y : nrm.x;
+  float p[D];
+  sfor<0, D>([&](auto d) { p[d] = fmaf(v[d].x, v[d].x, v[d].y * v[d].y) * myn; });
+  const unsigned lt_mask = (1u << lane) - 1u;
+  sfor<0, D / 2>([&](auto dp) {
+    const float send = sig ? p[dp] : p[dp + D / 2];
+    const float mine = sig ? p[dp + D / 2] : p[dp];
+    const float Fv = mine + __shfl_xor_sync(kFull, send, T);
+    const int d = dp + sig * (D / 2);
+    const int k2 = t + P * d;
+    Fs[k2 * (R + 1) + row] = Fv;
+    const bool hit = Fv > A.thr;
+    const unsigned m = __ballot_sync(kFull, hit);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(A.ncand, (unsigned long long)__popc(m));
+      base = __shfl_sync(kFull, base, leader);
+      if (hit) {
+        const unsigned long long idx = base + __popc(m & lt_mask);
+        if ((long long)idx < A.cap) {
+          fs_candidate c;
+          c.sky = (uint32_t)(A.sky_base + sky);
+          c.spin = (uint32_t)spin;
+          c.bin = (uint32_t)(k1 + A.N1 * k2);
+          c.F = Fv;
+          A.cand[idx] = c;
+        } else {
+          atomicOr(A.flags, ERRF_CAPACITY);
+        }
+      }
+    }
+  });
+  if (A.F == nullptr) return;
+  __syncthreads();
+  float *Fo = A.F + (int64_t)tm * A.nbins + rt * R;
+  constexpr int K2 = D * P;
+  for (int idx = threadIdx.x; idx < K2 * R; idx += blockDim.x) {
+    const int k2 = idx / R, r = idx - k2 * R;
+    __stcs(Fo + r + (int64_t)A.N1 * k2, Fs[k2 * (R + 1) + r]);
+  }
+}
+
+// ------------------------------------------------------------------ host orchestration
+struct FftShape {
+  int N1, N2;
+};
+static bool fft_shape(int64_t nfft, FftShape *s) {
+  int p = 0;
+  while (((int64_t)1 << p) < nfft) p++;
+  if (((int64_t)1 << p) != nfft || p < 12 || p > 18) return false;
+  s->N1 = 1 << ((p + 1) / 2);
+  s->N2 = 1 << (p / 2);
+  return true;
+}
+
+constexpr int kPass2Warps = 16;
+
+template <int P, int Q>
+static size_t pass1_smem() { return sizeof(float2) * ((size_t)P * Q * 32 + (size_t)P * Q); }
+template <int P, int Q, bool FULL>
+static size_t pass2_smem() {
+  constexpr int G = 16 / P, R = kPass2Warps * G, D = FULL ? Q : Q / 2;
+  return sizeof(float2) * ((size_t)kPass2Warps * 2 * G * P * (Q + 1) + (size_t)P * Q) +
+         sizeof(float) * (size_t)D * P * (R + 1);
+}
+
+template <int P, int Q>
+static cudaError_t launch_pass1(const Pass1Args &a, int nb, cudaStream_t st) {
+  size_t sm = pass1_smem<P, Q>();
+  cudaError_t e = cudaFuncSetAttribute(k_pass1<P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_pass1<P, Q><<<nb * (a.N2 / 16), 32 * P, sm, st>>>(a);
+  return cudaGetLastError();
+}
+template <int P, int Q, bool FULL>
+static cudaError_t launch_pass2(const Pass2Args &a, int nb, cudaStream_t st) {
+  size_t sm = pass2_smem<P, Q, FULL>();
+  auto kern = k_pass2<P, Q, kPass2Warps, FULL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  constexpr int R = kPass2Warps * (16 / P);
+  kern<<<nb * (a.N1 / R), 32 * kPass2Warps, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t dispatch_pass1(int N1, const Pass1Args &a, int nb, cudaStream_t st) {
+  switch (N1) {
+    case 64: return launch_pass1<8, 8>(a, nb, st);
+    case 128: return launch_pass1<8, 16>(a, nb, st);
+    case 256: return launch_pass1<16, 16>(a, nb, st);
+    case 512: return launch_pass1<16, 32>(a, nb, st);
+  }
+  return cudaErrorInvalidValue;
+}
+static cudaError_t dispatch_pass2(int N2, bool full, const Pass2Args &a, int nb, cudaStream_t st) {
+  switch (N2 * 2 + (full ? 1 : 0)) {
+    case 128: return launch_pass2<8, 8, false>(a, nb, st);
+    case 129: return launch_pass2<8, 8, true>(a, nb, st);
+    case 256: return launch_pass2<8, 16, false>(a, nb, st);
+    case 257: return launch_pass2<8, 16, true>(a, nb, st);
+    case 512: return launch_pass2<16, 16, false>(a, nb, st);
+    case 513: return launch_pass2<16, 16, true>(a, nb, st);
+    case 1024: return launch_pass2<16, 32, false>(a, nb, st);
+    case 1025: return launch_pass2<16, 32, true>(a, nb, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+struct Ws32 {
+  SkyConst32 *skyc;
+  float2 *ya, *yb, *qq, *norm;
+  double2 *ab2;
+  double *partial;
+  float2 *Z;
+  int64_t stride;
+  int nblk_a1;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static fs_status workspace32(fs_ctx *ctx, const fs_seg *seg, int G, int B, int64_t npad, cudaStream_t st,
+                             Ws32 *w) {
+  int64_t stride = (npad + 63) & ~(int64_t)63;
+  int nblk = (int)((npad + 255) / 256);
+  size_t off = 0;
+  size_t o_sky = off; off = align256(off + sizeof(SkyConst32) * G);
+  size_t o_ya = off; off = align256(off + sizeof(float2) * stride * G);
+  size_t o_yb = off; off = align256(off + sizeof(float2) * stride * G);
+  size_t o_qq = off; off = align256(off + sizeof(float2) * stride * G);
+  size_t o_nm = off; off = align256(off + sizeof(float2) * G);
+  size_t o_ab = off; off = align256(off + sizeof(double2) * G);
+  size_t o_pa = off; off = align256(off + sizeof(double) * 2 * (size_t)nblk * G);
+  size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)seg->g.nfft * B);
+  fs_status s = ensure_buffer(&ctx->ws, &ctx->ws_bytes, off, st);
+  if (s != FS_OK) return s;
+  char *base = (char *)ctx->ws;
+  w->skyc = (SkyConst32 *)(base + o_sky);
+  w->ya = (float2 *)(base + o_ya);
+  w->yb = (float2 *)(base + o_yb);
+  w->qq = (float2 *)(base + o_qq);
+  w->norm = (float2 *)(base + o_nm);
+  w->ab2 = (double2 *)(base + o_ab);
+  w->partial = (double *)(base + o_pa);
+  w->Z = (float2 *)(base + o_z);
+  w->stride = stride;
+  w->nblk_a1 = nblk;
+  return FS_OK;
+}
+
+static DemodArgs demod_args(const fs_seg *seg, const Ws32 &w, int64_t npad) {
+  DemodArgs A{};
+  A.g = seg->g;
+  A.dt2 = df_from_double(seg->g.dt);
+  A.dt = (float)seg->g.dt;
+  A.inv_dt = (float)(1.0 / seg->g.dt);
+  A.two_over_dt = (float)(2.0 / seg->g.dt);
+  A.fl = df_from_double(seg->g.fl);
+  A.sky = w.skyc;
+  A.tab0 = seg->tab0;
+  A.tab1 = seg->tab1;
+  A.coef = (const float4 *)seg->coef;
+  A.x32 = seg->x32;
+  A.ya = w.ya;
+  A.yb = w.yb;
+  A.qq = w.qq;
+  A.stride = w.stride;
+  A.npad = npad;
+  A.partial = w.partial;
+  A.tsrc = nullptr;
+  return A;
+}
+
+static cudaError_t launch_demod(const DemodArgs &A, int nsky, int nblk, int interp, cudaStream_t st) {
+  dim3 grid(nblk, nsky);
+  if (interp == FS_INTERP_NEAREST) k_demod32<FS_INTERP_NEAREST><<<grid, 256, 0, st>>>(A);
+  else k_demod32<FS_INTERP_SPLINE2X><<<grid, 256, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
+                   const double *f1, int nspin, float thr, float *F, int64_t nbins, fs_candidate *cand,
+                   int64_t cap, int64_t *ncand, cudaStream_t st) {
+  FftShape sh;
+  if (!fft_shape(seg->g.nfft, &sh)) return FS_ERR_SHAPE;
+  const int64_t n = seg->g.n;
+  const int n1max = (int)((n + sh.N2 - 1) / sh.N2);
+  const int64_t npad = (int64_t)n1max * sh.N2;
+  const int G = ctx->group_skies < nsky ? ctx->group_skies : nsky;
+  const int B = ctx->batch_templates;
+  Ws32 w;
+  fs_status s = workspace32(ctx, seg, G, B, npad, st, &w);
+  if (s != FS_OK) return s;
+  if (cudaMemsetAsync(ncand, 0, sizeof(int64_t), st) != cudaSuccess) return FS_ERR_CUDA;
+  const bool full = (nbins == seg->g.nfft);
+  DemodArgs DA = demod_args(seg, w, npad);
+  for (int g0 = 0; g0 < nsky; g0 += G) {
+    const int gs = (nsky - g0) < G ? (nsky - g0) : G;
+    {
+      ProfScope ps(ctx, PROF_OTHER, st);
+      if (sky_constants32(alpha + g0, delta + g0, gs, seg->g, ctx->det, w.skyc, st) != cudaSuccess) return FS_ERR_CUDA;
+    }
+    {
+      ProfScope ps(ctx, PROF_DEMOD, st);
+      if (launch_demod(DA, gs, w.nblk_a1, seg->d.interp, st) != cudaSuccess) return FS_ERR_CUDA;
+    }
+    {
+      ProfScope ps(ctx, PROF_OTHER, st);
+      k_demod_finalize<<<gs, 256, 0, st>>>(w.partial, w.nblk_a1, n, seg->g.dt, seg->g.S0, w.norm, w.ab2);
+    }
+    ctx->launches += 3;
+    const int ntm = gs * nspin;
+    for (int b0 = 0; b0 < ntm; b0 += B) {
+      const int nb = (ntm - b0) < B ? (ntm - b0) : B;
+      Pass1Args p1{};
+      p1.ya = w.ya;
+      p1.yb = w.yb;
+      p1.qq = w.qq;
+      p1.sky_stride = w.stride;
+      p1.f1 = f1;
+      p1.nspin = nspin;
+      p1.tmpl0 = b0;
+      p1.N2 = sh.N2;
+      p1.n1max = n1max;
+      p1.nfft = seg->g.nfft;
+      p1.Z = w.Z;
+      {
+        ProfScope ps(ctx, PROF_PASS1, st);
+        if (dispatch_pass1(sh.N1, p1, nb, st) != cudaSuccess) return FS_ERR_CUDA;
+      }
+      Pass2Args p2{};
+      p2.Z = w.Z;
+      p2.N1 = sh.N1;
+      p2.N2 = sh.N2;
+      p2.nfft = seg->g.nfft;
+      p2.norm = w.norm;
+      p2.nspin = nspin;
+      p2.tmpl0 = b0;
+      p2.sky_base = g0;
+      p2.F = F ? F + (int64_t)g0 * nspin * nbins : nullptr;
+      p2.nbins = nbins;
+      p2.thr = thr;
+      p2.cand = cand;
+      p2.cap = cap;
+      p2.ncand = (unsigned long long *)ncand;
+      p2.flags = ctx->d_flags;
+      {
+        ProfScope ps(ctx, PROF_PASS2, st);
+        if (dispatch_pass2(sh.N2, full, p2, nb, st) != cudaSuccess) return FS_ERR_CUDA;
+      }
+      ctx->launches += 2;
+    }
+  }
+  return FS_OK;
+}
+
+// Stage access: A1 for one sky, widened to double.
+__global__ void k_widen(const float2 *ya, const float2 *yb, double *oa, double *ob, int64_t n) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  oa[2 * j] = ya[j].x;
+  oa[2 * j + 1] = ya[j].y;
+  ob[2 * j] = yb[j].x;
+  ob[2 * j + 1] = yb[j].y;
+}
+
+fs_status demod32_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, double *ya, double *yb,
+                        double *tsrc, double *ab2, cudaStream_t st) {
+  const int64_t n = seg->g.n;
+  Ws32 w;
+  fs_status s = workspace32(ctx, seg, 1, 1, n, st, &w);
+  if (s != FS_OK) return s;
+  // alpha/delta are host values: stage them through the partial buffer's tail is not
+  // possible before allocation, so use a small device copy.
+  double hd[2] = {alpha, delta};
+  double *dd = (double *)w.ab2;  // 16 bytes, overwritten by finalize afterwards
+  if (cudaMemcpyAsync(dd, hd, sizeof(hd), cudaMemcpyHostToDevice, st) != cudaSuccess) return FS_ERR_CUDA;
+  if (sky_constants32(dd, dd + 1, 1, seg->g, ctx->det, w.skyc, st) != cudaSuccess) return FS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FS_ERR_CUDA;  // hd is on the stack
+  DemodArgs A = demod_args(seg, w, n);
+  A.tsrc = tsrc;
+  if (launch_demod(A, 1, w.nblk_a1, seg->d.interp, st) != cudaSuccess) return FS_ERR_CUDA;
+  k_demod_finalize<<<1, 256, 0, st>>>(w.partial, w.nblk_a1, n, seg->g.dt, seg->g.S0, nullptr, (double2 *)ab2);
+  k_widen<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.ya, w.yb, ya, yb, n);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace fs

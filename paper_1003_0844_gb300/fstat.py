@@ -1,0 +1,263 @@
+"""Python binding of the C ABI in include/fstat.h (argument marshalling only).
+
+Every computation runs in the CUDA library libfstat.so built in-tree by
+``paper_1003_0844_gb300.build``; nothing here computes on the CPU.  Device
+arrays are torch tensors; the current torch CUDA stream is passed to the
+library unless a stream is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfstat.so")
+
+FS_OK = 0
+STATUS = {0: "FS_OK", 1: "FS_ERR_ARG", 2: "FS_ERR_SHAPE", 3: "FS_ERR_CAPACITY", 4: "FS_ERR_NONFINITE",
+          5: "FS_ERR_CUDA", 6: "FS_ERR_TIMEOUT", 7: "FS_ERR_UNSUPPORTED", 8: "FS_ERR_NOMEM"}
+PREC = {"f32": 0, "f64": 1}
+INTERP = {"spline": 0, "nearest": 1}
+EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_seg_destroy", "fs_seg_load", "fs_search",
+           "fs_sync_status", "fs_strerror", "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling",
+           "fs_get_stats"]
+PROF_KINDS = ("prepare", "demodulate", "pass1", "pass2", "other")
+
+
+class FstatError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s failed: %s (%d)" % (what, STATUS.get(status, "?"), status))
+        self.status = status
+
+
+class _Detector(ctypes.Structure):
+    _fields_ = [("lat", ctypes.c_double), ("lon", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("eps", ctypes.c_double), ("lambda_e0", ctypes.c_double), ("theta_g0", ctypes.c_double)]
+
+
+class _SegDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nfft", ctypes.c_int64), ("dt", ctypes.c_double), ("fl", ctypes.c_double),
+                ("S0", ctypes.c_double), ("precision", ctypes.c_int32), ("interp", ctypes.c_int32),
+                ("x_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double * 5), ("count", ctypes.c_int64 * 5)]
+
+
+class _Injection(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("f0", "f1", "alpha", "delta", "psi", "cos_iota", "phi0", "snr")]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libfstat.so (built by paper_1003_0844_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libfstat.so is not built (%s); run paper_1003_0844_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, f32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+    lib.fs_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Detector), i32]
+    lib.fs_destroy.argtypes = [vp]
+    lib.fs_destroy.restype = None
+    lib.fs_prepare_segment.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(_SegDesc), vp, vp]
+    lib.fs_seg_destroy.argtypes = [vp]
+    lib.fs_seg_destroy.restype = None
+    lib.fs_seg_load.argtypes = [vp, vp, vp]
+    lib.fs_set_profiling.argtypes = [vp, i32]
+    lib.fs_get_stats.argtypes = [vp, ctypes.POINTER(_Stats), i32]
+    lib.fs_search.argtypes = [vp, vp, vp, vp, i32, vp, i32, f32, vp, i64, vp, i64, vp, vp]
+    lib.fs_sync_status.argtypes = [vp, vp]
+    lib.fs_strerror.argtypes = [ctypes.c_int]
+    lib.fs_strerror.restype = ctypes.c_char_p
+    lib.fs_seg_upsampled.argtypes = [vp, vp, vp]
+    lib.fs_demodulate.argtypes = [vp, vp, f64, f64, vp, vp, vp, vp, vp]
+    lib.fs_inject.argtypes = [vp, vp, i64, f64, f64, f64, ctypes.POINTER(_Injection), i32, vp]
+    for name in ("fs_create", "fs_prepare_segment", "fs_seg_load", "fs_search", "fs_sync_status",
+                 "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling", "fs_get_stats"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != FS_OK:
+        raise FstatError(status, what)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _need_cuda(t: torch.Tensor, name: str, dtype=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must be %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+class Context:
+    """A library context on one CUDA device for one detector (fs_create)."""
+
+    def __init__(self, det, device: int = 0):
+        self.lib = load_library()
+        d = _Detector(det.lat, det.lon, det.gamma, det.eps, det.lambda_e0, det.theta_g0)
+        h = ctypes.c_void_p()
+        _check(self.lib.fs_create(ctypes.byref(h), ctypes.byref(d), int(device)), "fs_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            self.lib.fs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync_status(self, stream=None) -> int:
+        return self.lib.fs_sync_status(self.handle, _stream(stream))
+
+    def check(self, stream=None):
+        _check(self.sync_status(stream), "device status")
+
+    def set_profiling(self, on: bool):
+        _check(self.lib.fs_set_profiling(self.handle, 1 if on else 0), "fs_set_profiling")
+
+    def stats(self, reset: bool = True) -> dict:
+        """Launch count and, with profiling on, summed event time / launches per kind."""
+        st = _Stats()
+        _check(self.lib.fs_get_stats(self.handle, ctypes.byref(st), 1 if reset else 0), "fs_get_stats")
+        return {"launches": st.launches,
+                "ms": {k: st.ms[i] for i, k in enumerate(PROF_KINDS)},
+                "count": {k: st.count[i] for i, k in enumerate(PROF_KINDS)}}
+
+
+class Segment:
+    """One prepared data segment (fs_prepare_segment): tables, x2 upsampling, spline."""
+
+    def __init__(self, ctx: Context, x: torch.Tensor, dt: float, nfft: int, fl: float, S0: float,
+                 precision: str = "f32", interp: str = "spline", stream=None):
+        _need_cuda(x, "x")
+        if x.dtype not in (torch.float32, torch.float64):
+            raise ValueError("x must be float32 or float64")
+        self.ctx = ctx
+        self.n = x.numel()
+        self.nfft = int(nfft)
+        self.dt, self.fl, self.S0 = float(dt), float(fl), float(S0)
+        self.precision = precision
+        d = _SegDesc(self.n, self.nfft, self.dt, self.fl, self.S0, PREC[precision], INTERP[interp],
+                     0 if x.dtype == torch.float32 else 1, 0)
+        h = ctypes.c_void_p()
+        _check(ctx.lib.fs_prepare_segment(ctx.handle, ctypes.byref(h), ctypes.byref(d), _ptr(x), _stream(stream)),
+               "fs_prepare_segment")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.fs_seg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, x: torch.Tensor, stream=None):
+        """Re-run the preparation on new data of the same shape (fs_seg_load, no allocation)."""
+        _need_cuda(x, "x")
+        if x.numel() != self.n:
+            raise ValueError("x has %d samples, the segment %d" % (x.numel(), self.n))
+        _check(self.ctx.lib.fs_seg_load(self.handle, _ptr(x), _stream(stream)), "fs_seg_load")
+
+    def upsampled(self, stream=None) -> torch.Tensor:
+        out = torch.empty(2 * self.n, dtype=torch.float64, device="cuda")
+        _check(self.ctx.lib.fs_seg_upsampled(self.handle, _ptr(out), _stream(stream)), "fs_seg_upsampled")
+        return out
+
+
+@dataclasses.dataclass
+class SearchResult:
+    F: torch.Tensor | None         # [nsky*nspin, nbins] or None
+    cand: torch.Tensor             # int32 [cap, 4]: sky, spin, bin, F bits
+    n_cand: torch.Tensor           # int64 [1] on the device
+
+    def candidates(self):
+        """(sky, spin, bin, F) numpy arrays of the stored candidates (synchronises)."""
+        n = int(self.n_cand.item())
+        n = min(n, self.cand.shape[0])
+        c = self.cand[:n].cpu()
+        F = c[:, 3].view(torch.float32).numpy().copy()
+        u = c[:, :3].numpy().astype("int64")
+        return u[:, 0], u[:, 1], u[:, 2], F
+
+
+def search(ctx: Context, seg: Segment, alpha: torch.Tensor, delta: torch.Tensor, f1: torch.Tensor,
+           F_thr: float, write_F: bool = True, nbins: int | None = None, cand_cap: int = 1 << 16,
+           F_out: torch.Tensor | None = None, cand: torch.Tensor | None = None,
+           n_cand: torch.Tensor | None = None, stream=None) -> SearchResult:
+    """fs_search over len(alpha) x len(f1) templates; returns device tensors."""
+    for t, nm in ((alpha, "alpha"), (delta, "delta"), (f1, "f1")):
+        _need_cuda(t, nm, torch.float64)
+    nsky, nspin = alpha.numel(), f1.numel()
+    if delta.numel() != nsky:
+        raise ValueError("alpha and delta differ in length")
+    nb = seg.nfft // 2 if nbins is None else int(nbins)
+    fdt = torch.float32 if seg.precision == "f32" else torch.float64
+    if write_F and F_out is None:
+        F_out = torch.empty((nsky * nspin, nb), dtype=fdt, device="cuda")
+    if not write_F:
+        F_out = None
+    if cand is None:
+        cand = torch.empty((max(cand_cap, 1), 4), dtype=torch.int32, device="cuda")
+    if n_cand is None:
+        n_cand = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = ctx.lib.fs_search(ctx.handle, seg.handle, _ptr(alpha), _ptr(delta), nsky, _ptr(f1), nspin,
+                           float(F_thr), _ptr(F_out) if F_out is not None else None, nb, _ptr(cand),
+                           int(cand.shape[0]) if cand_cap > 0 else 0, _ptr(n_cand), _stream(stream))
+    _check(st, "fs_search")
+    return SearchResult(F_out, cand, n_cand)
+
+
+def demodulate(ctx: Context, seg: Segment, alpha: float, delta: float, stream=None):
+    """Per-sky resampled, demodulated series (fs_demodulate) as device tensors:
+    (y^a complex128 [n], y^b complex128 [n], t_src float64 [n], (<a^2>, <b^2>))."""
+    n = seg.n
+    ya = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+    yb = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+    ts = torch.empty(n, dtype=torch.float64, device="cuda")
+    ab = torch.empty(2, dtype=torch.float64, device="cuda")
+    _check(ctx.lib.fs_demodulate(ctx.handle, seg.handle, float(alpha), float(delta), _ptr(ya), _ptr(yb), _ptr(ts),
+                                 _ptr(ab), _stream(stream)), "fs_demodulate")
+    return torch.view_as_complex(ya.view(n, 2)), torch.view_as_complex(yb.view(n, 2)), ts, ab
+
+
+def inject(ctx: Context, x: torch.Tensor, dt: float, fl: float, sigma: float, injections, stream=None):
+    """Add simulated signals (fs_inject) to the float64 CUDA tensor x in place."""
+    _need_cuda(x, "x", torch.float64)
+    arr = (_Injection * max(len(injections), 1))()
+    for i, j in enumerate(injections):
+        arr[i] = _Injection(j.f0, j.f1, j.alpha, j.delta, j.psi, j.cos_iota, j.phi0, j.snr)
+    _check(ctx.lib.fs_inject(ctx.handle, _ptr(x), x.numel(), float(dt), float(fl), float(sigma), arr,
+                             len(injections), _stream(stream)), "fs_inject")
+    return x

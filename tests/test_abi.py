@@ -1,0 +1,61 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/*.h declares.  No compute call: this runs without a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        names += re.findall(r"FS_API\s+[\w\s\*]*?\b(fs_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1003_0844_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = _declared_symbols()
+    for must in ("fs_create", "fs_prepare_segment", "fs_search", "fs_sync_status", "fs_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_export():
+    from paper_1003_0844_gb300 import fstat
+    assert sorted(fstat.EXPORTS) == _declared_symbols() or set(_declared_symbols()) <= set(fstat.EXPORTS)
+
+
+def test_strerror_is_host_only(lib):
+    lib.fs_strerror.restype = ctypes.c_char_p
+    assert lib.fs_strerror(0) == b"ok"
+    assert lib.fs_strerror(3) == b"candidate buffer overflow"
+
+
+def test_null_arguments_rejected_without_device(lib):
+    # argument errors are returned before any CUDA call
+    assert lib.fs_create(None, None, 0) == 1
+    assert lib.fs_search(None, None, None, None, 0, None, 0, ctypes.c_float(0), None, ctypes.c_int64(0), None,
+                         ctypes.c_int64(0), None, None) == 1
+
+
+def test_product_path_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_1003_0844_gb300")
+    for f in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
+        src = open(f).read()
+        assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f

@@ -1,0 +1,244 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same
+seeded inputs: each stage (upsampling, injection, per-sky demodulation) and
+the whole search (F on every bin and the candidate list), for FFT shapes that
+span several tiles and a ragged tail, both precisions, and the edge cases."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import fstat as ofs
+from oracle import resample as ors
+from oracle import response as orsp
+from paper_1003_0844_gb300 import workloads as W
+from tests.helpers import F32_TOL, F64_TOL, check_candidates, make_case, max_rel_dF, oracle_F
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fs():
+    if not torch.cuda.is_available():
+        pytest.fail("the GPU tests need a CUDA device")
+    from paper_1003_0844_gb300 import build, fstat
+    build.build()
+    fstat.load_library()
+    return fstat
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _run(fs, wl, det, x, alpha, delta, f1, precision="f32", interp="spline", nbins=None, thr=None,
+         x_dtype=torch.float32, cand_cap=1 << 16):
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, x_dtype), wl.dt, wl.nfft, wl.fl, wl.S0, precision=precision, interp=interp)
+    res = fs.search(ctx, seg, _dev(alpha), _dev(delta), _dev(f1), wl.F_thr if thr is None else thr,
+                    nbins=nbins, cand_cap=cand_cap)
+    status = ctx.sync_status()
+    F = res.F.double().cpu().numpy()
+    cand = res.candidates()
+    ncand = int(res.n_cand.item())
+    seg.close()
+    ctx.close()
+    return F, cand, ncand, status
+
+
+# ------------------------------------------------------------------ stages
+
+@pytest.mark.parametrize("name,xdt", [("tiny", torch.float32), ("small", torch.float64)])
+def test_upsample_matches_oracle(fs, name, xdt):
+    wl, det, x, *_ = make_case(name)
+    x = x.astype(np.float32).astype(np.float64) if xdt == torch.float32 else x
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, xdt), wl.dt, wl.nfft, wl.fl, wl.S0)
+    x2 = seg.upsampled().cpu().numpy()
+    ref = ors.fourier_upsample2(x)
+    assert np.max(np.abs(x2 - ref)) < 1e-11 * np.max(np.abs(x))
+    assert np.array_equal(x2[::2], x)
+
+
+def test_inject_matches_oracle(fs):
+    wl = W.WORKLOADS["small"]
+    det = W.detector_for(wl)
+    injs = W.injections(wl)
+    ctx = fs.Context(det)
+    xg = torch.zeros(wl.n, dtype=torch.float64, device="cuda")
+    fs.inject(ctx, xg, wl.dt, wl.fl, wl.sigma, injs)
+    ref = orsp.inject(wl.n, wl.dt, injs, wl.fl, det, wl.sigma)
+    assert np.max(np.abs(xg.cpu().numpy() - ref)) < 1e-9 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+@pytest.mark.parametrize("interp", ["spline", "nearest"])
+def test_demodulate_matches_oracle(fs, precision, interp):
+    wl, det, x, alpha, delta, _ = make_case("small")
+    x = x.astype(np.float32).astype(np.float64)
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0, precision=precision, interp=interp)
+    oseg = ors.Segment(x, wl.dt)
+    for s in range(len(alpha)):
+        ya, yb, ts, ab = fs.demodulate(ctx, seg, alpha[s], delta[s])
+        ref = ofs.demodulate(oseg, alpha[s], delta[s], 0.0, wl.fl, det, interp=interp)
+        ts = ts.cpu().numpy()
+        ya = ya.cpu().numpy()
+        yb = yb.cpu().numpy()
+        a2, b2 = ab.cpu().numpy()
+        tol_t = 2e-6 if precision == "f32" else 1e-9
+        assert np.max(np.abs(ts - ref.t_src)) < tol_t
+        tol = 2e-5 if precision == "f32" else 1e-9
+        rms = math.sqrt(np.mean(np.abs(ref.ya) ** 2))
+        assert np.max(np.abs(ya - ref.ya)) < tol * rms * 10
+        assert np.max(np.abs(yb - ref.yb)) < tol * rms * 10
+        tol_m = 1e-6 if precision == "f32" else 1e-12
+        assert abs(a2 / ref.a2 - 1) < tol_m and abs(b2 / ref.b2 - 1) < tol_m
+
+
+# ------------------------------------------------------------------ whole search
+
+SHAPES = [
+    # (workload, n, nfft): FFT splits 64x64, 128x64, 128x128, 256x128, 256x256, 512x256
+    ("tiny", None, 1 << 12),
+    ("tiny", None, 1 << 13),
+    ("small", None, 1 << 14),
+    ("small", None, 1 << 15),
+    ("single_fp64", 30011, 1 << 16),
+    ("single_fp64", None, 1 << 17),
+]
+
+
+@pytest.mark.parametrize("name,n,nfft", SHAPES)
+def test_search_f32_matches_oracle(fs, name, n, nfft):
+    nsky, nspin = (3, 2) if nfft <= (1 << 15) else (2, 2)
+    wl, det, x, alpha, delta, f1 = make_case(name, n=n, nfft=nfft, nsky=nsky, nspin=nspin)
+    if name == "single_fp64":
+        f1 = np.array([-1e-9, -7e-9])
+    x32 = x.astype(np.float32).astype(np.float64)
+    F, (cs, cm, cb, cF), ncand, status = _run(fs, wl, det, x32, alpha, delta, f1, thr=15.0)
+    assert status == 0
+    Fref = oracle_F(x32, wl, det, alpha, delta, f1)
+    assert max_rel_dF(F, Fref) < F32_TOL
+    missing, bad = check_candidates(cs, cm, cb, cF, Fref, 15.0, len(f1))
+    assert not missing and not bad
+    assert ncand == len(cs)
+    assert np.all(np.abs(cF - F[cs * len(f1) + cm, cb]) == 0.0)
+
+
+@pytest.mark.parametrize("name", ["tiny", "small"])
+def test_search_f64_matches_oracle(fs, name):
+    wl, det, x, alpha, delta, f1 = make_case(name)
+    F, (cs, cm, cb, cF), ncand, status = _run(fs, wl, det, x, alpha, delta, f1, precision="f64",
+                                              x_dtype=torch.float64)
+    assert status == 0
+    Fref = oracle_F(x, wl, det, alpha, delta, f1)
+    assert max_rel_dF(F, Fref) < F64_TOL
+    missing, bad = check_candidates(cs, cm, cb, cF, Fref, wl.F_thr, len(f1), rel=1e-7)
+    assert not missing and not bad
+
+
+def test_search_all_bins_and_nearest(fs):
+    wl, det, x, alpha, delta, f1 = make_case("tiny")
+    x32 = x.astype(np.float32).astype(np.float64)
+    F, *_ = _run(fs, wl, det, x32, alpha, delta, f1, nbins=wl.nfft)
+    Fref = oracle_F(x32, wl, det, alpha, delta, f1, nbins=wl.nfft)
+    assert max_rel_dF(F, Fref) < F32_TOL
+    Fn, *_ = _run(fs, wl, det, x32, alpha, delta, f1, interp="nearest")
+    Fnref = oracle_F(x32, wl, det, alpha, delta, f1, interp="nearest")
+    assert max_rel_dF(Fn, Fnref) < F32_TOL
+
+
+def test_search_full_size_2day_sampled_templates(fs):
+    # the 2-sidereal-day shape (N = 86,164, Nfft = 2^18) in the launch
+    # configuration of the benchmark; a few templates against the oracle's FFT mode
+    wl, det, x, alpha, delta, f1 = make_case("grid_2d", nsky=3, nspin=2)
+    x32 = x.astype(np.float32).astype(np.float64)
+    F, (cs, cm, cb, cF), ncand, status = _run(fs, wl, det, x32, alpha, delta, f1)
+    assert status == 0
+    Fref = oracle_F(x32, wl, det, alpha, delta, f1)
+    assert max_rel_dF(F, Fref) < F32_TOL
+    missing, bad = check_candidates(cs, cm, cb, cF, Fref, wl.F_thr, len(f1))
+    assert not missing and not bad
+
+
+def test_search_is_deterministic(fs):
+    wl, det, x, alpha, delta, f1 = make_case("small")
+    F1, c1, n1, _ = _run(fs, wl, det, x, alpha, delta, f1)
+    F2, c2, n2, _ = _run(fs, wl, det, x, alpha, delta, f1)
+    assert np.array_equal(F1, F2)
+    assert n1 == n2
+    k1 = sorted(zip(c1[0], c1[1], c1[2]))
+    k2 = sorted(zip(c2[0], c2[1], c2[2]))
+    assert k1 == k2
+
+
+# ------------------------------------------------------------------ statistics and signal
+
+def test_noise_only_F_is_chi2_4dof_on_gpu(fs):
+    from scipy.stats import chi2, kstest
+    # six independent noise realizations (templates sharing one realization are correlated)
+    means, thin = [], []
+    for r in range(6):
+        wl, det, x, alpha, delta, f1 = make_case("small", inject=False, seed_stream=100 + r, nsky=2, nspin=1)
+        F, *_ = _run(fs, wl, det, x, alpha[r % 2: r % 2 + 1], delta[r % 2: r % 2 + 1], f1, thr=1e9)
+        nb = F.shape[1]
+        core = F[:, nb // 20: 19 * nb // 20]
+        means.append(core.mean())
+        thin.append(core[:, ::3].ravel())  # bins 3 apart (~2 natural bins): nearly independent
+    # E[F] = 2 up to ~1% lost to samples whose source time leaves the data and to the
+    # spline's variance loss; the statistical sigma of the mean is ~0.4%
+    assert abs(np.mean(means) / 2.0 - 1.0) < 0.025
+    v = np.concatenate(thin)
+    assert kstest(2 * v / (np.mean(means) / 2.0), chi2(4).cdf).pvalue > 1e-4
+
+
+def test_noise_free_injection_peaks_at_injected_bin(fs):
+    wl = W.WORKLOADS["small"]
+    det = W.detector_for(wl)
+    inj = W.injections(wl, on_bin=True)[0]
+    x = orsp.inject(wl.n, wl.dt, [inj], wl.fl, det, wl.sigma)
+    F, *_ = _run(fs, wl, det, x, np.array([inj.alpha]), np.array([inj.delta]), np.array([inj.f1]), thr=1e9)
+    k0 = int(round(inj.f0 * wl.nfft * wl.dt))
+    assert abs(int(np.argmax(F[0])) - k0) <= 1
+    # F = rho^2/2 up to the resampling approximation and the samples lost at the edges
+    assert abs(F[0].max() / (inj.snr ** 2 / 2) - 1.0) < 0.02
+
+
+# ------------------------------------------------------------------ edge cases and errors
+
+def test_nonfinite_input_is_reported(fs):
+    wl, det, x, alpha, delta, f1 = make_case("tiny")
+    x = x.copy()
+    x[17] = np.nan
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0)
+    assert ctx.sync_status() == 4  # FS_ERR_NONFINITE
+    assert ctx.sync_status() == 0  # cleared after reading
+
+
+def test_candidate_overflow_counts_exactly(fs):
+    wl, det, x, alpha, delta, f1 = make_case("tiny")
+    F, (cs, *_), ncand, status = _run(fs, wl, det, x, alpha, delta, f1, thr=3.0, cand_cap=5)
+    assert status == 3  # FS_ERR_CAPACITY
+    assert ncand == int(np.sum(F > 3.0)) and ncand > 5
+    assert len(cs) == 5
+
+
+def test_argument_errors(fs):
+    wl, det, x, alpha, delta, f1 = make_case("tiny")
+    ctx = fs.Context(det)
+    xd = _dev(x, torch.float32)
+    with pytest.raises(fs.FstatError) as e:
+        fs.Segment(ctx, xd, wl.dt, 3000, wl.fl, wl.S0)  # not a power of two
+    assert e.value.status == 2
+    with pytest.raises(fs.FstatError) as e:
+        fs.Segment(ctx, xd, -1.0, wl.nfft, wl.fl, wl.S0)
+    assert e.value.status == 1
+    with pytest.raises(fs.FstatError) as e:
+        fs.Segment(ctx, xd, wl.dt, 1 << 19, wl.fl, wl.S0)  # FP32 path supports up to 2^18
+    assert e.value.status == 7
+    seg = fs.Segment(ctx, xd, wl.dt, wl.nfft, wl.fl, wl.S0)
+    with pytest.raises(fs.FstatError) as e:
+        fs.search(ctx, seg, _dev(alpha), _dev(delta), _dev(f1), 10.0, nbins=wl.nfft // 4)
+    assert e.value.status == 2

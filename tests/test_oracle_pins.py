@@ -315,14 +315,15 @@ def test_resampled_F_tracks_exact_F_for_noise_free_signal():
 
 
 def test_resampled_F_noise_mean_near_two():
+    # independent noise realizations: templates sharing one realization are correlated
     wl = W.WORKLOADS["small"]
     rng = np.random.default_rng(31)
-    x = rng.standard_normal(wl.n)
-    seg = resample.Segment(x, wl.dt)
     vals = []
-    for al, de in ((0.3, 0.1), (2.0, -0.9), (4.0, 1.1)):
+    for al, de in ((0.3, 0.1), (2.0, -0.9), (4.0, 1.1), (5.2, 0.4), (1.1, -0.3), (3.3, 0.8)):
+        seg = resample.Segment(rng.standard_normal(wl.n), wl.dt)
         F = fstat.fstat(seg, al, de, -2e-9, wl.fl, DET, wl.S0, wl.nfft)
         nb = F.size
-        vals.append(F[nb // 10: 8 * nb // 10])
+        vals.append(F[nb // 20: 19 * nb // 20])
     v = np.concatenate(vals)
-    assert abs(v.mean() / 2.0 - 1.0) < 0.02
+    # E[F] = 2 less ~1% (samples outside the data, spline variance loss); sigma of the mean ~0.4%
+    assert abs(v.mean() / 2.0 - 1.0) < 0.025

@@ -1,4 +1,4 @@
-// FP64 radix-2 Stockham FFT in global memory.
+// FP64 Stockham FFT (radix 4, one radix-2 stage for odd log2 n) in global memory.
 //
 // Used where FP64 is wanted and the transform is off the per-template hot
 // path: the Bluestein transforms of the Fourier x2 upsampler (once per
@@ -18,29 +18,59 @@ __global__ void k_twiddles64(double2 *tw, int64_t n) {
   }
 }
 
-// One Stockham autosort stage: l = n / 2^(t+1), m = 2^t.
-//   y[k + 2 j m]     = x[k + j m] + x[k + j m + l m]
-//   y[k + 2 j m + m] = W_{2l}^j (x[k + j m] - x[k + j m + l m]),  W_{2l}^j = tw[j m]
-__global__ void k_stockham64(const double2 *__restrict__ x, double2 *__restrict__ y,
-                             const double2 *__restrict__ tw, int64_t n, int log2m, int sign, int batch) {
-  int64_t half = n >> 1;
-  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= half * batch) return;
-  int64_t b = gid / half;
-  int64_t idx = gid - b * half;
-  int64_t m = (int64_t)1 << log2m;
-  int64_t j = idx >> log2m;
-  int64_t k = idx & (m - 1);
+// Stockham autosort stages (radix 2 and 4).  With p the product of the
+// radices already applied, thread i < n/R reads u_q = x[i + q n/R], k = i mod p,
+// multiplies u_q by W_{pR}^{q k}, takes the R-point DFT and writes
+// y[(i - k) R + k + q p].  The twiddle table holds W_n^e for e < n/2.
+__device__ inline double2 tw_get(const double2 *tw, int64_t e, int64_t half, int sign) {
+  double2 w = (e < half) ? tw[e] : make_double2(-tw[e - half].x, -tw[e - half].y);
+  if (sign > 0) w.y = -w.y;
+  return w;
+}
+
+__global__ void k_stockham64_r2(const double2 *__restrict__ x, double2 *__restrict__ y,
+                                const double2 *__restrict__ tw, int64_t n, int log2p, int sign, int batch) {
+  const int64_t h = n >> 1;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= h * batch) return;
+  const int64_t b = gid / h, i = gid - b * h;
+  const int64_t p = (int64_t)1 << log2p;
+  const int64_t k = i & (p - 1);
   const double2 *xs = x + b * n;
   double2 *ys = y + b * n;
-  double2 c0 = xs[k + j * m];
-  double2 c1 = xs[k + j * m + half];
-  double2 w = tw[j * m];
-  if (sign > 0) w.y = -w.y;
-  double2 s = make_double2(c0.x + c1.x, c0.y + c1.y);
-  double2 d = make_double2(c0.x - c1.x, c0.y - c1.y);
-  ys[k + 2 * j * m] = s;
-  ys[k + 2 * j * m + m] = cmul(w, d);
+  const double2 u0 = xs[i];
+  const double2 u1 = cmul(xs[i + h], tw_get(tw, k * (n >> (log2p + 1)), h, sign));
+  const int64_t j = (i - k) * 2 + k;
+  ys[j] = make_double2(u0.x + u1.x, u0.y + u1.y);
+  ys[j + p] = make_double2(u0.x - u1.x, u0.y - u1.y);
+}
+
+__global__ void k_stockham64_r4(const double2 *__restrict__ x, double2 *__restrict__ y,
+                                const double2 *__restrict__ tw, int64_t n, int log2p, int sign, int batch) {
+  const int64_t q4 = n >> 2, h = n >> 1;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= q4 * batch) return;
+  const int64_t b = gid / q4, i = gid - b * q4;
+  const int64_t p = (int64_t)1 << log2p;
+  const int64_t k = i & (p - 1);
+  const int64_t st = n >> (log2p + 2);
+  const double2 *xs = x + b * n;
+  double2 *ys = y + b * n;
+  const double2 u0 = xs[i];
+  const double2 u1 = cmul(xs[i + q4], tw_get(tw, k * st, h, sign));
+  const double2 u2 = cmul(xs[i + 2 * q4], tw_get(tw, 2 * k * st, h, sign));
+  const double2 u3 = cmul(xs[i + 3 * q4], tw_get(tw, 3 * k * st, h, sign));
+  const double2 a0 = make_double2(u0.x + u2.x, u0.y + u2.y);
+  const double2 a1 = make_double2(u0.x - u2.x, u0.y - u2.y);
+  const double2 a2 = make_double2(u1.x + u3.x, u1.y + u3.y);
+  const double2 d = make_double2(u1.x - u3.x, u1.y - u3.y);
+  // forward: multiply by -i; inverse: by +i
+  const double2 a3 = (sign < 0) ? make_double2(d.y, -d.x) : make_double2(-d.y, d.x);
+  const int64_t j = (i - k) * 4 + k;
+  ys[j] = make_double2(a0.x + a2.x, a0.y + a2.y);
+  ys[j + p] = make_double2(a1.x + a3.x, a1.y + a3.y);
+  ys[j + 2 * p] = make_double2(a0.x - a2.x, a0.y - a2.y);
+  ys[j + 3 * p] = make_double2(a1.x - a3.x, a1.y - a3.y);
 }
 
 cudaError_t fft64_twiddles(double2 *tw, int64_t n, cudaStream_t st) {
@@ -51,13 +81,20 @@ cudaError_t fft64_twiddles(double2 *tw, int64_t n, cudaStream_t st) {
 
 cudaError_t fft64(double2 *buf, double2 *tmp, const double2 *twiddle, int64_t n, int batch, int sign,
                   cudaStream_t st, int64_t *launches) {
-  int p = 0;
-  while (((int64_t)1 << p) < n) p++;
+  int lg = 0;
+  while (((int64_t)1 << lg) < n) lg++;
   double2 *src = buf, *dst = tmp;
-  int64_t threads = (n / 2) * batch;
-  unsigned blocks = (unsigned)((threads + 255) / 256);
-  for (int t = 0; t < p; t++) {
-    k_stockham64<<<blocks, 256, 0, st>>>(src, dst, twiddle, n, t, sign, batch);
+  int log2p = 0;
+  if (lg & 1) {
+    const int64_t threads = (n / 2) * batch;
+    k_stockham64_r2<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(src, dst, twiddle, n, log2p, sign, batch);
+    (*launches)++;
+    double2 *sw = src; src = dst; dst = sw;
+    log2p = 1;
+  }
+  const int64_t threads4 = (n / 4) * batch;
+  for (; log2p < lg; log2p += 2) {
+    k_stockham64_r4<<<(unsigned)((threads4 + 255) / 256), 256, 0, st>>>(src, dst, twiddle, n, log2p, sign, batch);
     (*launches)++;
     double2 *sw = src; src = dst; dst = sw;
   }

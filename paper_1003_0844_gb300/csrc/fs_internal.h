@@ -21,7 +21,7 @@ struct fs_ctx {
   void *scratch = nullptr;
   // tuning knobs (templates per batch, skies per group)
   int batch_templates = 16;
-  int group_skies = 1;
+  int group_skies = 16;
   // launch accounting and optional event profiling
   int64_t launches = 0;
   bool prof = false;

@@ -172,61 +172,112 @@ fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ P2 spline
-// Thomas recurrences for M_{i-1} + 4 M_i + M_{i+1} = r_i (i = 1..n2-2), M_0 = M_{n2-1} = 0:
+// Thomas recurrences for M_{i-1} + 4 M_i + M_{i+1} = r_i (i = 1..n2-2), M_0 = M_{n2-1} = 0,
+// r_i = 6 (y_{i+1} - 2 y_i + y_{i-1}):
 //   c'_1 = 1/4, c'_i = 1/(4 - c'_{i-1});  d'_1 = r_1 c'_1, d'_i = (r_i - d'_{i-1}) c'_i
 //   M_{n2-2} = d'_{n2-2},  M_i = d'_i - c'_i M_{i+1}
-constexpr int kSplChunk = 128;
-constexpr int kSplWarm = 40;
-constexpr int kSplCExact = 64;  // c'_i follows the recurrence up to here, then stays at its limit
+// c'_i reaches its limit c = 2 - sqrt(3) in double within ~20 steps.  Away
+// from the ends both recurrences are first-order filters with pole -c, so
+//   d'_i = c sum_{k=0}^{K} (-c)^k r_{i-k},   M_i = sum_{k=0}^{K} (-c)^k d'_{i+k}
+// with K = 40 (the dropped tail weighs c^41 ~ 4e-24); these run one point per
+// thread.  The first and last kSplEnd points follow the exact recurrences
+// serially, so the result equals the sequential Thomas solution to rounding.
+constexpr int kSplK = 40;
+constexpr int kSplEnd = 64;
 
-__device__ inline double spline_cprime(int64_t i) {
+__device__ inline double spline_climit() {
   double c = 0.25;
-  int64_t lim = i < kSplCExact ? i : kSplCExact;
-  for (int64_t k = 2; k <= lim; k++) c = 1.0 / (4.0 - c);
+  for (int k = 2; k <= kSplEnd; k++) c = 1.0 / (4.0 - c);
   return c;
 }
 
-__device__ inline double spline_rhs(const double *y, int64_t i) {
-  return 6.0 * (y[i + 1] - 2.0 * y[i] + y[i - 1]);
+__global__ void k_spline_rhs(const double *y, double *r, int64_t n2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= 1 && i <= n2 - 2) r[i] = 6.0 * (y[i + 1] - 2.0 * y[i] + y[i - 1]);
 }
 
-__global__ void k_spline_forward(const double *y, double *dp, int64_t n2) {
-  int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t lo = 1 + h * kSplChunk;
-  int64_t last = n2 - 2;
-  if (lo > last) return;
-  int64_t hi = lo + kSplChunk - 1;
-  if (hi > last) hi = last;
-  int64_t i0 = lo - kSplWarm;
-  if (i0 < 1) i0 = 1;
-  const double cinf = spline_cprime(kSplCExact);
-  double d = 0.0;  // d'_{i0-1}: exact (no term) at the true start, a warm-up guess otherwise
-  for (int64_t i = i0; i <= hi; i++) {
-    double c = (i < kSplCExact) ? spline_cprime(i) : cinf;
-    d = (spline_rhs(y, i) - d) * c;
-    if (i >= lo) dp[i] = d;
+// d'_i for i in [1, n2-2]; thread 0 runs the exact head [1, kSplEnd) serially.
+__global__ void k_spline_forward(const double *r, double *dp, int64_t n2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t last = n2 - 2;
+  if (i == 0) {
+    double c = 0.25, d = 0.0;
+    const int64_t h = last < kSplEnd - 1 ? last : kSplEnd - 1;
+    for (int64_t k = 1; k <= h; k++) {
+      if (k > 1) c = 1.0 / (4.0 - c);
+      d = (r[k] - d) * c;
+      dp[k] = d;
+    }
+    return;
   }
+  if (i < kSplEnd || i > last) return;
+  const double c = spline_climit();
+  double acc = 0.0, w = c;
+  for (int k = 0; k <= kSplK; k++) {
+    acc = fma(w, r[i - k], acc);
+    w *= -c;
+  }
+  dp[i] = acc;
 }
 
-// Back substitution over one chunk, started kSplWarm points beyond its end from
-// M = 0 (exact at the true end); reads the complete d' array of the forward pass.
+// M_i for i in [1, n2-2]; thread 0 runs the exact tail from n2-2 down, thread 1
+// the exact head from kSplEnd down to 1 (starting from the truncated-sum M_kSplEnd).
 __global__ void k_spline_backward(const double *dp, double *Mout, int64_t n2) {
-  int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t lo = 1 + h * kSplChunk;
-  int64_t last = n2 - 2;
-  if (lo > last) return;
-  int64_t hi = lo + kSplChunk - 1;
-  if (hi > last) hi = last;
-  int64_t i1 = hi + kSplWarm;
-  if (i1 > last) i1 = last;
-  const double cinf = spline_cprime(kSplCExact);
-  double Mnext = 0.0;  // M_{i1+1}
-  for (int64_t i = i1; i >= lo; i--) {
-    double c = (i < kSplCExact) ? spline_cprime(i) : cinf;
-    double m = dp[i] - c * Mnext;
-    if (i <= hi) Mout[i] = m;
-    Mnext = m;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t last = n2 - 2;
+  const double c = spline_climit();
+  if (i == 0) {
+    double m = 0.0;
+    const int64_t lo = last - kSplEnd + 1 > kSplEnd ? last - kSplEnd + 1 : kSplEnd;
+    for (int64_t k = last; k >= lo; k--) {
+      m = dp[k] - c * m;
+      Mout[k] = m;
+    }
+    return;
   }
+  if (i == 1) {
+    double m = 0.0, w = 1.0;
+    for (int k = 0; k <= kSplK; k++) {
+      m = fma(w, dp[kSplEnd + k], m);
+      w *= -c;
+    }
+    double cp[kSplEnd];
+    cp[1] = 0.25;
+    for (int k = 2; k < kSplEnd; k++) cp[k] = 1.0 / (4.0 - cp[k - 1]);
+    for (int k = kSplEnd - 1; k >= 1; k--) {
+      m = dp[k] - cp[k] * m;
+      Mout[k] = m;
+    }
+    return;
+  }
+  if (i < kSplEnd || i > last - kSplEnd) return;
+  double acc = 0.0, w = 1.0;
+  for (int k = 0; k <= kSplK; k++) {
+    acc = fma(w, dp[i + k], acc);
+    w *= -c;
+  }
+  Mout[i] = acc;
+}
+
+// Short series: the sequential Thomas algorithm in one thread.
+__global__ void k_spline_serial(const double *y, double *dp, double *Mout, int64_t n2) {
+  const int64_t last = n2 - 2;
+  double c = 0.25, d = 0.0;
+  for (int64_t k = 1; k <= last; k++) {
+    if (k > 1) c = 1.0 / (4.0 - c);
+    d = (6.0 * (y[k + 1] - 2.0 * y[k] + y[k - 1]) - d) * c;
+    dp[k] = d;
+  }
+  double m = 0.0;
+  c = 0.25;
+  // recompute c'_k on the way back (stored values would need another array)
+  for (int64_t k = last; k >= 1; k--) {
+    double ck = 0.25;
+    for (int64_t q = 2; q <= (k < kSplEnd ? k : kSplEnd); q++) ck = 1.0 / (4.0 - ck);
+    m = dp[k] - ck * m;
+    Mout[k] = m;
+  }
+  (void)c;
 }
 
 // coef[i] for u = i + f, f in [0,1):
@@ -258,16 +309,20 @@ __global__ void k_spline_coef<dcoef4>(const double *y, const double *Msd, dcoef4
 
 fs_status prepare_spline(fs_seg *seg, cudaStream_t st) {
   int64_t n2 = 2 * seg->g.n;
-  size_t need = sizeof(double) * 2 * (size_t)n2;
+  size_t need = sizeof(double) * 3 * (size_t)n2;
   fs_status s = ensure_buffer(&seg->ctx->scratch, &seg->ctx->scratch_bytes, need, st);
   if (s != FS_OK) return s;
-  double *dp = (double *)seg->ctx->scratch;
+  double *r = (double *)seg->ctx->scratch;
+  double *dp = r + n2;
   double *Msd = dp + n2;
-  int64_t chunks = (n2 - 2 + kSplChunk - 1) / kSplChunk;
-  seg->ctx->launches += (chunks > 0 ? 3 : 1);
-  if (chunks > 0) {
-    k_spline_forward<<<nblk(chunks, 128), 128, 0, st>>>(seg->x2, dp, n2);
-    k_spline_backward<<<nblk(chunks, 128), 128, 0, st>>>(dp, Msd, n2);
+  if (n2 - 2 < 4 * kSplEnd) {
+    k_spline_serial<<<1, 1, 0, st>>>(seg->x2, dp, Msd, n2);
+    seg->ctx->launches += 2;
+  } else {
+    k_spline_rhs<<<nblk(n2), 256, 0, st>>>(seg->x2, r, n2);
+    k_spline_forward<<<nblk(n2), 256, 0, st>>>(r, dp, n2);
+    k_spline_backward<<<nblk(n2), 256, 0, st>>>(dp, Msd, n2);
+    seg->ctx->launches += 4;
   }
   if (seg->d.precision == FS_PREC_F32)
     k_spline_coef<float4><<<nblk(n2), 256, 0, st>>>(seg->x2, Msd, (float4 *)seg->coef, n2);

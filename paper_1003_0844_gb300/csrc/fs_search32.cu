@@ -213,20 +213,24 @@ struct Pass1Args {
   float2 *Z;  // [batch][2][N1][N2]
 };
 
-template <int P, int Q>
-__global__ void __launch_bounds__(32 * P, 1) k_pass1(Pass1Args A) {
+// CW columns per CTA; a warp holds CW columns x 2 signals x TPW sub-DFT threads.
+template <int P, int Q, int CW>
+__global__ void __launch_bounds__(32 * P * 2 * CW / 32, 2) k_pass1(Pass1Args A) {
   constexpr int L = P * Q;
   constexpr int S = Q / P;
+  constexpr int CS = 2 * CW;     // (column, signal) pairs
+  constexpr int TPW = 32 / CS;   // sub-DFT threads per warp
   extern __shared__ float2 smem[];
-  float2 *xch = smem;           // [Q][P][32]
-  float2 *twL = smem + L * 32;  // W_L^q
-  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
-  const int col = lane & 15, sig = lane >> 4;
-  const int tiles = A.N2 >> 4;
+  float2 *xch = smem;           // [Q][P][CS]
+  float2 *twL = smem + L * CS;  // W_L^q
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cs = lane % CS, col = cs % CW, sig = cs / CW;
+  const int t = w * TPW + lane / CS;
+  const int tiles = A.N2 / CW;
   const int bt = blockIdx.x / tiles, tile = blockIdx.x - bt * tiles;
   const int tm = A.tmpl0 + bt;
   const int sky = tm / A.nspin, spin = tm - sky * A.nspin;
-  const int n2 = tile * 16 + col;
+  const int n2 = tile * CW + col;
   for (int q = threadIdx.x; q < L; q += blockDim.x) twL[q] = expm2pi((float)q * (1.0f / L));
   const float2 *y = (sig ? A.yb : A.ya) + sky * A.sky_stride;
   const float2 *qq = A.qq + sky * A.sky_stride;
@@ -236,24 +240,30 @@ __global__ void __launch_bounds__(32 * P, 1) k_pass1(Pass1Args A) {
 
   float2 v[Q];
   // load y_j and the chirp exp(-2 pi i f1 Q_j); the two signal lanes of a
-  // column share the chirp: each computes every other one and swaps.
+  // column share the chirp: each computes every other one and swaps.  All
+  // loads of a b-slot are issued before any of them is used.
   sfor<0, S>([&](auto s) {
     const int b = t + P * s;
+    float2 qv[P / 2];
+    sfor<0, P / 2>([&](auto ap) {
+      const int my = Q * (2 * ap + sig) + b;
+      qv[ap] = (my < n1max) ? qq[my * N2 + n2] : make_float2(0.f, 0.f);
+    });
+    sfor<0, P>([&](auto a) {
+      const int na = Q * a + b;
+      v[s * P + a] = (na < n1max) ? y[na * N2 + n2] : make_float2(0.f, 0.f);
+    });
     sfor<0, P / 2>([&](auto ap) {
       constexpr int a0 = 2 * ap, a1 = 2 * ap + 1;
       const int my = Q * (a0 + sig) + b;
       float2 cm = make_float2(0.f, 0.f);
-      if (my < n1max) {
-        const float2 qv = qq[my * N2 + n2];
-        cm = expm2pi(df_mul_frac(f1, df32{qv.x, qv.y}));
-      }
+      if (my < n1max) cm = expm2pi(df_mul_frac(f1, df32{qv[ap].x, qv[ap].y}));
       float2 cp;
-      cp.x = __shfl_xor_sync(kFull, cm.x, 16);
-      cp.y = __shfl_xor_sync(kFull, cm.y, 16);
+      cp.x = __shfl_xor_sync(kFull, cm.x, CW);
+      cp.y = __shfl_xor_sync(kFull, cm.y, CW);
       const float2 c0 = sig ? cp : cm, c1 = sig ? cm : cp;
-      const int na = Q * a0 + b, nb = Q * a1 + b;
-      v[s * P + a0] = (na < n1max) ? cmul(y[na * N2 + n2], c0) : make_float2(0.f, 0.f);
-      v[s * P + a1] = (nb < n1max) ? cmul(y[nb * N2 + n2], c1) : make_float2(0.f, 0.f);
+      v[s * P + a0] = cmul(v[s * P + a0], c0);
+      v[s * P + a1] = cmul(v[s * P + a1], c1);
     });
   });
   __syncthreads();  // twL ready
@@ -261,23 +271,23 @@ __global__ void __launch_bounds__(32 * P, 1) k_pass1(Pass1Args A) {
     const int b = t + P * s;
     dft_inplace<P>(v + s * P);
     sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twL[(b * c) & (L - 1)]); });
-    sfor<0, P>([&](auto c) { xch[(b * P + c) * 32 + lane] = v[s * P + c]; });
+    sfor<0, P>([&](auto c) { xch[(b * P + c) * CS + cs] = v[s * P + c]; });
   });
   __syncthreads();
-  sfor<0, Q>([&](auto bb) { v[bb] = xch[(bb * P + t) * 32 + lane]; });
+  sfor<0, Q>([&](auto bb) { v[bb] = xch[(bb * P + t) * CS + cs]; });
   dft_inplace<Q>(v);  // v[d] = X[k1 = t + P d] of column n2
   // inter-pass twiddle exp(-2 pi i n2 k1 / Nfft): exact anchors every 16 d, recurrence between
   const int64_t nf = A.nfft;
   const float inv_nf = 1.0f / (float)nf;
   const float2 step = expm2pi((float)(((int64_t)n2 * P) & (nf - 1)) * inv_nf);
-  float2 w = make_float2(1.f, 0.f);
+  float2 wt = make_float2(1.f, 0.f);
   sfor<0, Q>([&](auto d) {
     if constexpr (d % 16 == 0) {
-      w = expm2pi((float)(((int64_t)n2 * (t + P * d)) & (nf - 1)) * inv_nf);
+      wt = expm2pi((float)(((int64_t)n2 * (t + P * d)) & (nf - 1)) * inv_nf);
     } else {
-      w = cmul(w, step);
+      wt = cmul(wt, step);
     }
-    v[d] = cmul(v[d], w);
+    v[d] = cmul(v[d], wt);
   });
   float2 *Zs = A.Z + ((int64_t)bt * 2 + sig) * nf;
   sfor<0, Q>([&](auto d) { Zs[(int64_t)(t + P * d) * N2 + n2] = v[d]; });
@@ -301,7 +311,7 @@ struct Pass2Args {
 };
 
 template <int P, int Q, int WARPS, bool FULLBINS>
-__global__ void __launch_bounds__(32 * WARPS, 1) k_pass2(Pass2Args A) {
+__global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
   constexpr int L = P * Q, T = P, G = 16 / T, R = WARPS * G, S = Q / P;
   constexpr int D = FULLBINS ? Q : Q / 2;  // d values with k2 = t + P d in the output band
   constexpr int XW = P * (Q + 1);          // exchange floats2 per sub-DFT
@@ -325,7 +335,15 @@ __global__ void __launch_bounds__(32 * WARPS, 1) k_pass2(Pass2Args A) {
   sfor<0, S>([&](auto s) {
     const int b = t + P * s;
     dft_inplace<P>(v + s * P);
-    sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twL[(b * c) & (L - 1)]); });
+    // W_L^{b c}, c < P, as powers of W_L^b (lanes read consecutive entries: no
+    // bank conflicts); a balanced product tree keeps the rounding depth at log2 P
+    float2 pw[P];
+    pw[1] = twL[b];
+    sfor<2, P>([&](auto c) {
+      if constexpr (c % 2 == 0) pw[c] = cmul(pw[c / 2], pw[c / 2]);
+      else pw[c] = cmul(pw[c - 1], pw[1]);
+    });
+    sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], pw[c]); });
     sfor<0, P>([&](auto c) { xw[c * (Q + 1) + b] = v[s * P + c]; });
   });
   __syncwarp();
@@ -388,10 +406,11 @@ static bool fft_shape(int64_t nfft, FftShape *s) {
   return true;
 }
 
-constexpr int kPass2Warps = 16;
+constexpr int kPass1Cols = 8;   // columns per pass-1 CTA
+constexpr int kPass2Warps = 8;  // rows (warps) per pass-2 CTA for 16-thread sub-DFTs
 
 template <int P, int Q>
-static size_t pass1_smem() { return sizeof(float2) * ((size_t)P * Q * 32 + (size_t)P * Q); }
+static size_t pass1_smem() { return sizeof(float2) * ((size_t)P * Q * 2 * kPass1Cols + (size_t)P * Q); }
 template <int P, int Q, bool FULL>
 static size_t pass2_smem() {
   constexpr int G = 16 / P, R = kPass2Warps * G, D = FULL ? Q : Q / 2;
@@ -402,9 +421,11 @@ static size_t pass2_smem() {
 template <int P, int Q>
 static cudaError_t launch_pass1(const Pass1Args &a, int nb, cudaStream_t st) {
   size_t sm = pass1_smem<P, Q>();
-  cudaError_t e = cudaFuncSetAttribute(k_pass1<P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  constexpr int CW = kPass1Cols;
+  auto kern = k_pass1<P, Q, CW>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_pass1<P, Q><<<nb * (a.N2 / 16), 32 * P, sm, st>>>(a);
+  kern<<<nb * (a.N2 / CW), P * 2 * CW, sm, st>>>(a);
   return cudaGetLastError();
 }
 template <int P, int Q, bool FULL>
@@ -453,12 +474,12 @@ struct Ws32 {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static fs_status workspace32(fs_ctx *ctx, const fs_seg *seg, int G, int B, int64_t npad, cudaStream_t st,
-                             Ws32 *w) {
+static fs_status workspace32(fs_ctx *ctx, const fs_seg *seg, int G, int B, int64_t npad, int nsky,
+                             cudaStream_t st, Ws32 *w) {
   int64_t stride = (npad + 63) & ~(int64_t)63;
   int nblk = (int)((npad + 255) / 256);
   size_t off = 0;
-  size_t o_sky = off; off = align256(off + sizeof(SkyConst32) * G);
+  size_t o_sky = off; off = align256(off + sizeof(SkyConst32) * (nsky > G ? nsky : G));
   size_t o_ya = off; off = align256(off + sizeof(float2) * stride * G);
   size_t o_yb = off; off = align256(off + sizeof(float2) * stride * G);
   size_t o_qq = off; off = align256(off + sizeof(float2) * stride * G);
@@ -523,17 +544,19 @@ fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
   const int G = ctx->group_skies < nsky ? ctx->group_skies : nsky;
   const int B = ctx->batch_templates;
   Ws32 w;
-  fs_status s = workspace32(ctx, seg, G, B, npad, st, &w);
+  fs_status s = workspace32(ctx, seg, G, B, npad, nsky, st, &w);
   if (s != FS_OK) return s;
   if (cudaMemsetAsync(ncand, 0, sizeof(int64_t), st) != cudaSuccess) return FS_ERR_CUDA;
   const bool full = (nbins == seg->g.nfft);
   DemodArgs DA = demod_args(seg, w, npad);
+  {
+    ProfScope ps(ctx, PROF_OTHER, st);
+    if (sky_constants32(alpha, delta, nsky, seg->g, ctx->det, w.skyc, st) != cudaSuccess) return FS_ERR_CUDA;
+    ctx->launches += 1;
+  }
   for (int g0 = 0; g0 < nsky; g0 += G) {
     const int gs = (nsky - g0) < G ? (nsky - g0) : G;
-    {
-      ProfScope ps(ctx, PROF_OTHER, st);
-      if (sky_constants32(alpha + g0, delta + g0, gs, seg->g, ctx->det, w.skyc, st) != cudaSuccess) return FS_ERR_CUDA;
-    }
+    DA.sky = w.skyc + g0;
     {
       ProfScope ps(ctx, PROF_DEMOD, st);
       if (launch_demod(DA, gs, w.nblk_a1, seg->d.interp, st) != cudaSuccess) return FS_ERR_CUDA;
@@ -542,7 +565,7 @@ fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
       ProfScope ps(ctx, PROF_OTHER, st);
       k_demod_finalize<<<gs, 256, 0, st>>>(w.partial, w.nblk_a1, n, seg->g.dt, seg->g.S0, w.norm, w.ab2);
     }
-    ctx->launches += 3;
+    ctx->launches += 2;
     const int ntm = gs * nspin;
     for (int b0 = 0; b0 < ntm; b0 += B) {
       const int nb = (ntm - b0) < B ? (ntm - b0) : B;
@@ -602,7 +625,7 @@ fs_status demod32_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, do
                         double *tsrc, double *ab2, cudaStream_t st) {
   const int64_t n = seg->g.n;
   Ws32 w;
-  fs_status s = workspace32(ctx, seg, 1, 1, n, st, &w);
+  fs_status s = workspace32(ctx, seg, 1, 1, n, 1, st, &w);
   if (s != FS_OK) return s;
   // alpha/delta are host values: stage them through the partial buffer's tail is not
   // possible before allocation, so use a small device copy.

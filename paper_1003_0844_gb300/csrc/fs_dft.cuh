@@ -73,17 +73,25 @@ constexpr int cx_bitrev(int i, int bits) {
 
 // In-place DFT of v[0..N) (N = 2..32), natural order in and out: radix-2
 // decimation in frequency, then a compile-time bit-reversal (register renaming).
-template <int N>
+// NZ: the inputs v[NZ..N) are known to be zero (NZ = N or N/2); with NZ = N/2
+// the first stage reduces to copies and twiddle products.
+template <int N, int NZ = N>
 __device__ __forceinline__ void dft_inplace(float2 *v) {
+  static_assert(NZ == N || 2 * NZ == N, "pruning supports a zero upper half only");
   constexpr int LG = cx_log2(N);
   sfor<0, LG>([&](auto st) {
     constexpr int span = N >> (st + 1);
     sfor<0, N / (2 * span)>([&](auto g) {
       sfor<0, span>([&](auto k) {
         constexpr int i0 = g * 2 * span + k;
-        float2 a = v[i0], b = v[i0 + span];
-        v[i0] = cadd(a, b);
-        v[i0 + span] = twmul<2 * span, k>(csub(a, b));
+        if constexpr (st == 0 && NZ < N) {
+          const float2 a = v[i0];
+          v[i0 + span] = twmul<2 * span, k>(a);
+        } else {
+          float2 a = v[i0], b = v[i0 + span];
+          v[i0] = cadd(a, b);
+          v[i0 + span] = twmul<2 * span, k>(csub(a, b));
+        }
       });
     });
   });

@@ -214,7 +214,16 @@ struct Pass1Args {
 };
 
 // CW columns per CTA; a warp holds CW columns x 2 signals x TPW sub-DFT threads.
-template <int P, int Q, int CW>
+// AM: rows n1 = Q a + b with a >= AM are zero for every column (AM = P when the
+// data may fill the column, P/2 when n1max <= L/2, i.e. N <= Nfft/2).
+__device__ __forceinline__ float2 chirp_cycles(float f) {
+  // exp(-2 pi i f), |f| <= 1/2: hardware sine/cosine (absolute error < 1e-6 on [-pi, pi])
+  float s, c;
+  __sincosf(6.283185307179586f * f, &s, &c);
+  return make_float2(c, -s);
+}
+
+template <int P, int Q, int CW, int AM>
 __global__ void __launch_bounds__(32 * P * 2 * CW / 32, 2) k_pass1(Pass1Args A) {
   constexpr int L = P * Q;
   constexpr int S = Q / P;
@@ -244,20 +253,21 @@ __global__ void __launch_bounds__(32 * P * 2 * CW / 32, 2) k_pass1(Pass1Args A) 
   // loads of a b-slot are issued before any of them is used.
   sfor<0, S>([&](auto s) {
     const int b = t + P * s;
-    float2 qv[P / 2];
-    sfor<0, P / 2>([&](auto ap) {
+    float2 qv[AM / 2];
+    sfor<0, AM / 2>([&](auto ap) {
       const int my = Q * (2 * ap + sig) + b;
       qv[ap] = (my < n1max) ? qq[my * N2 + n2] : make_float2(0.f, 0.f);
     });
     sfor<0, P>([&](auto a) {
       const int na = Q * a + b;
-      v[s * P + a] = (na < n1max) ? y[na * N2 + n2] : make_float2(0.f, 0.f);
+      if constexpr (a < AM) v[s * P + a] = (na < n1max) ? y[na * N2 + n2] : make_float2(0.f, 0.f);
+      else v[s * P + a] = make_float2(0.f, 0.f);
     });
-    sfor<0, P / 2>([&](auto ap) {
+    sfor<0, AM / 2>([&](auto ap) {
       constexpr int a0 = 2 * ap, a1 = 2 * ap + 1;
       const int my = Q * (a0 + sig) + b;
       float2 cm = make_float2(0.f, 0.f);
-      if (my < n1max) cm = expm2pi(df_mul_frac(f1, df32{qv[ap].x, qv[ap].y}));
+      if (my < n1max) cm = chirp_cycles(df_mul_frac(f1, df32{qv[ap].x, qv[ap].y}));
       float2 cp;
       cp.x = __shfl_xor_sync(kFull, cm.x, CW);
       cp.y = __shfl_xor_sync(kFull, cm.y, CW);
@@ -269,7 +279,7 @@ __global__ void __launch_bounds__(32 * P * 2 * CW / 32, 2) k_pass1(Pass1Args A) 
   __syncthreads();  // twL ready
   sfor<0, S>([&](auto s) {
     const int b = t + P * s;
-    dft_inplace<P>(v + s * P);
+    dft_inplace<P, AM>(v + s * P);
     sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twL[(b * c) & (L - 1)]); });
     sfor<0, P>([&](auto c) { xch[(b * P + c) * CS + cs] = v[s * P + c]; });
   });
@@ -316,8 +326,8 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
   constexpr int D = FULLBINS ? Q : Q / 2;  // d values with k2 = t + P d in the output band
   constexpr int XW = P * (Q + 1);          // exchange floats2 per sub-DFT
   extern __shared__ float2 smem[];
-  float2 *twL = smem + WARPS * 2 * G * XW;
-  float *Fs = (float *)(twL + L);  // [D*P][R+1]
+  float2 *twM = smem + WARPS * 2 * G * XW;  // twM[c * Q + b] = W_L^{b c}
+  float *Fs = (float *)(twM + L);            // [D*P][R+1]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int t = lane % T, sig = (lane / T) & 1, gr = lane / (2 * T);
   const int row = w * G + gr;
@@ -326,24 +336,20 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
   const int k1 = rt * R + row;
   const int tm = A.tmpl0 + bt;
   const int sky = tm / A.nspin, spin = tm - sky * A.nspin;
-  for (int q = threadIdx.x; q < L; q += blockDim.x) twL[q] = expm2pi((float)q * (1.0f / L));
+  for (int q = threadIdx.x; q < L; q += blockDim.x) {
+    const int c = q / Q, b = q - c * Q;
+    twM[q] = expm2pi((float)((b * c) & (L - 1)) * (1.0f / L));
+  }
   const float2 *z = A.Z + ((int64_t)bt * 2 + sig) * A.nfft + (int64_t)k1 * A.N2;
   float2 v[Q];
   sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = z[Q * a + t + P * s]; }); });
-  __syncthreads();  // twL ready
+  __syncthreads();  // twM ready
   float2 *xw = smem + (w * 2 * G + (sig + 2 * gr)) * XW;
   sfor<0, S>([&](auto s) {
     const int b = t + P * s;
     dft_inplace<P>(v + s * P);
-    // W_L^{b c}, c < P, as powers of W_L^b (lanes read consecutive entries: no
-    // bank conflicts); a balanced product tree keeps the rounding depth at log2 P
-    float2 pw[P];
-    pw[1] = twL[b];
-    sfor<2, P>([&](auto c) {
-      if constexpr (c % 2 == 0) pw[c] = cmul(pw[c / 2], pw[c / 2]);
-      else pw[c] = cmul(pw[c - 1], pw[1]);
-    });
-    sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], pw[c]); });
+    // W_L^{b c} stored by c then b: lanes read consecutive entries (no bank conflicts)
+    sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twM[c * Q + b]); });
     sfor<0, P>([&](auto c) { xw[c * (Q + 1) + b] = v[s * P + c]; });
   });
   __syncwarp();
@@ -422,7 +428,7 @@ template <int P, int Q>
 static cudaError_t launch_pass1(const Pass1Args &a, int nb, cudaStream_t st) {
   size_t sm = pass1_smem<P, Q>();
   constexpr int CW = kPass1Cols;
-  auto kern = k_pass1<P, Q, CW>;
+  auto kern = (a.n1max <= P * Q / 2) ? k_pass1<P, Q, CW, P / 2> : k_pass1<P, Q, CW, P>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   kern<<<nb * (a.N2 / CW), P * 2 * CW, sm, st>>>(a);

@@ -200,7 +200,7 @@ def test_noise_only_F_is_chi2_4dof_on_gpu(fs):
         core = F[0, nb // 20: 19 * nb // 20]
         w = _kept_weight(x, wl, det, al[0], de[0], f1[0], "nearest")
         ratios.append(core.mean() / (2.0 * w))
-        shapes.append(2.0 * core[::3] / core.mean())  # bins 3 apart (~2 natural bins)
+        shapes.append(4.0 * core[::3] / core.mean())  # 2F normalised to mean 4; bins 3 apart
     ratios = np.array(ratios)
     sem = ratios.std(ddof=1) / math.sqrt(len(ratios))
     assert abs(ratios.mean() - 1.0) < max(4 * sem, 0.005) and abs(ratios.mean() - 1.0) < 0.03

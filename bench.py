@@ -227,27 +227,33 @@ def main():
     value = ntempl * world / (ms_per_step / 1e3)
 
     # dominant kernel and its roofline: FFT flops 5 Nfft log2(Nfft) per complex transform,
-    # two transforms (a, b) per template, split between the passes by log2 N1 : log2 N2
+    # two transforms (a, b) per template.  In the persistent mode one launch per sky
+    # group runs both passes (kind "pass2" then covers the whole transform); in the
+    # per-batch mode the flops split between the passes by log2 N1 : log2 N2.
     p = int(round(math.log2(wl.nfft)))
     lg1, lg2 = (p + 1) // 2, p // 2
     kinds = {k: (stats["ms"][k], stats["count"][k]) for k in ("prepare", "demodulate", "pass1", "pass2")}
+    fused = kinds["pass1"][1] == 0
+    names = {"pass1": "k_pass1", "pass2": "k_passes (both passes, persistent)" if fused else "k_pass2",
+             "demodulate": "k_demod32", "prepare": "segment preparation"}
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_n = kinds[dom]
-    tmpl_per_launch = {"pass1": ntempl * args.steps / max(kinds["pass1"][1], 1),
-                       "pass2": ntempl * args.steps / max(kinds["pass2"][1], 1)}
-    flops_tmpl = {"pass1": 2 * 5 * wl.nfft * lg1, "pass2": 2 * 5 * wl.nfft * lg2}
+    flops_tmpl = {"pass1": 2 * 5 * wl.nfft * lg1, "pass2": 2 * 5 * wl.nfft * (p if fused else lg2)}
     roof = None
     if dom in flops_tmpl and dom_n:
         per_launch_ms = dom_ms / dom_n
-        achieved = flops_tmpl[dom] * tmpl_per_launch[dom] / (per_launch_ms / 1e3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+        tpl = ntempl * args.steps / dom_n
+        achieved = flops_tmpl[dom] * tpl / (per_launch_ms / 1e3) / 1e12
+        roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                 "peak_kind": "FP32 CUDA-core peak from unit counts and max clock (152 SM x 128 x 2 x 2070 MHz)",
-                "per_launch_ms": per_launch_ms, "templates_per_launch": tmpl_per_launch[dom]}
+                "flop_convention": "5 Nfft log2 Nfft per complex FFT, 2 FFTs per template",
+                "per_launch_ms": per_launch_ms, "templates_per_launch": tpl}
     hbm_gbs, hbm_kind = _peaks()
     # whole-path HBM view: algorithmic bytes = F written (4 B per bin) per template
     hbm_alg = ntempl * nbins * 4 / (ms_per_step / 1e3) / 1e9
-    shares = {k: round(v[0] / max(sum(x[0] for x in kinds.values()), 1e-9), 4) for k, v in kinds.items()}
+    shares = {names[k]: round(v[0] / max(sum(x[0] for x in kinds.values()), 1e-9), 4)
+              for k, v in kinds.items() if v[1]}
 
     line = {
         "metric": METRIC, "value": value, "unit": "templates/s", "n_gpus": world, "steps": args.steps,

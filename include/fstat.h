@@ -159,8 +159,9 @@ FS_API fs_status fs_sync_status(fs_ctx *ctx, void *stream);
  * events on its stream; ms[k] / count[k] are their summed durations and
  * launch counts (read after the work completes; fs_get_stats synchronises
  * the device).  Kinds: 0 segment preparation (all of it), 1 per-sky
- * demodulation, 2 transform pass 1, 3 transform pass 2 + F epilogue,
- * 4 other. */
+ * demodulation, 2 transform pass 1 (per-batch launches), 3 transform
+ * pass 2 + F epilogue (per-batch launches) or both passes (the persistent
+ * launch used for nbins = nfft/2), 4 other. */
 #define FS_PROF_KINDS 5
 typedef struct {
   int64_t launches;

@@ -64,6 +64,8 @@ fs_status fs_create(fs_ctx **ctx, const fs_detector *det, int32_t device) {
   if (bt && atoi(bt) > 0) c->batch_templates = atoi(bt);
   const char *gs = getenv("FSTAT_GROUP_SKIES");
   if (gs && atoi(gs) > 0) c->group_skies = atoi(gs);
+  const char *pk = getenv("FSTAT_PERSISTENT");
+  if (pk) c->persistent = atoi(pk) != 0;
   *ctx = c;
   return FS_OK;
 }

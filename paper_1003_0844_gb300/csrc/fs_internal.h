@@ -22,6 +22,7 @@ struct fs_ctx {
   // tuning knobs (templates per batch, skies per group)
   int batch_templates = 16;
   int group_skies = 16;
+  bool persistent = true;  // both transform passes in one persistent launch per sky group
   // launch accounting and optional event profiling
   int64_t launches = 0;
   bool prof = false;

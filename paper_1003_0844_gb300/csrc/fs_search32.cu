@@ -223,24 +223,21 @@ __device__ __forceinline__ float2 chirp_cycles(float f) {
   return make_float2(c, -s);
 }
 
+// One pass-1 work item: template tm (index within the group) and its column
+// tile, writing Z slot zs.  Needs P * 2 * CW threads; xch holds L * 2 * CW
+// float2, twL the table W_L^q (q < L).  The caller synchronises before and after.
 template <int P, int Q, int CW, int AM>
-__global__ void __launch_bounds__(32 * P * 2 * CW / 32, 2) k_pass1(Pass1Args A) {
+__device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, int tile, float2 *xch,
+                                           const float2 *twL) {
   constexpr int L = P * Q;
   constexpr int S = Q / P;
   constexpr int CS = 2 * CW;     // (column, signal) pairs
   constexpr int TPW = 32 / CS;   // sub-DFT threads per warp
-  extern __shared__ float2 smem[];
-  float2 *xch = smem;           // [Q][P][CS]
-  float2 *twL = smem + L * CS;  // W_L^q
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int cs = lane % CS, col = cs % CW, sig = cs / CW;
   const int t = w * TPW + lane / CS;
-  const int tiles = A.N2 / CW;
-  const int bt = blockIdx.x / tiles, tile = blockIdx.x - bt * tiles;
-  const int tm = A.tmpl0 + bt;
   const int sky = tm / A.nspin, spin = tm - sky * A.nspin;
   const int n2 = tile * CW + col;
-  for (int q = threadIdx.x; q < L; q += blockDim.x) twL[q] = expm2pi((float)q * (1.0f / L));
   const float2 *y = (sig ? A.yb : A.ya) + sky * A.sky_stride;
   const float2 *qq = A.qq + sky * A.sky_stride;
   const df32 f1 = df_from_double(A.f1[spin]);
@@ -276,7 +273,6 @@ __global__ void __launch_bounds__(32 * P * 2 * CW / 32, 2) k_pass1(Pass1Args A) 
       v[s * P + a1] = cmul(v[s * P + a1], c1);
     });
   });
-  __syncthreads();  // twL ready
   sfor<0, S>([&](auto s) {
     const int b = t + P * s;
     dft_inplace<P, AM>(v + s * P);
@@ -299,8 +295,21 @@ __global__ void __launch_bounds__(32 * P * 2 * CW / 32, 2) k_pass1(Pass1Args A) 
     }
     v[d] = cmul(v[d], wt);
   });
-  float2 *Zs = A.Z + ((int64_t)bt * 2 + sig) * nf;
+  float2 *Zs = A.Z + ((int64_t)zs * 2 + sig) * nf;
   sfor<0, Q>([&](auto d) { Zs[(int64_t)(t + P * d) * N2 + n2] = v[d]; });
+}
+
+template <int P, int Q, int CW, int AM>
+__global__ void __launch_bounds__(P * 2 * CW, 2) k_pass1(Pass1Args A) {
+  constexpr int L = P * Q;
+  extern __shared__ float2 smem[];
+  float2 *xch = smem;               // [Q][P][2 CW]
+  float2 *twL = smem + L * 2 * CW;  // W_L^q
+  const int tiles = A.N2 / CW;
+  const int bt = blockIdx.x / tiles, tile = blockIdx.x - bt * tiles;
+  for (int q = threadIdx.x; q < L; q += blockDim.x) twL[q] = expm2pi((float)q * (1.0f / L));
+  __syncthreads();
+  pass1_item<P, Q, CW, AM>(A, A.tmpl0 + bt, bt, tile, xch, twL);
 }
 
 // ------------------------------------------------------------------ pass 2 + F epilogue
@@ -320,31 +329,26 @@ struct Pass2Args {
   uint32_t *flags;
 };
 
+// One pass-2 work item: template tm (within the group), row tile rt, reading Z
+// slot zs.  Needs 32 * WARPS threads; work holds the exchange and F tile areas
+// (pass2_work_floats2), twM the matrix W_L^{b c} stored by c then b.  Z is read
+// past L1 (it may have been rewritten since an earlier item on this SM).
 template <int P, int Q, int WARPS, bool FULLBINS>
-__global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
-  constexpr int L = P * Q, T = P, G = 16 / T, R = WARPS * G, S = Q / P;
+__device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
+                                           const float2 *twM) {
+  constexpr int T = P, G = 16 / T, R = WARPS * G, S = Q / P;
   constexpr int D = FULLBINS ? Q : Q / 2;  // d values with k2 = t + P d in the output band
   constexpr int XW = P * (Q + 1);          // exchange floats2 per sub-DFT
-  extern __shared__ float2 smem[];
-  float2 *twM = smem + WARPS * 2 * G * XW;  // twM[c * Q + b] = W_L^{b c}
-  float *Fs = (float *)(twM + L);            // [D*P][R+1]
+  float *Fs = (float *)(work + WARPS * 2 * G * XW);  // [D*P][R+1]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int t = lane % T, sig = (lane / T) & 1, gr = lane / (2 * T);
   const int row = w * G + gr;
-  const int rtiles = A.N1 / R;
-  const int bt = blockIdx.x / rtiles, rt = blockIdx.x - bt * rtiles;
   const int k1 = rt * R + row;
-  const int tm = A.tmpl0 + bt;
   const int sky = tm / A.nspin, spin = tm - sky * A.nspin;
-  for (int q = threadIdx.x; q < L; q += blockDim.x) {
-    const int c = q / Q, b = q - c * Q;
-    twM[q] = expm2pi((float)((b * c) & (L - 1)) * (1.0f / L));
-  }
-  const float2 *z = A.Z + ((int64_t)bt * 2 + sig) * A.nfft + (int64_t)k1 * A.N2;
+  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * A.nfft + (int64_t)k1 * A.N2;
   float2 v[Q];
-  sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = z[Q * a + t + P * s]; }); });
-  __syncthreads();  // twM ready
-  float2 *xw = smem + (w * 2 * G + (sig + 2 * gr)) * XW;
+  sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = __ldcg(z + Q * a + t + P * s); }); });
+  float2 *xw = work + (w * 2 * G + (sig + 2 * gr)) * XW;
   sfor<0, S>([&](auto s) {
     const int b = t + P * s;
     dft_inplace<P>(v + s * P);
@@ -399,6 +403,117 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
   }
 }
 
+template <int P, int Q, int WARPS, bool FULLBINS>
+constexpr size_t pass2_work_floats2() {
+  constexpr int G = 16 / P, R = WARPS * G, D = FULLBINS ? Q : Q / 2;
+  return (size_t)WARPS * 2 * G * P * (Q + 1) + ((size_t)D * P * (R + 1) + 1) / 2;
+}
+
+__device__ __forceinline__ void twiddle_matrix(float2 *twM, int P, int Q) {
+  const int L = P * Q;
+  for (int q = threadIdx.x; q < L; q += blockDim.x) {
+    const int c = q / Q, b = q - c * Q;
+    twM[q] = expm2pi((float)((b * c) & (L - 1)) * (1.0f / L));
+  }
+}
+
+template <int P, int Q, int WARPS, bool FULLBINS>
+__global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
+  constexpr int G = 16 / P, R = WARPS * G;
+  extern __shared__ float2 smem[];
+  float2 *twM = smem;
+  float2 *work = smem + P * Q;
+  const int rtiles = A.N1 / R;
+  const int bt = blockIdx.x / rtiles, rt = blockIdx.x - bt * rtiles;
+  twiddle_matrix(twM, P, Q);
+  __syncthreads();
+  pass2_item<P, Q, WARPS, FULLBINS>(A, A.tmpl0 + bt, bt, rt, work, twM);
+}
+
+// ------------------------------------------------------------------ persistent pass kernel
+// One launch runs both passes for every template of a sky group from a work
+// queue.  Round r holds the pass-1 items of template r and the pass-2 items of
+// template r - lag.  A pass-2 item waits until all pass-1 items of its template
+// have completed; a pass-1 item of template t waits until the pass-2 items of
+// template t - slots (the previous user of its Z slot) have completed.  Items
+// are taken in queue order, so every wait is on earlier items held by running
+// CTAs.  Waits are bounded: on exhaustion the kernel latches ERRF_TIMEOUT and
+// continues (results are then invalid, the device stays responsive).
+struct QueueArgs {
+  int ntm, tiles1, tiles2, lag, slots;
+  unsigned *counter;  // [1 + 2 ntm]: next item, pass-1 done per template, pass-2 done per template
+};
+
+constexpr long kSpinLimit = 20000000;  // ~100 ns per poll: a few seconds at most
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Called by one thread: wait until *p >= target (bounded).
+__device__ inline void wait_at_least(const unsigned *p, unsigned target, uint32_t *flags) {
+  for (long it = 0; ld_acquire(p) < target; it++) {
+    if (it > kSpinLimit) {
+      atomicOr(flags, ERRF_TIMEOUT);
+      return;
+    }
+    __nanosleep(100);
+  }
+}
+
+template <int P1, int Q1, int AM, int P2, int Q2>
+__global__ void __launch_bounds__(256, 2) k_passes(Pass1Args A1, Pass2Args A2, QueueArgs Qa) {
+  constexpr int CW = 256 / (2 * P1);
+  constexpr int L1 = P1 * Q1, L2 = P2 * Q2;
+  extern __shared__ float2 smem[];
+  float2 *twL = smem;            // W_{L1}^q
+  float2 *twM = smem + L1;       // W_{L2}^{b c} by c then b
+  float2 *work = smem + L1 + L2; // union of the pass-1 exchange and the pass-2 work areas
+  __shared__ int s_item;
+  for (int q = threadIdx.x; q < L1; q += blockDim.x) twL[q] = expm2pi((float)q * (1.0f / L1));
+  twiddle_matrix(twM, P2, Q2);
+  unsigned *next = Qa.counter;
+  unsigned *done1 = Qa.counter + 1;
+  unsigned *done2 = Qa.counter + 1 + Qa.ntm;
+  const int ipr = Qa.tiles1 + Qa.tiles2;
+  const int total = (Qa.ntm + Qa.lag) * ipr;
+  for (;;) {
+    __syncthreads();  // previous item finished with shared memory
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(next, 1u);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    const int r = item / ipr, j = item - r * ipr;
+    if (j < Qa.tiles1) {
+      const int tm = r;
+      if (tm >= Qa.ntm) continue;
+      if (threadIdx.x == 0 && tm >= Qa.slots) wait_at_least(done2 + (tm - Qa.slots), Qa.tiles2, A2.flags);
+      __syncthreads();
+      pass1_item<P1, Q1, CW, AM>(A1, tm, tm % Qa.slots, j, work, twL);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        red_release_add(done1 + tm, 1u);
+      }
+    } else {
+      const int tm = r - Qa.lag;
+      if (tm < 0) continue;
+      if (threadIdx.x == 0) wait_at_least(done1 + tm, Qa.tiles1, A2.flags);
+      __syncthreads();
+      pass2_item<P2, Q2, 8, false>(A2, tm, tm % Qa.slots, j - Qa.tiles1, work, twM);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        red_release_add(done2 + tm, 1u);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host orchestration
 struct FftShape {
   int N1, N2;
@@ -419,9 +534,7 @@ template <int P, int Q>
 static size_t pass1_smem() { return sizeof(float2) * ((size_t)P * Q * 2 * kPass1Cols + (size_t)P * Q); }
 template <int P, int Q, bool FULL>
 static size_t pass2_smem() {
-  constexpr int G = 16 / P, R = kPass2Warps * G, D = FULL ? Q : Q / 2;
-  return sizeof(float2) * ((size_t)kPass2Warps * 2 * G * P * (Q + 1) + (size_t)P * Q) +
-         sizeof(float) * (size_t)D * P * (R + 1);
+  return sizeof(float2) * ((size_t)P * Q + pass2_work_floats2<P, Q, kPass2Warps, FULL>());
 }
 
 template <int P, int Q>
@@ -468,12 +581,59 @@ static cudaError_t dispatch_pass2(int N2, bool full, const Pass2Args &a, int nb,
   return cudaErrorInvalidValue;
 }
 
+// Persistent pass kernel: shapes (N1 x N2) -> (P1, Q1, P2, Q2), pruning AM.
+constexpr int kLag = 3;    // rounds between a template's pass-1 and pass-2 items
+constexpr int kSlots = 8;  // Z ring slots
+
+template <int P1, int Q1, int AM, int P2, int Q2>
+static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
+  constexpr int CW = 256 / (2 * P1);
+  constexpr size_t w1 = (size_t)P1 * Q1 * 2 * CW;
+  constexpr size_t w2 = pass2_work_floats2<P2, Q2, 8, false>();
+  const size_t sm = sizeof(float2) * ((size_t)P1 * Q1 + (size_t)P2 * Q2 + (w1 > w2 ? w1 : w2));
+  auto kern = k_passes<P1, Q1, AM, P2, Q2>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, sm);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  const long total = (long)(qa.ntm + qa.lag) * (qa.tiles1 + qa.tiles2);
+  long grid = (long)occ * nsm;
+  if (grid > total) grid = total;
+  kern<<<(unsigned)grid, 256, sm, st>>>(a1, a2, qa);
+  return cudaGetLastError();
+}
+
+template <int P1, int Q1, int P2, int Q2>
+static cudaError_t launch_passes_am(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
+  if (a1.n1max <= P1 * Q1 / 2) return launch_passes_t<P1, Q1, P1 / 2, P2, Q2>(a1, a2, qa, st);
+  return launch_passes_t<P1, Q1, P1, P2, Q2>(a1, a2, qa, st);
+}
+
+static cudaError_t dispatch_passes(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
+                                   cudaStream_t st) {
+  switch (N1 * 4096 + N2) {
+    case 64 * 4096 + 64: return launch_passes_am<8, 8, 8, 8>(a1, a2, qa, st);
+    case 128 * 4096 + 64: return launch_passes_am<8, 16, 8, 8>(a1, a2, qa, st);
+    case 128 * 4096 + 128: return launch_passes_am<8, 16, 8, 16>(a1, a2, qa, st);
+    case 256 * 4096 + 128: return launch_passes_am<16, 16, 8, 16>(a1, a2, qa, st);
+    case 256 * 4096 + 256: return launch_passes_am<16, 16, 16, 16>(a1, a2, qa, st);
+    case 512 * 4096 + 256: return launch_passes_am<16, 32, 16, 16>(a1, a2, qa, st);
+    case 512 * 4096 + 512: return launch_passes_am<16, 32, 16, 32>(a1, a2, qa, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 struct Ws32 {
   SkyConst32 *skyc;
   float2 *ya, *yb, *qq, *norm;
   double2 *ab2;
   double *partial;
   float2 *Z;
+  unsigned *counters;
   int64_t stride;
   int nblk_a1;
 };
@@ -481,7 +641,7 @@ struct Ws32 {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static fs_status workspace32(fs_ctx *ctx, const fs_seg *seg, int G, int B, int64_t npad, int nsky,
-                             cudaStream_t st, Ws32 *w) {
+                             int nspin, cudaStream_t st, Ws32 *w) {
   int64_t stride = (npad + 63) & ~(int64_t)63;
   int nblk = (int)((npad + 255) / 256);
   size_t off = 0;
@@ -492,7 +652,8 @@ static fs_status workspace32(fs_ctx *ctx, const fs_seg *seg, int G, int B, int64
   size_t o_nm = off; off = align256(off + sizeof(float2) * G);
   size_t o_ab = off; off = align256(off + sizeof(double2) * G);
   size_t o_pa = off; off = align256(off + sizeof(double) * 2 * (size_t)nblk * G);
-  size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)seg->g.nfft * B);
+  size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)seg->g.nfft * (B > kSlots ? B : kSlots));
+  size_t o_ct = off; off = align256(off + sizeof(unsigned) * (1 + 2 * (size_t)G * nspin));
   fs_status s = ensure_buffer(&ctx->ws, &ctx->ws_bytes, off, st);
   if (s != FS_OK) return s;
   char *base = (char *)ctx->ws;
@@ -504,6 +665,7 @@ static fs_status workspace32(fs_ctx *ctx, const fs_seg *seg, int G, int B, int64
   w->ab2 = (double2 *)(base + o_ab);
   w->partial = (double *)(base + o_pa);
   w->Z = (float2 *)(base + o_z);
+  w->counters = (unsigned *)(base + o_ct);
   w->stride = stride;
   w->nblk_a1 = nblk;
   return FS_OK;
@@ -550,10 +712,11 @@ fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
   const int G = ctx->group_skies < nsky ? ctx->group_skies : nsky;
   const int B = ctx->batch_templates;
   Ws32 w;
-  fs_status s = workspace32(ctx, seg, G, B, npad, nsky, st, &w);
+  fs_status s = workspace32(ctx, seg, G, B, npad, nsky, nspin, st, &w);
   if (s != FS_OK) return s;
   if (cudaMemsetAsync(ncand, 0, sizeof(int64_t), st) != cudaSuccess) return FS_ERR_CUDA;
   const bool full = (nbins == seg->g.nfft);
+  const bool persistent = !full && ctx->persistent;
   DemodArgs DA = demod_args(seg, w, npad);
   {
     ProfScope ps(ctx, PROF_OTHER, st);
@@ -573,40 +736,57 @@ fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
     }
     ctx->launches += 2;
     const int ntm = gs * nspin;
+    Pass1Args p1{};
+    p1.ya = w.ya;
+    p1.yb = w.yb;
+    p1.qq = w.qq;
+    p1.sky_stride = w.stride;
+    p1.f1 = f1;
+    p1.nspin = nspin;
+    p1.N2 = sh.N2;
+    p1.n1max = n1max;
+    p1.nfft = seg->g.nfft;
+    p1.Z = w.Z;
+    Pass2Args p2{};
+    p2.Z = w.Z;
+    p2.N1 = sh.N1;
+    p2.N2 = sh.N2;
+    p2.nfft = seg->g.nfft;
+    p2.norm = w.norm;
+    p2.nspin = nspin;
+    p2.sky_base = g0;
+    p2.F = F ? F + (int64_t)g0 * nspin * nbins : nullptr;
+    p2.nbins = nbins;
+    p2.thr = thr;
+    p2.cand = cand;
+    p2.cap = cap;
+    p2.ncand = (unsigned long long *)ncand;
+    p2.flags = ctx->d_flags;
+    if (persistent) {
+      QueueArgs qa{};
+      qa.ntm = ntm;
+      qa.tiles1 = sh.N2 / (256 / (2 * (sh.N1 <= 128 ? 8 : 16)));
+      qa.tiles2 = sh.N1 / (8 * (16 / (sh.N2 <= 128 ? 8 : 16)));
+      qa.lag = kLag;
+      qa.slots = kSlots;
+      qa.counter = w.counters;
+      if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)ntm), st) != cudaSuccess)
+        return FS_ERR_CUDA;
+      {
+        ProfScope ps(ctx, PROF_PASS2, st);
+        if (dispatch_passes(sh.N1, sh.N2, p1, p2, qa, st) != cudaSuccess) return FS_ERR_CUDA;
+      }
+      ctx->launches += 1;
+      continue;
+    }
     for (int b0 = 0; b0 < ntm; b0 += B) {
       const int nb = (ntm - b0) < B ? (ntm - b0) : B;
-      Pass1Args p1{};
-      p1.ya = w.ya;
-      p1.yb = w.yb;
-      p1.qq = w.qq;
-      p1.sky_stride = w.stride;
-      p1.f1 = f1;
-      p1.nspin = nspin;
       p1.tmpl0 = b0;
-      p1.N2 = sh.N2;
-      p1.n1max = n1max;
-      p1.nfft = seg->g.nfft;
-      p1.Z = w.Z;
+      p2.tmpl0 = b0;
       {
         ProfScope ps(ctx, PROF_PASS1, st);
         if (dispatch_pass1(sh.N1, p1, nb, st) != cudaSuccess) return FS_ERR_CUDA;
       }
-      Pass2Args p2{};
-      p2.Z = w.Z;
-      p2.N1 = sh.N1;
-      p2.N2 = sh.N2;
-      p2.nfft = seg->g.nfft;
-      p2.norm = w.norm;
-      p2.nspin = nspin;
-      p2.tmpl0 = b0;
-      p2.sky_base = g0;
-      p2.F = F ? F + (int64_t)g0 * nspin * nbins : nullptr;
-      p2.nbins = nbins;
-      p2.thr = thr;
-      p2.cand = cand;
-      p2.cap = cap;
-      p2.ncand = (unsigned long long *)ncand;
-      p2.flags = ctx->d_flags;
       {
         ProfScope ps(ctx, PROF_PASS2, st);
         if (dispatch_pass2(sh.N2, full, p2, nb, st) != cudaSuccess) return FS_ERR_CUDA;
@@ -631,7 +811,7 @@ fs_status demod32_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, do
                         double *tsrc, double *ab2, cudaStream_t st) {
   const int64_t n = seg->g.n;
   Ws32 w;
-  fs_status s = workspace32(ctx, seg, 1, 1, n, 1, st, &w);
+  fs_status s = workspace32(ctx, seg, 1, 1, n, 1, 1, st, &w);
   if (s != FS_OK) return s;
   // alpha/delta are host values: stage them through the partial buffer's tail is not
   // possible before allocation, so use a small device copy.

@@ -66,6 +66,11 @@ fs_status fs_create(fs_ctx **ctx, const fs_detector *det, int32_t device) {
   if (gs && atoi(gs) > 0) c->group_skies = atoi(gs);
   const char *pk = getenv("FSTAT_PERSISTENT");
   if (pk) c->persistent = atoi(pk) != 0;
+  const char *lg = getenv("FSTAT_QUEUE_LAG");
+  if (lg && atoi(lg) > 0) c->queue_lag = atoi(lg);
+  const char *zs = getenv("FSTAT_Z_SLOTS");
+  if (zs && atoi(zs) > 1) c->z_slots = atoi(zs);
+  if (c->z_slots < c->queue_lag + 2) c->z_slots = c->queue_lag + 2;
   *ctx = c;
   return FS_OK;
 }

@@ -23,6 +23,8 @@ struct fs_ctx {
   int batch_templates = 16;
   int group_skies = 16;
   bool persistent = true;  // both transform passes in one persistent launch per sky group
+  int queue_lag = 8;       // rounds between a template's pass-1 and pass-2 items
+  int z_slots = 16;        // Z ring slots (each 2 x Nfft complex floats)
   // launch accounting and optional event profiling
   int64_t launches = 0;
   bool prof = false;

@@ -158,12 +158,12 @@ __global__ void __launch_bounds__(256) k_demod32(DemodArgs A) {
     A.yb[s * A.stride + j] = ob;
     A.qq[s * A.stride + j] = oq;
   }
-  // deterministic block sums of a^2, b^2 in FP64
-  double da = a2, db = b2;
+  // deterministic block sums of a^2, b^2: FP32 within a warp (32 terms), FP64 beyond
   for (int o = 16; o > 0; o >>= 1) {
-    da += __shfl_down_sync(kFull, da, o);
-    db += __shfl_down_sync(kFull, db, o);
+    a2 += __shfl_down_sync(kFull, a2, o);
+    b2 += __shfl_down_sync(kFull, b2, o);
   }
+  const double da = a2, db = b2;
   __shared__ double wa[8], wb[8];
   if ((threadIdx.x & 31) == 0) { wa[threadIdx.x >> 5] = da; wb[threadIdx.x >> 5] = db; }
   __syncthreads();
@@ -282,14 +282,17 @@ __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, i
   __syncthreads();
   sfor<0, Q>([&](auto bb) { v[bb] = xch[(bb * P + t) * CS + cs]; });
   dft_inplace<Q>(v);  // v[d] = X[k1 = t + P d] of column n2
-  // inter-pass twiddle exp(-2 pi i n2 k1 / Nfft): exact anchors every 16 d, recurrence between
+  // inter-pass twiddle exp(-2 pi i n2 k1 / Nfft): anchors every 16 d from the
+  // hardware sine/cosine (argument reduced to half a turn), and an exactly
+  // rounded step for the recurrence between anchors so errors do not build up
   const int64_t nf = A.nfft;
   const float inv_nf = 1.0f / (float)nf;
   const float2 step = expm2pi((float)(((int64_t)n2 * P) & (nf - 1)) * inv_nf);
   float2 wt = make_float2(1.f, 0.f);
   sfor<0, Q>([&](auto d) {
     if constexpr (d % 16 == 0) {
-      wt = expm2pi((float)(((int64_t)n2 * (t + P * d)) & (nf - 1)) * inv_nf);
+      const float f = (float)(((int64_t)n2 * (t + P * d)) & (nf - 1)) * inv_nf;
+      wt = chirp_cycles(f > 0.5f ? f - 1.0f : f);
     } else {
       wt = cmul(wt, step);
     }
@@ -473,7 +476,6 @@ __global__ void __launch_bounds__(256, 2) k_passes(Pass1Args A1, Pass2Args A2, Q
   float2 *twL = smem;            // W_{L1}^q
   float2 *twM = smem + L1;       // W_{L2}^{b c} by c then b
   float2 *work = smem + L1 + L2; // union of the pass-1 exchange and the pass-2 work areas
-  __shared__ int s_item;
   for (int q = threadIdx.x; q < L1; q += blockDim.x) twL[q] = expm2pi((float)q * (1.0f / L1));
   twiddle_matrix(twM, P2, Q2);
   unsigned *next = Qa.counter;
@@ -481,36 +483,39 @@ __global__ void __launch_bounds__(256, 2) k_passes(Pass1Args A1, Pass2Args A2, Q
   unsigned *done2 = Qa.counter + 1 + Qa.ntm;
   const int ipr = Qa.tiles1 + Qa.tiles2;
   const int total = (Qa.ntm + Qa.lag) * ipr;
-  for (;;) {
-    __syncthreads();  // previous item finished with shared memory
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(next, 1u);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= total) break;
-    const int r = item / ipr, j = item - r * ipr;
-    if (j < Qa.tiles1) {
-      const int tm = r;
-      if (tm >= Qa.ntm) continue;
-      if (threadIdx.x == 0 && tm >= Qa.slots) wait_at_least(done2 + (tm - Qa.slots), Qa.tiles2, A2.flags);
-      __syncthreads();
-      pass1_item<P1, Q1, CW, AM>(A1, tm, tm % Qa.slots, j, work, twL);
-      __syncthreads();
+  // the next item is taken from the queue while the current one runs: thread 0
+  // keeps the atomic's result in a register and publishes it at the end of the item
+  __shared__ int s_next;
+  if (threadIdx.x == 0) s_next = (int)atomicAdd(next, 1u);
+  __syncthreads();
+  int cur = s_next;
+  while (cur < total) {
+    int nxt = 0;
+    if (threadIdx.x == 0) nxt = (int)atomicAdd(next, 1u);
+    const int r = cur / ipr, j = cur - r * ipr;
+    const bool is1 = j < Qa.tiles1;
+    const int tm = is1 ? r : r - Qa.lag;
+    const bool valid = tm >= 0 && tm < Qa.ntm;
+    if (valid) {
       if (threadIdx.x == 0) {
-        __threadfence();
-        red_release_add(done1 + tm, 1u);
+        if (is1) {
+          if (tm >= Qa.slots) wait_at_least(done2 + (tm - Qa.slots), Qa.tiles2, A2.flags);
+        } else {
+          wait_at_least(done1 + tm, Qa.tiles1, A2.flags);
+        }
       }
-    } else {
-      const int tm = r - Qa.lag;
-      if (tm < 0) continue;
-      if (threadIdx.x == 0) wait_at_least(done1 + tm, Qa.tiles1, A2.flags);
-      __syncthreads();
-      pass2_item<P2, Q2, 8, false>(A2, tm, tm % Qa.slots, j - Qa.tiles1, work, twM);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        red_release_add(done2 + tm, 1u);
-      }
+      __syncthreads();  // dependencies met; every thread has read s_next
+      if (is1) pass1_item<P1, Q1, CW, AM>(A1, tm, tm % Qa.slots, j, work, twL);
+      else pass2_item<P2, Q2, 8, false>(A2, tm, tm % Qa.slots, j - Qa.tiles1, work, twM);
     }
+    __syncthreads();  // item complete: global writes done, shared memory free
+    if (threadIdx.x == 0) {
+      // the barrier orders every thread's writes before this gpu-scope release
+      if (valid) red_release_add((is1 ? done1 : done2) + tm, 1u);
+      s_next = nxt;
+    }
+    __syncthreads();
+    cur = s_next;
   }
 }
 
@@ -582,8 +587,6 @@ static cudaError_t dispatch_pass2(int N2, bool full, const Pass2Args &a, int nb,
 }
 
 // Persistent pass kernel: shapes (N1 x N2) -> (P1, Q1, P2, Q2), pruning AM.
-constexpr int kLag = 3;    // rounds between a template's pass-1 and pass-2 items
-constexpr int kSlots = 8;  // Z ring slots
 
 template <int P1, int Q1, int AM, int P2, int Q2>
 static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
@@ -652,7 +655,7 @@ static fs_status workspace32(fs_ctx *ctx, const fs_seg *seg, int G, int B, int64
   size_t o_nm = off; off = align256(off + sizeof(float2) * G);
   size_t o_ab = off; off = align256(off + sizeof(double2) * G);
   size_t o_pa = off; off = align256(off + sizeof(double) * 2 * (size_t)nblk * G);
-  size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)seg->g.nfft * (B > kSlots ? B : kSlots));
+  size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)seg->g.nfft * (B > ctx->z_slots ? B : ctx->z_slots));
   size_t o_ct = off; off = align256(off + sizeof(unsigned) * (1 + 2 * (size_t)G * nspin));
   fs_status s = ensure_buffer(&ctx->ws, &ctx->ws_bytes, off, st);
   if (s != FS_OK) return s;
@@ -767,8 +770,8 @@ fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
       qa.ntm = ntm;
       qa.tiles1 = sh.N2 / (256 / (2 * (sh.N1 <= 128 ? 8 : 16)));
       qa.tiles2 = sh.N1 / (8 * (16 / (sh.N2 <= 128 ? 8 : 16)));
-      qa.lag = kLag;
-      qa.slots = kSlots;
+      qa.lag = ctx->queue_lag;
+      qa.slots = ctx->z_slots;
       qa.counter = w.counters;
       if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)ntm), st) != cudaSuccess)
         return FS_ERR_CUDA;

@@ -468,9 +468,9 @@ __device__ inline void wait_at_least(const unsigned *p, unsigned target, uint32_
   }
 }
 
-template <int P1, int Q1, int AM, int P2, int Q2>
-__global__ void __launch_bounds__(256, 2) k_passes(Pass1Args A1, Pass2Args A2, QueueArgs Qa) {
-  constexpr int CW = 256 / (2 * P1);
+template <int P1, int Q1, int AM, int P2, int Q2, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_passes(Pass1Args A1, Pass2Args A2, QueueArgs Qa) {
+  constexpr int CW = NT / (2 * P1);
   constexpr int L1 = P1 * Q1, L2 = P2 * Q2;
   extern __shared__ float2 smem[];
   float2 *twL = smem;            // W_{L1}^q
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(256, 2) k_passes(Pass1Args A1, Pass2Args A2, Q
       }
       __syncthreads();  // dependencies met; every thread has read s_next
       if (is1) pass1_item<P1, Q1, CW, AM>(A1, tm, tm % Qa.slots, j, work, twL);
-      else pass2_item<P2, Q2, 8, false>(A2, tm, tm % Qa.slots, j - Qa.tiles1, work, twM);
+      else pass2_item<P2, Q2, NT / 32, false>(A2, tm, tm % Qa.slots, j - Qa.tiles1, work, twM);
     }
     __syncthreads();  // item complete: global writes done, shared memory free
     if (threadIdx.x == 0) {
@@ -588,46 +588,61 @@ static cudaError_t dispatch_pass2(int N2, bool full, const Pass2Args &a, int nb,
 
 // Persistent pass kernel: shapes (N1 x N2) -> (P1, Q1, P2, Q2), pruning AM.
 
-template <int P1, int Q1, int AM, int P2, int Q2>
+template <int P1, int Q1, int AM, int P2, int Q2, int NT>
 static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
-  constexpr int CW = 256 / (2 * P1);
+  constexpr int CW = NT / (2 * P1);
   constexpr size_t w1 = (size_t)P1 * Q1 * 2 * CW;
-  constexpr size_t w2 = pass2_work_floats2<P2, Q2, 8, false>();
+  constexpr size_t w2 = pass2_work_floats2<P2, Q2, NT / 32, false>();
   const size_t sm = sizeof(float2) * ((size_t)P1 * Q1 + (size_t)P2 * Q2 + (w1 > w2 ? w1 : w2));
-  auto kern = k_passes<P1, Q1, AM, P2, Q2>;
+  auto kern = k_passes<P1, Q1, AM, P2, Q2, NT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, sm);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
   const long total = (long)(qa.ntm + qa.lag) * (qa.tiles1 + qa.tiles2);
   long grid = (long)occ * nsm;
   if (grid > total) grid = total;
-  kern<<<(unsigned)grid, 256, sm, st>>>(a1, a2, qa);
+  kern<<<(unsigned)grid, NT, sm, st>>>(a1, a2, qa);
   return cudaGetLastError();
 }
 
-template <int P1, int Q1, int P2, int Q2>
+template <int P1, int Q1, int P2, int Q2, int NT>
 static cudaError_t launch_passes_am(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
-  if (a1.n1max <= P1 * Q1 / 2) return launch_passes_t<P1, Q1, P1 / 2, P2, Q2>(a1, a2, qa, st);
-  return launch_passes_t<P1, Q1, P1, P2, Q2>(a1, a2, qa, st);
+  if (a1.n1max <= P1 * Q1 / 2) return launch_passes_t<P1, Q1, P1 / 2, P2, Q2, NT>(a1, a2, qa, st);
+  return launch_passes_t<P1, Q1, P1, P2, Q2, NT>(a1, a2, qa, st);
 }
 
-static cudaError_t dispatch_passes(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
-                                   cudaStream_t st) {
+template <int NT>
+static cudaError_t dispatch_passes_nt(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2,
+                                      const QueueArgs &qa, cudaStream_t st) {
   switch (N1 * 4096 + N2) {
-    case 64 * 4096 + 64: return launch_passes_am<8, 8, 8, 8>(a1, a2, qa, st);
-    case 128 * 4096 + 64: return launch_passes_am<8, 16, 8, 8>(a1, a2, qa, st);
-    case 128 * 4096 + 128: return launch_passes_am<8, 16, 8, 16>(a1, a2, qa, st);
-    case 256 * 4096 + 128: return launch_passes_am<16, 16, 8, 16>(a1, a2, qa, st);
-    case 256 * 4096 + 256: return launch_passes_am<16, 16, 16, 16>(a1, a2, qa, st);
-    case 512 * 4096 + 256: return launch_passes_am<16, 32, 16, 16>(a1, a2, qa, st);
-    case 512 * 4096 + 512: return launch_passes_am<16, 32, 16, 32>(a1, a2, qa, st);
+    case 64 * 4096 + 64: return launch_passes_am<8, 8, 8, 8, NT>(a1, a2, qa, st);
+    case 128 * 4096 + 64: return launch_passes_am<8, 16, 8, 8, NT>(a1, a2, qa, st);
+    case 128 * 4096 + 128: return launch_passes_am<8, 16, 8, 16, NT>(a1, a2, qa, st);
+    case 256 * 4096 + 128: return launch_passes_am<16, 16, 8, 16, NT>(a1, a2, qa, st);
+    case 256 * 4096 + 256: return launch_passes_am<16, 16, 16, 16, NT>(a1, a2, qa, st);
+    case 512 * 4096 + 256: return launch_passes_am<16, 32, 16, 16, NT>(a1, a2, qa, st);
+    case 512 * 4096 + 512: return launch_passes_am<16, 32, 16, 32, NT>(a1, a2, qa, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// Work-item geometry of the persistent kernel for NT threads per CTA.
+static void queue_tiles(int N1, int N2, int NT, int *tiles1, int *tiles2) {
+  const int P1 = N1 <= 128 ? 8 : 16, P2 = N2 <= 128 ? 8 : 16;
+  *tiles1 = N2 / (NT / (2 * P1));
+  *tiles2 = N1 / ((NT / 32) * (16 / P2));
+}
+
+// 256 threads (2 CTAs per SM): measured faster than 128 threads with half-size items.
+constexpr int kPersistThreads = 256;
+static cudaError_t dispatch_passes(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2,
+                                   const QueueArgs &qa, cudaStream_t st) {
+  return dispatch_passes_nt<kPersistThreads>(N1, N2, a1, a2, qa, st);
 }
 
 struct Ws32 {
@@ -768,8 +783,7 @@ fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
     if (persistent) {
       QueueArgs qa{};
       qa.ntm = ntm;
-      qa.tiles1 = sh.N2 / (256 / (2 * (sh.N1 <= 128 ? 8 : 16)));
-      qa.tiles2 = sh.N1 / (8 * (16 / (sh.N2 <= 128 ? 8 : 16)));
+      queue_tiles(sh.N1, sh.N2, kPersistThreads, &qa.tiles1, &qa.tiles2);
       qa.lag = ctx->queue_lag;
       qa.slots = ctx->z_slots;
       qa.counter = w.counters;

@@ -57,7 +57,8 @@ typedef enum {
   FS_ERR_CUDA = 5,        /* a CUDA runtime call failed                      */
   FS_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out              */
   FS_ERR_UNSUPPORTED = 7, /* valid request this build does not implement     */
-  FS_ERR_NOMEM = 8        /* device allocation failed                        */
+  FS_ERR_NOMEM = 8,       /* device allocation failed                        */
+  FS_ERR_SCRATCH = 9      /* request needs more than FS_NOALLOC_SCRATCH_BYTES */
 } fs_status;
 
 /* Detector site and analytic-Earth parameters, radians.
@@ -148,6 +149,34 @@ FS_API fs_status fs_search(fs_ctx *ctx, fs_seg *seg,
  * of desc->x_dtype at x_dev), reusing the segment's buffers: no allocation.
  * Same work and errors as fs_prepare_segment. */
 FS_API fs_status fs_seg_load(fs_seg *seg, const void *x_dev, void *stream);
+
+/* Allocation-free search.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory while searching,
+ * for example an application whose framework already owns the GPU's memory
+ * through its own caching pool (a cudaMalloc here could fail or fragment that
+ * pool), or a latency-sensitive loop that cannot afford the device-wide
+ * synchronisation that cudaFree implies.
+ *
+ * Same arguments and results as fs_search, restricted to segments prepared
+ * with FS_PREC_F32 and nbins = nfft/2 (else FS_ERR_UNSUPPORTED).  Its working
+ * memory is one fixed array of FS_NOALLOC_SCRATCH_BYTES that the library
+ * holds on every device where it is loaded, until the process exits; a request
+ * whose per-sky arrays, transform ring and counters do not fit returns
+ * FS_ERR_SCRATCH before launching anything (roughly: nfft up to 2^17).  The
+ * call allocates nothing: no cudaMalloc, no cudaFree, no library allocator.
+ * The first call on a device looks up the array's device address (no
+ * allocation); make that first call before any stream capture.  Every call
+ * shares the one array and the array keeps the last call's contents (the call
+ * clears what must start at zero itself): calls whose work overlaps on the GPU,
+ * from any context or stream, race with each other and must be serialised by
+ * the caller. */
+#define FS_NOALLOC_SCRATCH_BYTES (16u << 20)
+FS_API fs_status fs_search_noalloc(fs_ctx *ctx, fs_seg *seg,
+                                   const double *alpha_dev, const double *delta_dev, int32_t nsky,
+                                   const double *f1_dev, int32_t nspin, float F_thr,
+                                   float *F_out_dev, int64_t nbins,
+                                   fs_candidate *cand_dev, int64_t cand_cap, int64_t *n_cand_dev,
+                                   void *stream);
 
 /* Synchronise `stream` and return (and clear) the first device-side error
  * latched since the last call, or FS_OK. */

@@ -18,6 +18,7 @@
 // stride-Q samples, twiddle exp(-2 pi i b c / L), DFT_Q) with one exchange
 // through shared memory.
 #include <stdio.h>
+#include <mutex>
 #include "fs_internal.h"
 #include "fs_model.cuh"
 #include "fs_dft.cuh"
@@ -843,6 +844,118 @@ fs_status demod32_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, do
   k_demod_finalize<<<1, 256, 0, st>>>(w.partial, w.nblk_a1, n, seg->g.dt, seg->g.S0, nullptr, (double2 *)ab2);
   k_widen<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.ya, w.yb, ya, yb, n);
   return cuda_status(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ allocation-free search
+// The working memory of fs_search_noalloc: one fixed array per device, alive
+// until the process exits.  Host code never dereferences the symbol; it looks up
+// the array's device address once per device and passes that address on.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FS_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_addr[256];
+
+static fs_status noalloc_scratch(unsigned char **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return FS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return FS_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = (unsigned char *)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return FS_OK;
+}
+
+fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
+                           const double *f1, int nspin, float thr, float *F, int64_t nbins, fs_candidate *cand,
+                           int64_t cap, int64_t *ncand, cudaStream_t st) {
+  if (seg->d.precision != FS_PREC_F32 || nbins != seg->g.nfft / 2) return FS_ERR_UNSUPPORTED;
+  FftShape sh;
+  if (!fft_shape(seg->g.nfft, &sh)) return FS_ERR_SHAPE;
+  const int64_t n = seg->g.n;
+  const int n1max = (int)((n + sh.N2 - 1) / sh.N2);
+  const int64_t npad = (int64_t)n1max * sh.N2;
+  const int64_t stride = (npad + 63) & ~(int64_t)63;
+  const int nblk = (int)((npad + 255) / 256);
+  const int lag = 4, slots = 6;  // one sky per launch: a short ring suffices
+  // layout inside the fixed array (one sky at a time)
+  size_t off = 0;
+  const size_t o_sky = off; off = align256(off + sizeof(SkyConst32));
+  const size_t o_ya = off; off = align256(off + sizeof(float2) * stride);
+  const size_t o_yb = off; off = align256(off + sizeof(float2) * stride);
+  const size_t o_qq = off; off = align256(off + sizeof(float2) * stride);
+  const size_t o_nm = off; off = align256(off + sizeof(float2));
+  const size_t o_ab = off; off = align256(off + sizeof(double2));
+  const size_t o_pa = off; off = align256(off + sizeof(double) * 2 * (size_t)nblk);
+  const size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)seg->g.nfft * slots);
+  const size_t o_ct = off; off = align256(off + sizeof(unsigned) * (1 + 2 * (size_t)nspin));
+  if (off > (size_t)FS_NOALLOC_SCRATCH_BYTES) return FS_ERR_SCRATCH;
+  unsigned char *base = nullptr;
+  fs_status s = noalloc_scratch(&base);
+  if (s != FS_OK) return s;
+  Ws32 w{};
+  w.skyc = (SkyConst32 *)(base + o_sky);
+  w.ya = (float2 *)(base + o_ya);
+  w.yb = (float2 *)(base + o_yb);
+  w.qq = (float2 *)(base + o_qq);
+  w.norm = (float2 *)(base + o_nm);
+  w.ab2 = (double2 *)(base + o_ab);
+  w.partial = (double *)(base + o_pa);
+  w.Z = (float2 *)(base + o_z);
+  w.counters = (unsigned *)(base + o_ct);
+  w.stride = stride;
+  w.nblk_a1 = nblk;
+  if (cudaMemsetAsync(ncand, 0, sizeof(int64_t), st) != cudaSuccess) return FS_ERR_CUDA;
+  DemodArgs DA = demod_args(seg, w, npad);
+  for (int g0 = 0; g0 < nsky; g0++) {
+    if (sky_constants32(alpha + g0, delta + g0, 1, seg->g, ctx->det, w.skyc, st) != cudaSuccess) return FS_ERR_CUDA;
+    if (launch_demod(DA, 1, nblk, seg->d.interp, st) != cudaSuccess) return FS_ERR_CUDA;
+    k_demod_finalize<<<1, 256, 0, st>>>(w.partial, nblk, n, seg->g.dt, seg->g.S0, w.norm, w.ab2);
+    Pass1Args p1{};
+    p1.ya = w.ya;
+    p1.yb = w.yb;
+    p1.qq = w.qq;
+    p1.sky_stride = w.stride;
+    p1.f1 = f1;
+    p1.nspin = nspin;
+    p1.N2 = sh.N2;
+    p1.n1max = n1max;
+    p1.nfft = seg->g.nfft;
+    p1.Z = w.Z;
+    Pass2Args p2{};
+    p2.Z = w.Z;
+    p2.N1 = sh.N1;
+    p2.N2 = sh.N2;
+    p2.nfft = seg->g.nfft;
+    p2.norm = w.norm;
+    p2.nspin = nspin;
+    p2.sky_base = g0;
+    p2.F = F ? F + (int64_t)g0 * nspin * nbins : nullptr;
+    p2.nbins = nbins;
+    p2.thr = thr;
+    p2.cand = cand;
+    p2.cap = cap;
+    p2.ncand = (unsigned long long *)ncand;
+    p2.flags = ctx->d_flags;
+    QueueArgs qa{};
+    qa.ntm = nspin;
+    queue_tiles(sh.N1, sh.N2, kPersistThreads, &qa.tiles1, &qa.tiles2);
+    qa.lag = lag;
+    qa.slots = slots;
+    qa.counter = w.counters;
+    // the array keeps the previous call's contents: the queue counters start at zero
+    if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)nspin), st) != cudaSuccess)
+      return FS_ERR_CUDA;
+    if (dispatch_passes(sh.N1, sh.N2, p1, p2, qa, st) != cudaSuccess) return FS_ERR_CUDA;
+    ctx->launches += 4;
+  }
+  return FS_OK;
 }
 
 }  // namespace fs

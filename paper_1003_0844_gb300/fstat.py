@@ -19,12 +19,12 @@ LIB_PATH = os.path.join(_HERE, "libfstat.so")
 
 FS_OK = 0
 STATUS = {0: "FS_OK", 1: "FS_ERR_ARG", 2: "FS_ERR_SHAPE", 3: "FS_ERR_CAPACITY", 4: "FS_ERR_NONFINITE",
-          5: "FS_ERR_CUDA", 6: "FS_ERR_TIMEOUT", 7: "FS_ERR_UNSUPPORTED", 8: "FS_ERR_NOMEM"}
+          5: "FS_ERR_CUDA", 6: "FS_ERR_TIMEOUT", 7: "FS_ERR_UNSUPPORTED", 8: "FS_ERR_NOMEM", 9: "FS_ERR_SCRATCH"}
 PREC = {"f32": 0, "f64": 1}
 INTERP = {"spline": 0, "nearest": 1}
 EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_seg_destroy", "fs_seg_load", "fs_search",
            "fs_sync_status", "fs_strerror", "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling",
-           "fs_get_stats"]
+           "fs_get_stats", "fs_search_noalloc"]
 PROF_KINDS = ("prepare", "demodulate", "pass1", "pass2", "other")
 
 
@@ -75,13 +75,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fs_set_profiling.argtypes = [vp, i32]
     lib.fs_get_stats.argtypes = [vp, ctypes.POINTER(_Stats), i32]
     lib.fs_search.argtypes = [vp, vp, vp, vp, i32, vp, i32, f32, vp, i64, vp, i64, vp, vp]
+    lib.fs_search_noalloc.argtypes = [vp, vp, vp, vp, i32, vp, i32, f32, vp, i64, vp, i64, vp, vp]
     lib.fs_sync_status.argtypes = [vp, vp]
     lib.fs_strerror.argtypes = [ctypes.c_int]
     lib.fs_strerror.restype = ctypes.c_char_p
     lib.fs_seg_upsampled.argtypes = [vp, vp, vp]
     lib.fs_demodulate.argtypes = [vp, vp, f64, f64, vp, vp, vp, vp, vp]
     lib.fs_inject.argtypes = [vp, vp, i64, f64, f64, f64, ctypes.POINTER(_Injection), i32, vp]
-    for name in ("fs_create", "fs_prepare_segment", "fs_seg_load", "fs_search", "fs_sync_status",
+    for name in ("fs_create", "fs_prepare_segment", "fs_seg_load", "fs_search", "fs_search_noalloc", "fs_sync_status",
                  "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling", "fs_get_stats"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib

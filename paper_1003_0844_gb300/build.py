@@ -35,8 +35,8 @@ def _flags(extra=()):
                    "-Xcompiler", "-fvisibility=hidden"] + list(extra)
 
 
-def _compile(src: str, verbose: bool, extra) -> str:
-    obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, verbose: bool, extra, out_dir=OUT_DIR) -> str:
+    obj = os.path.join(out_dir, os.path.splitext(src)[0] + ".o")
     srcp = os.path.join(CSRC, src)
     deps = [srcp] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     deps.append(os.path.join(HERE, "..", "include", "fstat.h"))
@@ -53,19 +53,21 @@ def _compile(src: str, verbose: bool, extra) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(verbose: bool = False, extra=(), lib: str = LIB, out_dir: str = OUT_DIR) -> str:
+    """Compile and link; `extra` nvcc flags, `lib`/`out_dir` select another output."""
+    os.makedirs(out_dir, exist_ok=True)
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose, extra), SOURCES))
-    if os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(o) for o in objs):
-        return LIB
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose, extra, out_dir), SOURCES))
+    LIB_ = lib
+    if os.path.exists(LIB_) and all(os.path.getmtime(LIB_) >= os.path.getmtime(o) for o in objs):
+        return LIB_
+    tmp = LIB_ + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, LIB_)
+    return LIB_
 
 
 if __name__ == "__main__":

@@ -72,6 +72,7 @@ fs_status fs_create(fs_ctx **ctx, const fs_detector *det, int32_t device) {
   const char *zs = getenv("FSTAT_Z_SLOTS");
   if (zs && atoi(zs) > 1) c->z_slots = atoi(zs);
   if (c->z_slots < c->queue_lag + 2) c->z_slots = c->queue_lag + 2;
+
   *ctx = c;
   return FS_OK;
 }

@@ -21,7 +21,7 @@ struct fs_ctx {
   void *scratch = nullptr;
   // tuning knobs (templates per batch, skies per group)
   int batch_templates = 16;
-  int group_skies = 16;
+  int group_skies = 256;
   bool persistent = true;  // both transform passes in one persistent launch per sky group
   int queue_lag = 8;       // rounds between a template's pass-1 and pass-2 items
   int z_slots = 16;        // Z ring slots (each 2 x Nfft complex floats)

@@ -337,13 +337,26 @@ struct Pass2Args {
 // slot zs.  Needs 32 * WARPS threads; work holds the exchange and F tile areas
 // (pass2_work_floats2), twM the matrix W_L^{b c} stored by c then b.  Z is read
 // past L1 (it may have been rewritten since an earlier item on this SM).
-template <int P, int Q, int WARPS, bool FULLBINS>
+// Exchange layout of one sub-DFT: element (c, b) at c * PITCH + col(c, b).  For
+// 16-thread sub-DFTs the row pitch is Q and the column is XOR-swizzled by c
+// (conflict-free, no padding); otherwise rows are padded to Q + 1.
+template <int P, int Q>
+struct Xch2 {
+  static constexpr bool SWZ = (P == 16);
+  static constexpr int PITCH = SWZ ? Q : Q + 1;
+  static constexpr int SIZE = P * PITCH;
+  static __device__ __forceinline__ int at(int c, int b) { return c * PITCH + (SWZ ? (b ^ (c & 15)) : b); }
+};
+
+// ALIAS_F: the F tile reuses the exchange area (one more barrier, less shared memory).
+template <int P, int Q, int WARPS, bool FULLBINS, bool ALIAS_F = false>
 __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
                                            const float2 *twM) {
   constexpr int T = P, G = 16 / T, R = WARPS * G, S = Q / P;
   constexpr int D = FULLBINS ? Q : Q / 2;  // d values with k2 = t + P d in the output band
-  constexpr int XW = P * (Q + 1);          // exchange floats2 per sub-DFT
-  float *Fs = (float *)(work + WARPS * 2 * G * XW);  // [D*P][R+1]
+  using X = Xch2<P, Q>;
+  constexpr int XW = X::SIZE;              // exchange float2s per sub-DFT
+  float *Fs = (float *)(ALIAS_F ? work : work + WARPS * 2 * G * XW);  // [D*P][R+1]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int t = lane % T, sig = (lane / T) & 1, gr = lane / (2 * T);
   const int row = w * G + gr;
@@ -358,10 +371,11 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
     dft_inplace<P>(v + s * P);
     // W_L^{b c} stored by c then b: lanes read consecutive entries (no bank conflicts)
     sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twM[c * Q + b]); });
-    sfor<0, P>([&](auto c) { xw[c * (Q + 1) + b] = v[s * P + c]; });
+    sfor<0, P>([&](auto c) { xw[X::at(c, b)] = v[s * P + c]; });
   });
   __syncwarp();
-  sfor<0, Q>([&](auto bb) { v[bb] = xw[t * (Q + 1) + bb]; });
+  sfor<0, Q>([&](auto bb) { v[bb] = xw[X::at(t, bb)]; });
+  if constexpr (ALIAS_F) __syncthreads();  // every warp is done with the exchange area
   dft_inplace<Q>(v);  // v[d] = X[k2 = t + P d] of row k1
   const float2 nrm = A.norm[sky];
   const float myn = sig ? nrm.y : nrm.x;
@@ -407,10 +421,12 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
   }
 }
 
-template <int P, int Q, int WARPS, bool FULLBINS>
+template <int P, int Q, int WARPS, bool FULLBINS, bool ALIAS_F = false>
 constexpr size_t pass2_work_floats2() {
   constexpr int G = 16 / P, R = WARPS * G, D = FULLBINS ? Q : Q / 2;
-  return (size_t)WARPS * 2 * G * P * (Q + 1) + ((size_t)D * P * (R + 1) + 1) / 2;
+  constexpr size_t xch = (size_t)WARPS * 2 * G * Xch2<P, Q>::SIZE;
+  constexpr size_t ftile = ((size_t)D * P * (R + 1) + 1) / 2;
+  return ALIAS_F ? (xch > ftile ? xch : ftile) : xch + ftile;
 }
 
 __device__ __forceinline__ void twiddle_matrix(float2 *twM, int P, int Q) {
@@ -469,8 +485,8 @@ __device__ inline void wait_at_least(const unsigned *p, unsigned target, uint32_
   }
 }
 
-template <int P1, int Q1, int AM, int P2, int Q2, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) k_passes(Pass1Args A1, Pass2Args A2, QueueArgs Qa) {
+template <int P1, int Q1, int AM, int P2, int Q2, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2, QueueArgs Qa) {
   constexpr int CW = NT / (2 * P1);
   constexpr int L1 = P1 * Q1, L2 = P2 * Q2;
   extern __shared__ float2 smem[];
@@ -507,7 +523,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_passes(Pass1Args A1, Pass2Args
       }
       __syncthreads();  // dependencies met; every thread has read s_next
       if (is1) pass1_item<P1, Q1, CW, AM>(A1, tm, tm % Qa.slots, j, work, twL);
-      else pass2_item<P2, Q2, NT / 32, false>(A2, tm, tm % Qa.slots, j - Qa.tiles1, work, twM);
+      else pass2_item<P2, Q2, NT / 32, false, (MINB > 2)>(A2, tm, tm % Qa.slots, j - Qa.tiles1, work, twM);
     }
     __syncthreads();  // item complete: global writes done, shared memory free
     if (threadIdx.x == 0) {
@@ -588,14 +604,19 @@ static cudaError_t dispatch_pass2(int N2, bool full, const Pass2Args &a, int nb,
 }
 
 // Persistent pass kernel: shapes (N1 x N2) -> (P1, Q1, P2, Q2), pruning AM.
+#ifndef FS_PERSIST_MINB
+#define FS_PERSIST_MINB 3
+#endif
+constexpr int kPersistMinBlocks = FS_PERSIST_MINB;  // CTAs per SM the kernel is compiled for
 
 template <int P1, int Q1, int AM, int P2, int Q2, int NT>
 static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
   constexpr int CW = NT / (2 * P1);
+  constexpr int MINB = kPersistMinBlocks;
   constexpr size_t w1 = (size_t)P1 * Q1 * 2 * CW;
-  constexpr size_t w2 = pass2_work_floats2<P2, Q2, NT / 32, false>();
+  constexpr size_t w2 = pass2_work_floats2<P2, Q2, NT / 32, false, (MINB > 2)>();
   const size_t sm = sizeof(float2) * ((size_t)P1 * Q1 + (size_t)P2 * Q2 + (w1 > w2 ? w1 : w2));
-  auto kern = k_passes<P1, Q1, AM, P2, Q2, NT>;
+  auto kern = k_passes<P1, Q1, AM, P2, Q2, NT, MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, occ = 0;

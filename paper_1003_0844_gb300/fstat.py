@@ -56,11 +56,13 @@ class _Injection(ctypes.Structure):
 _lib = None
 
 
-def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load libfstat.so (built by paper_1003_0844_gb300.build); raise if it is missing."""
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libfstat.so (built by paper_1003_0844_gb300.build, or the file named by
+    the FSTAT_LIB environment variable); raise if it is missing."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("FSTAT_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError("libfstat.so is not built (%s); run paper_1003_0844_gb300.build.build()" % path)
     lib = ctypes.CDLL(path)

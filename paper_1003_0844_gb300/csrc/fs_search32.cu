@@ -500,39 +500,64 @@ __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2,
   unsigned *done2 = Qa.counter + 1 + Qa.ntm;
   const int ipr = Qa.tiles1 + Qa.tiles2;
   const int total = (Qa.ntm + Qa.lag) * ipr;
-  // the next item is taken from the queue while the current one runs: thread 0
-  // keeps the atomic's result in a register and publishes it at the end of the item
-  __shared__ int s_next;
-  if (threadIdx.x == 0) s_next = (int)atomicAdd(next, 1u);
+  // Items are decoded identically by every thread; thread 0 takes the next item
+  // from the queue while the current one runs, checks whether the next item's
+  // dependency is already met, and publishes both through ping-pong slots before
+  // the end-of-item barrier (the slot it writes was last read before the previous
+  // end-of-item barrier).  A ready item then needs no extra barrier.
+  struct Item {
+    int tm, j;
+    bool is1, valid;
+  };
+  auto decode = [&](int it) {
+    Item d;
+    const int r = it / ipr;
+    d.j = it - r * ipr;
+    d.is1 = d.j < Qa.tiles1;
+    d.tm = d.is1 ? r : r - Qa.lag;
+    d.valid = it < total && d.tm >= 0 && d.tm < Qa.ntm;
+    return d;
+  };
+  auto dep_met = [&](const Item &d) {  // thread 0 only
+    if (!d.valid) return true;
+    if (d.is1) return d.tm < Qa.slots || ld_acquire(done2 + (d.tm - Qa.slots)) >= (unsigned)Qa.tiles2;
+    return ld_acquire(done1 + d.tm) >= (unsigned)Qa.tiles1;
+  };
+  __shared__ int s_next[2], s_ready[2];
+  if (threadIdx.x == 0) {
+    s_next[0] = (int)atomicAdd(next, 1u);
+    s_ready[0] = 0;
+  }
   __syncthreads();
-  int cur = s_next;
+  int buf = 0;
+  int cur = s_next[0], ready = s_ready[0];
   while (cur < total) {
     int nxt = 0;
     if (threadIdx.x == 0) nxt = (int)atomicAdd(next, 1u);
-    const int r = cur / ipr, j = cur - r * ipr;
-    const bool is1 = j < Qa.tiles1;
-    const int tm = is1 ? r : r - Qa.lag;
-    const bool valid = tm >= 0 && tm < Qa.ntm;
-    if (valid) {
-      if (threadIdx.x == 0) {
-        if (is1) {
-          if (tm >= Qa.slots) wait_at_least(done2 + (tm - Qa.slots), Qa.tiles2, A2.flags);
-        } else {
-          wait_at_least(done1 + tm, Qa.tiles1, A2.flags);
+    const Item d = decode(cur);
+    if (d.valid) {
+      if (!ready) {
+        if (threadIdx.x == 0) {
+          if (d.is1) {
+            if (d.tm >= Qa.slots) wait_at_least(done2 + (d.tm - Qa.slots), Qa.tiles2, A2.flags);
+          } else {
+            wait_at_least(done1 + d.tm, Qa.tiles1, A2.flags);
+          }
         }
+        __syncthreads();
       }
-      __syncthreads();  // dependencies met; every thread has read s_next
-      if (is1) pass1_item<P1, Q1, CW, AM>(A1, tm, tm % Qa.slots, j, work, twL);
-      else pass2_item<P2, Q2, NT / 32, false, (MINB > 2)>(A2, tm, tm % Qa.slots, j - Qa.tiles1, work, twM);
+      if (d.is1) pass1_item<P1, Q1, CW, AM>(A1, d.tm, d.tm % Qa.slots, d.j, work, twL);
+      else pass2_item<P2, Q2, NT / 32, false, (MINB > 2)>(A2, d.tm, d.tm % Qa.slots, d.j - Qa.tiles1, work, twM);
     }
-    __syncthreads();  // item complete: global writes done, shared memory free
     if (threadIdx.x == 0) {
-      // the barrier orders every thread's writes before this gpu-scope release
-      if (valid) red_release_add((is1 ? done1 : done2) + tm, 1u);
-      s_next = nxt;
+      s_next[buf ^ 1] = nxt;
+      s_ready[buf ^ 1] = dep_met(decode(nxt)) ? 1 : 0;
     }
-    __syncthreads();
-    cur = s_next;
+    __syncthreads();  // item complete: global writes done, shared memory free, next item published
+    if (threadIdx.x == 0 && d.valid) red_release_add((d.is1 ? done1 : done2) + d.tm, 1u);
+    buf ^= 1;
+    cur = s_next[buf];
+    ready = s_ready[buf];
   }
 }
 

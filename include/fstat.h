@@ -146,8 +146,9 @@ FS_API fs_status fs_search(fs_ctx *ctx, fs_seg *seg,
                     void *stream);
 
 /* Re-run the segment preparation on new data of the same shape (n samples
- * of desc->x_dtype at x_dev), reusing the segment's buffers: no allocation.
- * Same work and errors as fs_prepare_segment. */
+ * of desc->x_dtype at x_dev), reusing the segment's buffers and its length-n
+ * transform plan: no allocation.  Same results and errors as
+ * fs_prepare_segment. */
 FS_API fs_status fs_seg_load(fs_seg *seg, const void *x_dev, void *stream);
 
 /* Allocation-free search.  The paper has no counterpart: this entry point

@@ -169,6 +169,8 @@ void fs_seg_destroy(fs_seg *s) {
   cudaFree(s->x32);
   cudaFree(s->x2);
   cudaFree(s->coef);
+  cudaFree(s->blu_bhat);
+  cudaFree(s->blu_tw);
   delete s;
 }
 

@@ -46,6 +46,10 @@ struct fs_seg {
   float *x32 = nullptr;     // input as float [n] (nearest-neighbour path)
   double *x2 = nullptr;     // Fourier x2 upsampled [2n]
   void *coef = nullptr;     // spline coefficients per interval: float4 or double[4] x [2n]
+  // Bluestein plan of the length-n DFT (depends on n only): transform length m,
+  // FFT of the chirp b and the FFT twiddles; built by the first load
+  int64_t blu_m = 0;
+  double2 *blu_bhat = nullptr, *blu_tw = nullptr;
 };
 
 // ---- launchers implemented in the .cu files (all asynchronous on `st`) ----

@@ -139,24 +139,42 @@ fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st) {
   int64_t N = seg->g.n;
   int64_t M = 1;
   while (M < 2 * N - 1) M <<= 1;
-  // scratch: Bhat, a, tmp, X (M each) + twiddles (M/2)
-  size_t need = sizeof(double2) * (4 * (size_t)M + (size_t)M / 2 + 1);
+  int64_t *L = &seg->ctx->launches;
+  // plan (once per segment): chirp spectrum Bhat = FFT_M(b) and the FFT twiddles
+  if (seg->blu_m != M) {
+    cudaFree(seg->blu_bhat);
+    cudaFree(seg->blu_tw);
+    seg->blu_bhat = seg->blu_tw = nullptr;
+    seg->blu_m = 0;
+    if (cudaMalloc(&seg->blu_bhat, sizeof(double2) * M) != cudaSuccess ||
+        cudaMalloc(&seg->blu_tw, sizeof(double2) * (M / 2)) != cudaSuccess) {
+      cudaGetLastError();
+      return FS_ERR_NOMEM;
+    }
+  }
+  // scratch: a, tmp, X (M each)
+  size_t need = sizeof(double2) * 3 * (size_t)M;
   fs_status s = ensure_buffer(&seg->ctx->scratch, &seg->ctx->scratch_bytes, need, st);
   if (s != FS_OK) return s;
-  double2 *Bhat = (double2 *)seg->ctx->scratch;
-  double2 *a = Bhat + M, *tmp = a + M, *X = tmp + M, *tw = X + M;
+  double2 *a = (double2 *)seg->ctx->scratch;
+  double2 *tmp = a + M, *X = tmp + M;
+  double2 *Bhat = seg->blu_bhat, *tw = seg->blu_tw;
+  cudaError_t e;
+  if (seg->blu_m != M) {
+    e = fft64_twiddles(tw, M, st);
+    if (e != cudaSuccess) return FS_ERR_CUDA;
+    k_bluestein_b<<<nblk(M), 256, 0, st>>>(Bhat, N, M);
+    *L += 2;
+    e = fft64(Bhat, tmp, tw, M, 1, -1, st, L);
+    if (e != cudaSuccess) return FS_ERR_CUDA;
+    seg->blu_m = M;
+  }
 
   if (seg->d.x_dtype == FS_X_F32)
     k_load_x<float><<<nblk(N), 256, 0, st>>>((const float *)x_dev, seg->x64, seg->x32, N, seg->ctx->d_flags);
   else
     k_load_x<double><<<nblk(N), 256, 0, st>>>((const double *)x_dev, seg->x64, seg->x32, N, seg->ctx->d_flags);
-  int64_t *L = &seg->ctx->launches;
-  cudaError_t e = fft64_twiddles(tw, M, st);
-  if (e != cudaSuccess) return FS_ERR_CUDA;
-  k_bluestein_b<<<nblk(M), 256, 0, st>>>(Bhat, N, M);
-  *L += 3;
-  e = fft64(Bhat, tmp, tw, M, 1, -1, st, L);
-  if (e != cudaSuccess) return FS_ERR_CUDA;
+  *L += 1;
   // X = DFT_N(x)
   e = bluestein_dft(X, seg->x64, nullptr, 0, N, M, Bhat, a, tmp, tw, st, L);
   if (e != cudaSuccess) return FS_ERR_CUDA;

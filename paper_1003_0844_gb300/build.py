@@ -35,10 +35,10 @@ def _flags(extra=()):
                    "-Xcompiler", "-fvisibility=hidden"] + list(extra)
 
 
-def _compile(src: str, verbose: bool, extra, out_dir=OUT_DIR) -> str:
+def _compile(src: str, verbose: bool, extra, out_dir=OUT_DIR, src_dir=CSRC) -> str:
     obj = os.path.join(out_dir, os.path.splitext(src)[0] + ".o")
-    srcp = os.path.join(CSRC, src)
-    deps = [srcp] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
+    srcp = os.path.join(src_dir, src)
+    deps = [srcp] + [os.path.join(src_dir, h) for h in os.listdir(src_dir) if h.endswith((".h", ".cuh"))]
     deps.append(os.path.join(HERE, "..", "include", "fstat.h"))
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj
@@ -53,11 +53,12 @@ def _compile(src: str, verbose: bool, extra, out_dir=OUT_DIR) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=(), lib: str = LIB, out_dir: str = OUT_DIR) -> str:
-    """Compile and link; `extra` nvcc flags, `lib`/`out_dir` select another output."""
+def build(verbose: bool = False, extra=(), lib: str = LIB, out_dir: str = OUT_DIR, src_dir: str = CSRC) -> str:
+    """Compile and link; `extra` nvcc flags, `lib`/`out_dir` select another output,
+    `src_dir` another copy of the sources (it must sit two levels below include/)."""
     os.makedirs(out_dir, exist_ok=True)
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose, extra, out_dir), SOURCES))
+        objs = list(ex.map(lambda s: _compile(s, verbose, extra, out_dir, src_dir), SOURCES))
     LIB_ = lib
     if os.path.exists(LIB_) and all(os.path.getmtime(LIB_) >= os.path.getmtime(o) for o in objs):
         return LIB_

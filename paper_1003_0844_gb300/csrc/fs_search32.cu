@@ -376,7 +376,7 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
   __syncwarp();
   sfor<0, Q>([&](auto bb) { v[bb] = xw[X::at(t, bb)]; });
   if constexpr (ALIAS_F) __syncthreads();  // every warp is done with the exchange area
-  dft_inplace<Q>(v);  // v[d] = X[k2 = t + P d] of row k1
+  dft_inplace<Q, Q, (FULLBINS ? Q : Q / 2)>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)
   const float2 nrm = A.norm[sky];
   const float myn = sig ? nrm.y : nrm.x;
   float p[D];

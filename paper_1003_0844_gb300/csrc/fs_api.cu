@@ -71,7 +71,8 @@ fs_status fs_create(fs_ctx **ctx, const fs_detector *det, int32_t device) {
   if (lg && atoi(lg) > 0) c->queue_lag = atoi(lg);
   const char *zs = getenv("FSTAT_Z_SLOTS");
   if (zs && atoi(zs) > 1) c->z_slots = atoi(zs);
-  if (c->z_slots < c->queue_lag + 2) c->z_slots = c->queue_lag + 2;
+  const char *qr = getenv("FSTAT_QUEUE_ROUND");
+  if (qr && atoi(qr) > 0) c->queue_round = atoi(qr);
 
   *ctx = c;
   return FS_OK;

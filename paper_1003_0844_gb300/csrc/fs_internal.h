@@ -23,8 +23,11 @@ struct fs_ctx {
   int batch_templates = 16;
   int group_skies = 256;
   bool persistent = true;  // both transform passes in one persistent launch per sky group
-  int queue_lag = 8;       // rounds between a template's pass-1 and pass-2 items
-  int z_slots = 16;        // Z ring slots (each 2 x Nfft complex floats)
+  // persistent-queue shape; 0 = automatic (a round's pass-1 items fill ~85% of the
+  // resident CTAs, pass 2 one round behind, a ring of three rounds)
+  int queue_lag = 0;       // rounds between a template's pass-1 and pass-2 items
+  int z_slots = 0;         // Z ring slots (each 2 x Nfft complex floats)
+  int queue_round = 0;     // templates per queue round
   // launch accounting and optional event profiling
   int64_t launches = 0;
   bool prof = false;

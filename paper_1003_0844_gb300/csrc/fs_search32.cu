@@ -461,6 +461,8 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
 // continues (results are then invalid, the device stays responsive).
 struct QueueArgs {
   int ntm, tiles1, tiles2, lag, slots;
+  int kr;             // templates per round: a round holds the pass-1 items of kr templates,
+                      // then the pass-2 items of the kr templates lag rounds earlier
   unsigned *counter;  // [1 + 2 ntm]: next item, pass-1 done per template, pass-2 done per template
 };
 
@@ -498,8 +500,9 @@ __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2,
   unsigned *next = Qa.counter;
   unsigned *done1 = Qa.counter + 1;
   unsigned *done2 = Qa.counter + 1 + Qa.ntm;
-  const int ipr = Qa.tiles1 + Qa.tiles2;
-  const int total = (Qa.ntm + Qa.lag) * ipr;
+  const int kr = Qa.kr;
+  const int ipr = kr * (Qa.tiles1 + Qa.tiles2);
+  const int total = ((Qa.ntm + kr - 1) / kr + Qa.lag) * ipr;
   // Items are decoded identically by every thread; thread 0 takes the next item
   // from the queue while the current one runs, checks whether the next item's
   // dependency is already met, and publishes both through ping-pong slots before
@@ -512,9 +515,18 @@ __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2,
   auto decode = [&](int it) {
     Item d;
     const int r = it / ipr;
-    d.j = it - r * ipr;
-    d.is1 = d.j < Qa.tiles1;
-    d.tm = d.is1 ? r : r - Qa.lag;
+    const int jr = it - r * ipr;
+    d.is1 = jr < kr * Qa.tiles1;
+    if (d.is1) {
+      const int k = jr / Qa.tiles1;
+      d.j = jr - k * Qa.tiles1;
+      d.tm = r * kr + k;
+    } else {
+      const int j2 = jr - kr * Qa.tiles1;
+      const int k = j2 / Qa.tiles2;
+      d.j = Qa.tiles1 + (j2 - k * Qa.tiles2);
+      d.tm = (r - Qa.lag) * kr + k;
+    }
     d.valid = it < total && d.tm >= 0 && d.tm < Qa.ntm;
     return d;
   };
@@ -650,7 +662,7 @@ static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, con
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, sm);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
-  const long total = (long)(qa.ntm + qa.lag) * (qa.tiles1 + qa.tiles2);
+  const long total = (long)((qa.ntm + qa.kr - 1) / qa.kr + qa.lag) * qa.kr * (qa.tiles1 + qa.tiles2);
   long grid = (long)occ * nsm;
   if (grid > total) grid = total;
   kern<<<(unsigned)grid, NT, sm, st>>>(a1, a2, qa);
@@ -717,7 +729,7 @@ static fs_status workspace32(fs_ctx *ctx, const fs_seg *seg, int G, int B, int64
   size_t o_nm = off; off = align256(off + sizeof(float2) * G);
   size_t o_ab = off; off = align256(off + sizeof(double2) * G);
   size_t o_pa = off; off = align256(off + sizeof(double) * 2 * (size_t)nblk * G);
-  size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)seg->g.nfft * (B > ctx->z_slots ? B : ctx->z_slots));
+  size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)seg->g.nfft * B);
   size_t o_ct = off; off = align256(off + sizeof(unsigned) * (1 + 2 * (size_t)G * nspin));
   fs_status s = ensure_buffer(&ctx->ws, &ctx->ws_bytes, off, st);
   if (s != FS_OK) return s;
@@ -766,6 +778,25 @@ static cudaError_t launch_demod(const DemodArgs &A, int nsky, int nblk, int inte
   return cudaGetLastError();
 }
 
+// Shape of the persistent queue: templates per round, lag (rounds) and Z slots.
+struct QueueShape {
+  int kr, lag, slots, tiles1, tiles2;
+};
+static QueueShape queue_shape(const fs_ctx *ctx, const FftShape &sh) {
+  QueueShape q{};
+  queue_tiles(sh.N1, sh.N2, kPersistThreads, &q.tiles1, &q.tiles2);
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int ctas = kPersistMinBlocks * (nsm > 0 ? nsm : 1);
+  q.kr = ctx->queue_round > 0 ? ctx->queue_round : (int)(0.85 * ctas / q.tiles1 + 0.5);
+  if (q.kr < 1) q.kr = 1;
+  q.lag = ctx->queue_lag > 0 ? ctx->queue_lag : 1;
+  const int need = (q.lag + 2) * q.kr;
+  q.slots = ctx->z_slots > need ? ctx->z_slots : need;
+  return q;
+}
+
 fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
                    const double *f1, int nspin, float thr, float *F, int64_t nbins, fs_candidate *cand,
                    int64_t cap, int64_t *ncand, cudaStream_t st) {
@@ -775,13 +806,14 @@ fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
   const int n1max = (int)((n + sh.N2 - 1) / sh.N2);
   const int64_t npad = (int64_t)n1max * sh.N2;
   const int G = ctx->group_skies < nsky ? ctx->group_skies : nsky;
-  const int B = ctx->batch_templates;
+  const bool full = (nbins == seg->g.nfft);
+  const bool persistent = !full && ctx->persistent;
+  const QueueShape qs = queue_shape(ctx, sh);
+  const int B = persistent ? qs.slots : ctx->batch_templates;  // Z slots of the workspace
   Ws32 w;
   fs_status s = workspace32(ctx, seg, G, B, npad, nsky, nspin, st, &w);
   if (s != FS_OK) return s;
   if (cudaMemsetAsync(ncand, 0, sizeof(int64_t), st) != cudaSuccess) return FS_ERR_CUDA;
-  const bool full = (nbins == seg->g.nfft);
-  const bool persistent = !full && ctx->persistent;
   DemodArgs DA = demod_args(seg, w, npad);
   {
     ProfScope ps(ctx, PROF_OTHER, st);
@@ -830,9 +862,11 @@ fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
     if (persistent) {
       QueueArgs qa{};
       qa.ntm = ntm;
-      queue_tiles(sh.N1, sh.N2, kPersistThreads, &qa.tiles1, &qa.tiles2);
-      qa.lag = ctx->queue_lag;
-      qa.slots = ctx->z_slots;
+      qa.tiles1 = qs.tiles1;
+      qa.tiles2 = qs.tiles2;
+      qa.kr = qs.kr;
+      qa.lag = qs.lag;
+      qa.slots = qs.slots;
       qa.counter = w.counters;
       if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)ntm), st) != cudaSuccess)
         return FS_ERR_CUDA;
@@ -992,6 +1026,7 @@ fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
     QueueArgs qa{};
     qa.ntm = nspin;
     queue_tiles(sh.N1, sh.N2, kPersistThreads, &qa.tiles1, &qa.tiles2);
+    qa.kr = 1;
     qa.lag = lag;
     qa.slots = slots;
     qa.counter = w.counters;

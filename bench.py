@@ -49,6 +49,30 @@ def _args():
     return p.parse_args()
 
 
+def _profile_traffic(kernel_profile: str):
+    """DRAM bytes per template of the persistent kernel from the committed ncu summary,
+    or None when the kernel's sources changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", kernel_profile)
+    if not os.path.exists(path):
+        return None, "no profile"
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.split(":")[0] in ("traffic_bytes_per_template", "kernel_sources_sha256",
+                                                  "kernel_sources"):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    try:
+        h = hashlib.sha256()
+        for f in fields["kernel_sources"].split():
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+    except (KeyError, OSError):
+        return None, "profile incomplete"
+    if h.hexdigest() != fields.get("kernel_sources_sha256"):
+        return None, "kernel changed since the ncu capture"
+    return float(fields["traffic_bytes_per_template"]), "ncu capture, scaled by templates per launch"
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -155,7 +179,7 @@ def main():
         return run_reference(args)
     import torch
     import torch.distributed as dist
-    from paper_1003_0844_gb300 import build, fstat as fs
+    from paper_1003_0844_gb300 import build, fstat as fs, shard
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -176,8 +200,9 @@ def main():
     x32 = x64.float().contiguous()
     # weak scaling: rank r searches its own 256-sky shard of a lattice of 256 x world points
     a_all, d_all = W.sky_grid(wl.nsky * world)
-    alpha = torch.as_tensor(np.ascontiguousarray(a_all[rank::world]), device="cuda")
-    delta = torch.as_tensor(np.ascontiguousarray(d_all[rank::world]), device="cuda")
+    mine = shard.sky_shard(wl.nsky, rank, world)
+    alpha = torch.as_tensor(np.ascontiguousarray(a_all[mine]), device="cuda")
+    delta = torch.as_tensor(np.ascontiguousarray(d_all[mine]), device="cuda")
     f1 = torch.as_tensor(W.spin_grid(wl.nspin, *wl.f1_range), device="cuda")
     nsky, nspin, nbins = alpha.numel(), f1.numel(), wl.nbins
     ntempl = nsky * nspin
@@ -219,10 +244,7 @@ def main():
     stats = ctx.stats(reset=True)
     ctx.set_profiling(False)
     ctx.check()
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = shard.max_over_ranks(total_ms, device="cuda")
     ms_per_step = total_ms / args.steps
     value = ntempl * world / (ms_per_step / 1e3)
 
@@ -244,8 +266,11 @@ def main():
         per_launch_ms = dom_ms / dom_n
         tpl = ntempl * args.steps / dom_n
         achieved = flops_tmpl[dom] * tpl / (per_launch_ms / 1e3) / 1e12
+        tpt, tnote = _profile_traffic("k_passes_grid_2d.md") if fused else (None, "per-batch mode")
         roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": (tpt * tpl if tpt is not None else None), "traffic_unit": "bytes per launch",
+                "traffic_note": tnote,
                 "peak_kind": "FP32 CUDA-core peak from unit counts and max clock (152 SM x 128 x 2 x 2070 MHz)",
                 "flop_convention": "5 Nfft log2 Nfft per complex FFT, 2 FFTs per template",
                 "per_launch_ms": per_launch_ms, "templates_per_launch": tpl}
@@ -289,7 +314,7 @@ def main():
         seg64.close()
         # the oracle on the host cores, bounded sample
         xh = x32.cpu().numpy()
-        rate, secs, done = cpu_oracle_rate(xh, wl, det, a_all[rank::world], d_all[rank::world],
+        rate, secs, done = cpu_oracle_rate(xh, wl, det, a_all[mine], d_all[mine],
                                            W.spin_grid(wl.nspin, *wl.f1_range), args.cpu_templates)
         line["cpu_baseline"] = {"value": rate, "unit": "templates/s", "cores": 1, "kind": "oracle",
                                 "sample": "segment preparation + %d templates (FFT mode), %.1f s" % (done, secs)}

@@ -88,9 +88,14 @@ def spline_eval(y: np.ndarray, M: np.ndarray, u: np.ndarray) -> np.ndarray:
 
 def source_times(tb: np.ndarray, alpha: float, delta: float, det, tol: float = 1e-10,
                  max_iter: int = 50) -> np.ndarray:
-    """Solve t + phi_m(t) = t_b (Eq. eq:Bt) for the source time t by fixed-point iteration."""
+    """Solve t + phi_m(t) = t_b (Eq. eq:Bt) for the source time t by fixed-point iteration.
+
+    Stops when the largest step is below tol or below 8 FP64 spacings of the
+    largest time (the finer of the two that FP64 can resolve)."""
     tb = np.asarray(tb, dtype=np.float64)
     t = tb.copy()
+    if tb.size:
+        tol = max(tol, 8.0 * np.spacing(np.max(np.abs(tb)) + 600.0))
     for _ in range(max_iter):
         t_new = tb - earth.phi_m(t, alpha, delta, det)
         step = np.max(np.abs(t_new - t)) if t.size else 0.0

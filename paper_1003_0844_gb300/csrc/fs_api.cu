@@ -99,7 +99,6 @@ fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d
   if (d->interp != FS_INTERP_SPLINE2X && d->interp != FS_INTERP_NEAREST) return FS_ERR_ARG;
   if (d->x_dtype != FS_X_F32 && d->x_dtype != FS_X_F64) return FS_ERR_ARG;
   if (!is_pow2(d->nfft) || d->nfft < d->n || d->nfft < 4096 || d->nfft > (int64_t(1) << 20)) return FS_ERR_SHAPE;
-  if (d->precision == FS_PREC_F32 && d->nfft > (int64_t(1) << 18)) return FS_ERR_UNSUPPORTED;
   if (d->n > (int64_t(1) << 28)) return FS_ERR_SHAPE;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
   cudaStream_t st = as_stream(stream);

@@ -338,21 +338,99 @@ struct Pass2Args {
 // (pass2_work_floats2), twM the matrix W_L^{b c} stored by c then b.  Z is read
 // past L1 (it may have been rewritten since an earlier item on this SM).
 // Exchange layout of one sub-DFT: element (c, b) at c * PITCH + col(c, b).  For
-// 16-thread sub-DFTs the row pitch is Q and the column is XOR-swizzled by c
-// (conflict-free, no padding); otherwise rows are padded to Q + 1.
+// 16- and 32-thread sub-DFTs the row pitch is Q and the column is XOR-swizzled
+// by c (conflict-free, no padding); otherwise rows are padded to Q + 1.
 template <int P, int Q>
 struct Xch2 {
-  static constexpr bool SWZ = (P == 16);
+  static constexpr bool SWZ = (P >= 16);
   static constexpr int PITCH = SWZ ? Q : Q + 1;
   static constexpr int SIZE = P * PITCH;
   static __device__ __forceinline__ int at(int c, int b) { return c * PITCH + (SWZ ? (b ^ (c & 15)) : b); }
 };
 
+// Pass-2 work item for 32-thread row DFTs (N2 = 1024): a warp holds one signal of
+// one row (warps 2r, 2r+1: signals a, b of row r), so an item covers WARPS/2
+// rows; the two signals' |X|^2 terms meet through the F tile.
+template <int Q, int WARPS, bool FULLBINS>
+__device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
+                                                const float2 *twM) {
+  constexpr int P = 32, R = WARPS / 2, S = Q / P;
+  constexpr int D = FULLBINS ? Q : Q / 2;
+  using X = Xch2<P, Q>;
+  constexpr int XW = X::SIZE;
+  constexpr int K2 = D * P;
+  float *Fs = (float *)work;  // [K2][R + 1], aliased over the exchange area
+  const int t = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int sig = w & 1, row = w >> 1;
+  const int k1 = rt * R + row;
+  const int sky = tm / A.nspin, spin = tm - sky * A.nspin;
+  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * A.nfft + (int64_t)k1 * A.N2;
+  float2 v[Q];
+  sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = __ldcg(z + Q * a + t + P * s); }); });
+  float2 *xw = work + w * XW;
+  sfor<0, S>([&](auto s) {
+    const int b = t + P * s;
+    dft_inplace<P>(v + s * P);
+    sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twM[c * Q + b]); });
+    sfor<0, P>([&](auto c) { xw[X::at(c, b)] = v[s * P + c]; });
+  });
+  __syncwarp();
+  sfor<0, Q>([&](auto bb) { v[bb] = xw[X::at(t, bb)]; });
+  __syncthreads();  // every warp is done with the exchange area (reused for the F tile)
+  dft_inplace<Q, Q, D>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)
+  const float2 nrm = A.norm[sky];
+  if (sig == 0) {
+    sfor<0, D>([&](auto d) { Fs[(t + P * d) * (R + 1) + row] = fmaf(v[d].x, v[d].x, v[d].y * v[d].y) * nrm.x; });
+  }
+  __syncthreads();
+  const unsigned lt_mask = (1u << t) - 1u;
+  if (sig == 1) {
+    sfor<0, D>([&](auto d) {
+      const int k2 = t + P * d;
+      float *fp = Fs + k2 * (R + 1) + row;
+      const float Fv = *fp + fmaf(v[d].x, v[d].x, v[d].y * v[d].y) * nrm.y;
+      *fp = Fv;
+      const bool hit = Fv > A.thr;
+      const unsigned m = __ballot_sync(kFull, hit);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (t == leader) base = atomicAdd(A.ncand, (unsigned long long)__popc(m));
+        base = __shfl_sync(kFull, base, leader);
+        if (hit) {
+          const unsigned long long idx = base + __popc(m & lt_mask);
+          if ((long long)idx < A.cap) {
+            fs_candidate c;
+            c.sky = (uint32_t)(A.sky_base + sky);
+            c.spin = (uint32_t)spin;
+            c.bin = (uint32_t)(k1 + A.N1 * k2);
+            c.F = Fv;
+            A.cand[idx] = c;
+          } else {
+            atomicOr(A.flags, ERRF_CAPACITY);
+          }
+        }
+      }
+    });
+  }
+  if (A.F == nullptr) return;
+  __syncthreads();
+  float *Fo = A.F + (int64_t)tm * A.nbins + rt * R;
+  for (int idx = threadIdx.x; idx < K2 * R; idx += blockDim.x) {
+    const int k2 = idx / R, r = idx - k2 * R;
+    __stcs(Fo + r + (int64_t)A.N1 * k2, Fs[k2 * (R + 1) + r]);
+  }
+}
+
 // ALIAS_F: the F tile reuses the exchange area (one more barrier, less shared memory).
 template <int P, int Q, int WARPS, bool FULLBINS, bool ALIAS_F = false>
 __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
                                            const float2 *twM) {
-  constexpr int T = P, G = 16 / T, R = WARPS * G, S = Q / P;
+  if constexpr (P == 32) {
+    pass2_item_wide<Q, WARPS, FULLBINS>(A, tm, zs, rt, work, twM);
+    return;
+  }
+  constexpr int T = P, G = (P <= 16 ? 16 / P : 1), R = WARPS * G, S = Q / P;
   constexpr int D = FULLBINS ? Q : Q / 2;  // d values with k2 = t + P d in the output band
   using X = Xch2<P, Q>;
   constexpr int XW = X::SIZE;              // exchange float2s per sub-DFT
@@ -423,10 +501,11 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
 
 template <int P, int Q, int WARPS, bool FULLBINS, bool ALIAS_F = false>
 constexpr size_t pass2_work_floats2() {
-  constexpr int G = 16 / P, R = WARPS * G, D = FULLBINS ? Q : Q / 2;
-  constexpr size_t xch = (size_t)WARPS * 2 * G * Xch2<P, Q>::SIZE;
+  constexpr int G = P <= 16 ? 16 / P : 1;
+  constexpr int R = P <= 16 ? WARPS * G : WARPS / 2, D = FULLBINS ? Q : Q / 2;
+  constexpr size_t xch = P <= 16 ? (size_t)WARPS * 2 * G * Xch2<P, Q>::SIZE : (size_t)WARPS * Xch2<P, Q>::SIZE;
   constexpr size_t ftile = ((size_t)D * P * (R + 1) + 1) / 2;
-  return ALIAS_F ? (xch > ftile ? xch : ftile) : xch + ftile;
+  return (ALIAS_F || P == 32) ? (xch > ftile ? xch : ftile) : xch + ftile;
 }
 
 __device__ __forceinline__ void twiddle_matrix(float2 *twM, int P, int Q) {
@@ -439,7 +518,7 @@ __device__ __forceinline__ void twiddle_matrix(float2 *twM, int P, int Q) {
 
 template <int P, int Q, int WARPS, bool FULLBINS>
 __global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
-  constexpr int G = 16 / P, R = WARPS * G;
+  constexpr int R = P <= 16 ? WARPS * (16 / P) : WARPS / 2;
   extern __shared__ float2 smem[];
   float2 *twM = smem;
   float2 *work = smem + P * Q;
@@ -559,7 +638,7 @@ __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2,
         __syncthreads();
       }
       if (d.is1) pass1_item<P1, Q1, CW, AM>(A1, d.tm, d.tm % Qa.slots, d.j, work, twL);
-      else pass2_item<P2, Q2, NT / 32, false, (MINB > 2)>(A2, d.tm, d.tm % Qa.slots, d.j - Qa.tiles1, work, twM);
+      else pass2_item<P2, Q2, NT / 32, false, true>(A2, d.tm, d.tm % Qa.slots, d.j - Qa.tiles1, work, twM);
     }
     if (threadIdx.x == 0) {
       s_next[buf ^ 1] = nxt;
@@ -580,17 +659,16 @@ struct FftShape {
 static bool fft_shape(int64_t nfft, FftShape *s) {
   int p = 0;
   while (((int64_t)1 << p) < nfft) p++;
-  if (((int64_t)1 << p) != nfft || p < 12 || p > 18) return false;
+  if (((int64_t)1 << p) != nfft || p < 12 || p > 20) return false;
   s->N1 = 1 << ((p + 1) / 2);
   s->N2 = 1 << (p / 2);
   return true;
 }
 
-constexpr int kPass1Cols = 8;   // columns per pass-1 CTA
-constexpr int kPass2Warps = 8;  // rows (warps) per pass-2 CTA for 16-thread sub-DFTs
+constexpr int kPass2Warps = 8;  // warps per pass-2 CTA
 
 template <int P, int Q>
-static size_t pass1_smem() { return sizeof(float2) * ((size_t)P * Q * 2 * kPass1Cols + (size_t)P * Q); }
+static size_t pass1_smem() { return sizeof(float2) * ((size_t)P * Q * 2 * (256 / (2 * P)) + (size_t)P * Q); }
 template <int P, int Q, bool FULL>
 static size_t pass2_smem() {
   return sizeof(float2) * ((size_t)P * Q + pass2_work_floats2<P, Q, kPass2Warps, FULL>());
@@ -599,7 +677,7 @@ static size_t pass2_smem() {
 template <int P, int Q>
 static cudaError_t launch_pass1(const Pass1Args &a, int nb, cudaStream_t st) {
   size_t sm = pass1_smem<P, Q>();
-  constexpr int CW = kPass1Cols;
+  constexpr int CW = 256 / (2 * P);
   auto kern = (a.n1max <= P * Q / 2) ? k_pass1<P, Q, CW, P / 2> : k_pass1<P, Q, CW, P>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -612,7 +690,7 @@ static cudaError_t launch_pass2(const Pass2Args &a, int nb, cudaStream_t st) {
   auto kern = k_pass2<P, Q, kPass2Warps, FULL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  constexpr int R = kPass2Warps * (16 / P);
+  constexpr int R = P <= 16 ? kPass2Warps * (16 / P) : kPass2Warps / 2;
   kern<<<nb * (a.N1 / R), 32 * kPass2Warps, sm, st>>>(a);
   return cudaGetLastError();
 }
@@ -623,6 +701,7 @@ static cudaError_t dispatch_pass1(int N1, const Pass1Args &a, int nb, cudaStream
     case 128: return launch_pass1<8, 16>(a, nb, st);
     case 256: return launch_pass1<16, 16>(a, nb, st);
     case 512: return launch_pass1<16, 32>(a, nb, st);
+    case 1024: return launch_pass1<32, 32>(a, nb, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -636,6 +715,8 @@ static cudaError_t dispatch_pass2(int N2, bool full, const Pass2Args &a, int nb,
     case 513: return launch_pass2<16, 16, true>(a, nb, st);
     case 1024: return launch_pass2<16, 32, false>(a, nb, st);
     case 1025: return launch_pass2<16, 32, true>(a, nb, st);
+    case 2048: return launch_pass2<32, 32, false>(a, nb, st);
+    case 2049: return launch_pass2<32, 32, true>(a, nb, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -646,13 +727,21 @@ static cudaError_t dispatch_pass2(int N2, bool full, const Pass2Args &a, int nb,
 #endif
 constexpr int kPersistMinBlocks = FS_PERSIST_MINB;  // CTAs per SM the kernel is compiled for
 
+template <int P1, int Q1, int P2, int Q2, int NT>
+constexpr size_t persist_smem() {
+  constexpr int CW = NT / (2 * P1);
+  constexpr size_t w1 = (size_t)P1 * Q1 * 2 * CW;
+  constexpr size_t w2 = pass2_work_floats2<P2, Q2, NT / 32, false, true>();
+  return sizeof(float2) * ((size_t)P1 * Q1 + (size_t)P2 * Q2 + (w1 > w2 ? w1 : w2));
+}
+// CTAs per SM the kernel is compiled for: 3 when three fit in shared memory.
+template <int P1, int Q1, int P2, int Q2, int NT>
+constexpr int persist_minb() { return persist_smem<P1, Q1, P2, Q2, NT>() <= 74 * 1024 ? kPersistMinBlocks : 2; }
+
 template <int P1, int Q1, int AM, int P2, int Q2, int NT>
 static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
-  constexpr int CW = NT / (2 * P1);
-  constexpr int MINB = kPersistMinBlocks;
-  constexpr size_t w1 = (size_t)P1 * Q1 * 2 * CW;
-  constexpr size_t w2 = pass2_work_floats2<P2, Q2, NT / 32, false, (MINB > 2)>();
-  const size_t sm = sizeof(float2) * ((size_t)P1 * Q1 + (size_t)P2 * Q2 + (w1 > w2 ? w1 : w2));
+  constexpr int MINB = persist_minb<P1, Q1, P2, Q2, NT>();
+  const size_t sm = persist_smem<P1, Q1, P2, Q2, NT>();
   auto kern = k_passes<P1, Q1, AM, P2, Q2, NT, MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -686,15 +775,18 @@ static cudaError_t dispatch_passes_nt(int N1, int N2, const Pass1Args &a1, const
     case 256 * 4096 + 256: return launch_passes_am<16, 16, 16, 16, NT>(a1, a2, qa, st);
     case 512 * 4096 + 256: return launch_passes_am<16, 32, 16, 16, NT>(a1, a2, qa, st);
     case 512 * 4096 + 512: return launch_passes_am<16, 32, 16, 32, NT>(a1, a2, qa, st);
+    case 1024 * 4096 + 512: return launch_passes_am<32, 32, 16, 32, NT>(a1, a2, qa, st);
+    case 1024 * 4096 + 1024: return launch_passes_am<32, 32, 32, 32, NT>(a1, a2, qa, st);
   }
   return cudaErrorInvalidValue;
 }
 
 // Work-item geometry of the persistent kernel for NT threads per CTA.
 static void queue_tiles(int N1, int N2, int NT, int *tiles1, int *tiles2) {
-  const int P1 = N1 <= 128 ? 8 : 16, P2 = N2 <= 128 ? 8 : 16;
+  const int P1 = N1 <= 128 ? 8 : (N1 <= 512 ? 16 : 32);
+  const int P2 = N2 <= 128 ? 8 : (N2 <= 512 ? 16 : 32);
   *tiles1 = N2 / (NT / (2 * P1));
-  *tiles2 = N1 / ((NT / 32) * (16 / P2));
+  *tiles2 = N1 / (P2 <= 16 ? (NT / 32) * (16 / P2) : (NT / 32) / 2);
 }
 
 // 256 threads (2 CTAs per SM): measured faster than 128 threads with half-size items.
@@ -788,7 +880,7 @@ static QueueShape queue_shape(const fs_ctx *ctx, const FftShape &sh) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int ctas = kPersistMinBlocks * (nsm > 0 ? nsm : 1);
+  const int ctas = (sh.N1 * sh.N2 >= (1 << 19) ? 2 : kPersistMinBlocks) * (nsm > 0 ? nsm : 1);
   q.kr = ctx->queue_round > 0 ? ctx->queue_round : (int)(0.85 * ctas / q.tiles1 + 0.5);
   if (q.kr < 1) q.kr = 1;
   q.lag = ctx->queue_lag > 0 ? ctx->queue_lag : 1;

@@ -106,12 +106,17 @@ SHAPES = [
     ("small", None, 1 << 15),
     ("single_fp64", 30011, 1 << 16),
     ("single_fp64", None, 1 << 17),
+    # 1024-point column DFTs: 3 sidereal days (zero upper half pruned), an unpruned
+    # 2^19 case, and 6 sidereal days on 1024 x 1024
+    ("grid_2d", 129246, 1 << 19),
+    ("grid_2d", 300000, 1 << 19),
+    ("grid_2d", 258492, 1 << 20),
 ]
 
 
 @pytest.mark.parametrize("name,n,nfft", SHAPES)
 def test_search_f32_matches_oracle(fs, name, n, nfft):
-    nsky, nspin = (3, 2) if nfft <= (1 << 15) else (2, 2)
+    nsky, nspin = (3, 2) if nfft <= (1 << 15) else ((2, 2) if nfft <= (1 << 18) else (2, 1))
     wl, det, x, alpha, delta, f1 = make_case(name, n=n, nfft=nfft, nsky=nsky, nspin=nspin)
     if name == "single_fp64":
         f1 = np.array([-1e-9, -7e-9])
@@ -251,8 +256,8 @@ def test_argument_errors(fs):
         fs.Segment(ctx, xd, -1.0, wl.nfft, wl.fl, wl.S0)
     assert e.value.status == 1
     with pytest.raises(fs.FstatError) as e:
-        fs.Segment(ctx, xd, wl.dt, 1 << 19, wl.fl, wl.S0)  # FP32 path supports up to 2^18
-    assert e.value.status == 7
+        fs.Segment(ctx, xd, wl.dt, 1 << 21, wl.fl, wl.S0)  # transforms up to 2^20
+    assert e.value.status == 2
     seg = fs.Segment(ctx, xd, wl.dt, wl.nfft, wl.fl, wl.S0)
     with pytest.raises(fs.FstatError) as e:
         fs.search(ctx, seg, _dev(alpha), _dev(delta), _dev(f1), 10.0, nbins=wl.nfft // 4)

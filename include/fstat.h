@@ -84,7 +84,7 @@ enum { FS_X_F32 = 0, FS_X_F64 = 1 };
 
 /* One data segment: x_k = x(k dt), k < n, t = 0 at the first sample.
  * nfft: zero-padded transform length, a power of two with nfft >= n and
- *   4096 <= nfft <= 2^20;
+ *   4096 <= nfft <= 2^21 (with FS_PREC_F32 and nfft = 2^21, n <= 2^20);
  * fl: lower edge of the band [Hz] (heterodyne reference);
  * S0: one-sided noise spectral density (2 sigma^2 dt for white noise). */
 typedef struct {
@@ -96,7 +96,12 @@ typedef struct {
   int32_t precision; /* FS_PREC_* */
   int32_t interp;    /* FS_INTERP_* */
   int32_t x_dtype;   /* FS_X_F32 or FS_X_F64: element type of x_dev */
-  int32_t reserved;
+  int32_t reserved;  /* must be 0 */
+  /* Epoch of the first sample [s] after the detector's t = 0: the Earth's
+   * orbital and sidereal angles at the segment start are
+   * lambda_e0 + Omega_o t0 and theta_g0 + lon + Omega_r t0 (Sec. V).  Phases,
+   * spindown and the bins keep t = 0 at the segment's first sample. */
+  double t0;
 } fs_segment_desc;
 
 /* A threshold crossing: template (sky index, spindown index), bin k, F_k. */
@@ -113,6 +118,8 @@ typedef struct fs_seg fs_seg;
  * Returns FS_ERR_ARG for null pointers, FS_ERR_CUDA if the device cannot be
  * used.  On success *ctx must be released with fs_destroy. */
 FS_API fs_status fs_create(fs_ctx **ctx, const fs_detector *det, int32_t device);
+/* Release the context and every segment of it still alive (their handles are
+ * invalid afterwards: do not pass them to fs_seg_destroy). */
 FS_API void fs_destroy(fs_ctx *ctx);
 
 /* Prepare the template-independent part of the resampler for one segment
@@ -179,6 +186,58 @@ FS_API fs_status fs_search_noalloc(fs_ctx *ctx, fs_seg *seg,
                                    fs_candidate *cand_dev, int64_t cand_cap, int64_t *n_cand_dev,
                                    void *stream);
 
+/* First, coherent stage of a hierarchical search (Sec. I): the same template
+ * grid searched in each of nseg segments, candidates only.  Every segment
+ * must be prepared with FS_PREC_F32 on this context; lengths and transform
+ * sizes may differ.  Bins are nfft/2 per segment (bins up to Nyquist).
+ * cand_dev: [nseg][cand_cap] candidates, segment s at cand_dev + s cand_cap;
+ * n_cand_dev: [nseg] device int64 counts, overwritten (semantics of
+ * fs_search per segment).  The segments run longest transform first on two
+ * concurrent branches, each with its own workspace.  The first call for a
+ * given set of arguments sizes the workspaces, records the launches of all
+ * segments into a CUDA graph and launches it; a later call with the same
+ * arguments (same segments, pointers, sizes, threshold and tuning) launches
+ * the recorded graph only, so a caller that reloads the segments with
+ * fs_seg_load and calls again repeats the whole batch in one graph launch.
+ * The call must not itself be made inside a stream capture.  FS_ERR_ARG for a
+ * segment of another context or precision. */
+FS_API fs_status fs_search_batch(fs_ctx *ctx, fs_seg *const *segs_host, int32_t nseg,
+                                 const double *alpha_dev, const double *delta_dev, int32_t nsky,
+                                 const double *f1_dev, int32_t nspin, float F_thr,
+                                 fs_candidate *cand_dev, int64_t cand_cap, int64_t *n_cand_dev,
+                                 void *stream);
+
+/* Launch configuration of the FP32 search for one transform length nfft
+ * (no counterpart in the paper: it changes the speed, not the result beyond
+ * rounding).  Zero fields take the defaults.
+ * n1: first-pass length N1 of the split Nsub = N1 x N2 of each
+ *   sub-transform (Nsub = nfft, or 2^20 for nfft = 2^21); the splits built
+ *   are N1/N2 in {1/4, 1/2, 1, 2, 4} with 64 <= N1, N2 <= 1024;
+ * queue_round: templates per round of the persistent work queue;
+ * queue_lag: rounds between a template's first and second pass;
+ * group_skies: skies demodulated per group;
+ * ms_per_template: filled by fs_autotune (ignored by fs_set_tuning). */
+typedef struct {
+  int32_t n1, queue_round, queue_lag, group_skies;
+  float ms_per_template;
+  int32_t reserved;
+} fs_tuning;
+/* Set (t non-NULL) or clear (t NULL) the configuration for nfft.
+ * FS_ERR_ARG for a split this build does not provide. */
+FS_API fs_status fs_set_tuning(fs_ctx *ctx, int64_t nfft, const fs_tuning *t_host);
+/* Current configuration for nfft; FS_ERR_UNSUPPORTED when none is set. */
+FS_API fs_status fs_get_tuning(fs_ctx *ctx, int64_t nfft, fs_tuning *out_host);
+/* Time the candidate configurations for the segment's transform length on
+ * the given grid (candidates only; `reps` timed searches after one warm-up
+ * per configuration) and keep the fastest for that length; *out_host
+ * receives it.  Synchronous.  The candidates are every split built for the
+ * length times queue rounds of about 1/2, 3/4 and 1 of the resident CTAs'
+ * first-pass items times lags 1 and 2. */
+FS_API fs_status fs_autotune(fs_ctx *ctx, fs_seg *seg,
+                             const double *alpha_dev, const double *delta_dev, int32_t nsky,
+                             const double *f1_dev, int32_t nspin, int32_t reps,
+                             fs_tuning *out_host, void *stream);
+
 /* Synchronise `stream` and return (and clear) the first device-side error
  * latched since the last call, or FS_OK. */
 FS_API fs_status fs_sync_status(fs_ctx *ctx, void *stream);
@@ -222,12 +281,14 @@ FS_API fs_status fs_demodulate(fs_ctx *ctx, fs_seg *seg, double alpha, double de
 /* Signal injection (software simulation of Eqs. resp-hphc, sig-eq:ampone):
  * adds to x_dev (n doubles, t_k = k dt) the response to each injection,
  * scaled so that its optimal SNR (Eq. snr-def with Eq. approx1,
- * S0 = 2 sigma^2 dt) is inj[i].snr.  Host array of n_inj records. FP64. */
+ * S0 = 2 sigma^2 dt) is inj[i].snr.  t0: epoch of the first sample, as in
+ * fs_segment_desc (the injection's phase, f0 and f1 refer to t = 0 at the
+ * first sample).  Host array of n_inj records. FP64. */
 typedef struct {
   double f0, f1, alpha, delta, psi, cos_iota, phi0, snr;
 } fs_injection;
 FS_API fs_status fs_inject(fs_ctx *ctx, double *x_dev, int64_t n, double dt, double fl, double sigma,
-                    const fs_injection *inj_host, int32_t n_inj, void *stream);
+                           double t0, const fs_injection *inj_host, int32_t n_inj, void *stream);
 
 #ifdef __cplusplus
 }

@@ -9,6 +9,7 @@ height.  All positions are returned in light-seconds.
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 
 import numpy as np
@@ -32,6 +33,14 @@ def site_equatorial_radius_and_z(lat: float):
     b = ELL_A_M * (1.0 - ELL_FLAT)
     psi = math.atan(b * math.tan(lat) / ELL_A_M)
     return ELL_A_M * math.cos(psi), b * math.sin(psi)
+
+
+def detector_at_epoch(det, t0: float):
+    """The detector seen from a segment that starts t0 seconds after the
+    detector's t = 0: the orbital longitude and the sidereal angle at the
+    segment's first sample are those at t0 (Sec. V), and the segment keeps
+    t = 0 at its first sample."""
+    return dataclasses.replace(det, lambda_e0=det.lambda_e0 + OMEGA_O * t0, theta_g0=det.theta_g0 + OMEGA_R * t0)
 
 
 def sidereal_angle(t, det):

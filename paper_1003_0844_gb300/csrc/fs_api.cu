@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <atomic>
 #include <new>
 #include "fs_internal.h"
 #include "fs_model.cuh"
@@ -32,6 +33,14 @@ fs_status ensure_buffer(void **buf, size_t *cur, size_t bytes, cudaStream_t st) 
 static inline cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
 
 static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static std::atomic<uint64_t> g_seg_serial{0};
+
+// Orbital and sidereal angles at the epoch t0 of a segment's first sample (Sec. V).
+static void set_epoch(const fs_detector &det, double t0, SegGeom *g) {
+  g->theta0 = fmod(det.theta_g0 + det.lon + fmod(kOmegaR * t0, kTwoPi), kTwoPi);
+  g->lambda0 = fmod(det.lambda_e0 + fmod(kOmegaO * t0, kTwoPi), kTwoPi);
+}
 
 extern "C" {
 
@@ -78,12 +87,32 @@ fs_status fs_create(fs_ctx **ctx, const fs_detector *det, int32_t device) {
   return FS_OK;
 }
 
+static void seg_release(fs_seg *s) {
+  cudaFree(s->tab0);
+  cudaFree(s->tab1);
+  cudaFree(s->x64);
+  cudaFree(s->x32);
+  cudaFree(s->x2);
+  cudaFree(s->coef);
+  cudaFree(s->blu_bhat);
+  cudaFree(s->blu_tw);
+  delete s;
+}
+
 void fs_destroy(fs_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  for (fs_seg *s : ctx->segs) seg_release(s);
+  ctx->segs.clear();
+  batch_plan_release(ctx);
+  for (int i = 0; i < 2; i++) {
+    if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+    if (ctx->join[i]) cudaEventDestroy(ctx->join[i]);
+  }
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
   cudaFree(ctx->d_flags);
-  cudaFree(ctx->ws);
+  for (int i = 0; i < fs_ctx::kWsSlots; i++) cudaFree(ctx->ws[i]);
   cudaFree(ctx->ws64);
   cudaFree(ctx->scratch);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
@@ -98,7 +127,10 @@ fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d
   if (d->precision != FS_PREC_F32 && d->precision != FS_PREC_F64) return FS_ERR_ARG;
   if (d->interp != FS_INTERP_SPLINE2X && d->interp != FS_INTERP_NEAREST) return FS_ERR_ARG;
   if (d->x_dtype != FS_X_F32 && d->x_dtype != FS_X_F64) return FS_ERR_ARG;
-  if (!is_pow2(d->nfft) || d->nfft < d->n || d->nfft < 4096 || d->nfft > (int64_t(1) << 20)) return FS_ERR_SHAPE;
+  if (d->reserved != 0 || !isfinite(d->t0)) return FS_ERR_ARG;
+  if (!is_pow2(d->nfft) || d->nfft < d->n || d->nfft < 4096 || d->nfft > (int64_t(1) << 21)) return FS_ERR_SHAPE;
+  // the FP32 path splits a 2^21 transform into two 2^20 ones: the data must fit one
+  if (d->precision == FS_PREC_F32 && d->nfft > (int64_t(1) << 20) && d->n > (int64_t(1) << 20)) return FS_ERR_SHAPE;
   if (d->n > (int64_t(1) << 28)) return FS_ERR_SHAPE;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
   cudaStream_t st = as_stream(stream);
@@ -106,6 +138,7 @@ fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d
   fs_seg *s = new (std::nothrow) fs_seg();
   if (!s) return FS_ERR_NOMEM;
   s->ctx = ctx;
+  s->serial = ++g_seg_serial;
   s->d = *d;
   SegGeom &g = s->g;
   g.n = d->n;
@@ -115,8 +148,7 @@ fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d
   g.S0 = d->S0;
   g.margin = (int64_t)ceil(kMaxDelay / d->dt) + 4;
   g.ngrid = g.n + 2 * g.margin;
-  g.theta0 = ctx->det.theta_g0 + ctx->det.lon;
-  g.lambda0 = ctx->det.lambda_e0;
+  set_epoch(ctx->det, d->t0, &g);
   double re, z;
   site_radius(ctx->det.lat, &re, &z);
   g.re_c = re / kC;
@@ -135,9 +167,10 @@ fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d
   }
   if (!ok) {
     cudaGetLastError();
-    fs_seg_destroy(s);
+    seg_release(s);
     return FS_ERR_NOMEM;
   }
+  ctx->segs.insert(s);
   fs_status r = fs_seg_load(s, x_dev, stream);
   if (r != FS_OK) {
     fs_seg_destroy(s);
@@ -161,17 +194,11 @@ fs_status fs_seg_load(fs_seg *s, const void *x_dev, void *stream) {
 
 void fs_seg_destroy(fs_seg *s) {
   if (!s) return;
-  cudaSetDevice(s->ctx->device);
+  fs_ctx *ctx = s->ctx;
+  cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
-  cudaFree(s->tab0);
-  cudaFree(s->tab1);
-  cudaFree(s->x64);
-  cudaFree(s->x32);
-  cudaFree(s->x2);
-  cudaFree(s->coef);
-  cudaFree(s->blu_bhat);
-  cudaFree(s->blu_tw);
-  delete s;
+  ctx->segs.erase(s);
+  seg_release(s);
 }
 
 fs_status fs_search(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const double *delta_dev, int32_t nsky,
@@ -202,6 +229,63 @@ fs_status fs_search_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, c
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
   return search32_noalloc(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, F_out_dev, nbins, cand_dev,
                           cand_cap, n_cand_dev, as_stream(stream));
+}
+
+fs_status fs_search_batch(fs_ctx *ctx, fs_seg *const *segs, int32_t nseg, const double *alpha_dev,
+                          const double *delta_dev, int32_t nsky, const double *f1_dev, int32_t nspin, float F_thr,
+                          fs_candidate *cand_dev, int64_t cand_cap, int64_t *n_cand_dev, void *stream) {
+  if (!ctx || !segs || nseg < 1 || !alpha_dev || !delta_dev || !f1_dev || !n_cand_dev) return FS_ERR_ARG;
+  if (nsky < 1 || nspin < 1 || cand_cap < 0 || (cand_cap > 0 && !cand_dev)) return FS_ERR_ARG;
+  if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
+  for (int i = 0; i < nseg; i++) {
+    if (!segs[i] || segs[i]->ctx != ctx || segs[i]->d.precision != FS_PREC_F32) return FS_ERR_ARG;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  return search32_batch(ctx, segs, nseg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, cand_dev, cand_cap,
+                        n_cand_dev, as_stream(stream));
+}
+
+static int tune_index(int64_t nfft) {
+  if (!is_pow2(nfft) || nfft < 4096 || nfft > (int64_t(1) << 21)) return -1;
+  int p = 0;
+  while (((int64_t)1 << p) < nfft) p++;
+  return p;
+}
+
+fs_status fs_set_tuning(fs_ctx *ctx, int64_t nfft, const fs_tuning *t) {
+  if (!ctx) return FS_ERR_ARG;
+  const int p = tune_index(nfft);
+  if (p < 0) return FS_ERR_SHAPE;
+  if (!t) {
+    ctx->tuned[p] = false;
+    ctx->tune[p] = fs_tuning{};
+  } else {
+    if (!tuning_valid(nfft, *t)) return FS_ERR_ARG;
+    ctx->tune[p] = *t;
+    ctx->tune[p].ms_per_template = 0.f;
+    ctx->tuned[p] = true;
+  }
+  ctx->tune_version++;
+  return FS_OK;
+}
+
+fs_status fs_get_tuning(fs_ctx *ctx, int64_t nfft, fs_tuning *out) {
+  if (!ctx || !out) return FS_ERR_ARG;
+  const int p = tune_index(nfft);
+  if (p < 0) return FS_ERR_SHAPE;
+  if (!ctx->tuned[p]) return FS_ERR_UNSUPPORTED;
+  *out = ctx->tune[p];
+  return FS_OK;
+}
+
+fs_status fs_autotune(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const double *delta_dev, int32_t nsky,
+                      const double *f1_dev, int32_t nspin, int32_t reps, fs_tuning *out, void *stream) {
+  if (!ctx || !seg || !alpha_dev || !delta_dev || !f1_dev || !out) return FS_ERR_ARG;
+  if (seg->ctx != ctx || seg->d.precision != FS_PREC_F32) return FS_ERR_ARG;
+  if (nsky < 1 || nspin < 1 || reps < 1 || reps > 100) return FS_ERR_ARG;
+  if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  return autotune32(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, nspin, reps, out, as_stream(stream));
 }
 
 fs_status fs_sync_status(fs_ctx *ctx, void *stream) {
@@ -259,12 +343,15 @@ fs_status fs_demodulate(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, do
   return demod64_debug(ctx, seg, alpha, delta, ya_dev, yb_dev, tsrc_dev, ab2_dev, as_stream(stream));
 }
 
-fs_status fs_inject(fs_ctx *ctx, double *x_dev, int64_t n, double dt, double fl, double sigma,
+fs_status fs_inject(fs_ctx *ctx, double *x_dev, int64_t n, double dt, double fl, double sigma, double t0,
                     const fs_injection *inj_host, int32_t n_inj, void *stream) {
   if (!ctx || !x_dev || n < 1 || !(dt > 0.0) || !(sigma > 0.0) || n_inj < 0 || (n_inj > 0 && !inj_host))
     return FS_ERR_ARG;
+  if (!isfinite(t0)) return FS_ERR_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
-  return inject64(ctx, x_dev, n, dt, fl, sigma, inj_host, n_inj, as_stream(stream));
+  SegGeom g{};
+  set_epoch(ctx->det, t0, &g);
+  return inject64(ctx, x_dev, n, dt, fl, sigma, g.theta0, g.lambda0, inj_host, n_inj, as_stream(stream));
 }
 
 }  // extern "C"

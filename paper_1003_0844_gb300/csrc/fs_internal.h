@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <unordered_set>
 #include <vector>
 
 #include "fs_common.cuh"
@@ -10,9 +11,11 @@ struct fs_ctx {
   int device = 0;
   fs_detector det{};
   uint32_t *d_flags = nullptr;       // latched device error bits
-  // FP32 search workspace (grown on demand)
-  size_t ws_bytes = 0;
-  void *ws = nullptr;
+  // FP32 search workspaces (grown on demand): slot 0 serves fs_search and
+  // fs_autotune, slots 1 and 2 the two concurrent branches of fs_search_batch
+  static constexpr int kWsSlots = 3;
+  void *ws[kWsSlots] = {};
+  size_t ws_bytes[kWsSlots] = {};
   // FP64 search workspace
   size_t ws64_bytes = 0;
   void *ws64 = nullptr;
@@ -28,6 +31,16 @@ struct fs_ctx {
   int queue_lag = 0;       // rounds between a template's pass-1 and pass-2 items
   int z_slots = 0;         // Z ring slots (each 2 x Nfft complex floats)
   int queue_round = 0;     // templates per queue round
+  // launch configuration per transform length 2^p (fs_set_tuning / fs_autotune)
+  fs_tuning tune[32] = {};
+  bool tuned[32] = {};
+  uint64_t tune_version = 0;
+  // fs_search_batch: the captured graph and what it was captured for
+  struct BatchPlan *plan = nullptr;
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+  // live segments of this context (fs_destroy releases those still alive)
+  std::unordered_set<fs_seg *> segs;
   // launch accounting and optional event profiling
   int64_t launches = 0;
   bool prof = false;
@@ -39,6 +52,7 @@ struct fs_ctx {
 
 struct fs_seg {
   fs_ctx *ctx = nullptr;
+  uint64_t serial = 0;      // unique per segment in the process (keys captured graphs)
   fs_segment_desc d{};
   fs::SegGeom g{};
   // FP32 path tables on the grid t_m = m dt, m in [-margin, n + margin):
@@ -93,8 +107,8 @@ fs_status demod32_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, do
                         double *tsrc, double *ab2, cudaStream_t st);
 fs_status demod64_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, double *ya, double *yb,
                         double *tsrc, double *ab2, cudaStream_t st);
-fs_status inject64(fs_ctx *ctx, double *x, int64_t n, double dt, double fl, double sigma,
-                   const fs_injection *inj, int n_inj, cudaStream_t st);
+fs_status inject64(fs_ctx *ctx, double *x, int64_t n, double dt, double fl, double sigma, double theta0,
+                   double lambda0, const fs_injection *inj, int n_inj, cudaStream_t st);
 
 // Event profiling of one launch (or group of launches) of a given kind.
 enum { PROF_PREP = 0, PROF_DEMOD = 1, PROF_PASS1 = 2, PROF_PASS2 = 3, PROF_OTHER = 4 };
@@ -125,5 +139,14 @@ struct ProfScope {
 
 // Workspace helper: grow *buf to at least `bytes` (synchronising `st` first).
 fs_status ensure_buffer(void **buf, size_t *cur, size_t bytes, cudaStream_t st);
+
+// Batched search over several segments and the launch-configuration tuner.
+fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const double *alpha, const double *delta,
+                         int nsky, const double *f1, int nspin, float thr, fs_candidate *cand, int64_t cap,
+                         int64_t *ncand, cudaStream_t st);
+void batch_plan_release(fs_ctx *ctx);
+fs_status autotune32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
+                     const double *f1, int nspin, int reps, fs_tuning *out, cudaStream_t st);
+bool tuning_valid(int64_t nfft, const fs_tuning &t);
 
 }  // namespace fs

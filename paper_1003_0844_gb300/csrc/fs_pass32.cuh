@@ -1,0 +1,644 @@
+// Transform passes of the FP32 search path (device code and launch templates),
+// shared by the translation units that instantiate them per transform shape.
+//
+// Per template (sky, f1), the zero-padded transform of length
+// Nfft = N1 * N2 runs in two passes (index n = N2 n1 + n2, bin k = k1 + N1 k2):
+//  pass 1: multiply by the chirp exp(-2 pi i f1 Q_j), DFTs of length N1 over
+//    n1 for a tile of columns n2 (both signals a and b), twiddle
+//    exp(-2 pi i n2 k1 / Nfft), write Z[k1][n2];
+//  pass 2: DFTs of length N2 over n2 for a tile of rows k1, then
+//    F_k = 2/(S0 To) (|Fa_k|^2/<a^2> + |Fb_k|^2/<b^2>) (Eq. OS), threshold
+//    compaction, and a transposed store of F in natural bin order.
+// Each length-L DFT (L = P Q) is itself two register stages (DFT_P over the
+// stride-Q samples, twiddle exp(-2 pi i b c / L), DFT_Q) with one exchange
+// through shared memory.  Both passes run either as separate per-batch launches
+// (k_pass1, k_pass2) or from one persistent work queue (k_passes).
+#pragma once
+#include "fs_internal.h"
+#include "fs_model.cuh"
+#include "fs_dft.cuh"
+
+namespace fs {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------ pass 1
+struct Pass1Args {
+  const float2 *ya, *yb, *qq;
+  int64_t sky_stride;
+  const double *f1;
+  int nspin, tmpl0;
+  int N2, n1max;
+  int64_t nfft;  // sub-transform length N1 N2
+  // A template's transform of length Nfft = nfft << vshift (data no longer than
+  // nfft) is split into 2^vshift sub-transforms of length nfft: sub-transform
+  // s takes the samples times exp(-2 pi i s j / Nfft) and gives the bins
+  // k = (m << vshift) + s (decimation in frequency).  Work items carry the
+  // virtual template index (template << vshift) + s.
+  int vshift;
+  float inv_nfft_total;  // 1 / Nfft
+  float2 *Z;  // [batch][2][N1][N2]
+};
+
+// CW columns per CTA; a warp holds CW columns x 2 signals x TPW sub-DFT threads.
+// AM: rows n1 = Q a + b with a >= AM are zero for every column (AM = P when the
+// data may fill the column, P/2 when n1max <= L/2, i.e. N <= Nfft/2).
+__device__ __forceinline__ float2 chirp_cycles(float f) {
+  // exp(-2 pi i f), |f| <= 1/2: hardware sine/cosine (absolute error < 1e-6 on [-pi, pi])
+  float s, c;
+  __sincosf(6.283185307179586f * f, &s, &c);
+  return make_float2(c, -s);
+}
+
+// One pass-1 work item: template tm (index within the group) and its column
+// tile, writing Z slot zs.  Needs P * 2 * CW threads; xch holds L * 2 * CW
+// float2, twL the table W_L^q (q < L).  The caller synchronises before and after.
+template <int P, int Q, int CW, int AM, int VS = 0>
+__device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, int tile, float2 *xch,
+                                           const float2 *twL) {
+  constexpr int L = P * Q;
+  constexpr int S = Q / P;
+  constexpr int CS = 2 * CW;     // (column, signal) pairs
+  constexpr int TPW = 32 / CS;   // sub-DFT threads per warp
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cs = lane % CS, col = cs % CW, sig = cs / CW;
+  const int t = w * TPW + lane / CS;
+  const int tr = tm >> VS, par = tm & ((1 << VS) - 1);
+  const int sky = tr / A.nspin, spin = tr - sky * A.nspin;
+  const int n2 = tile * CW + col;
+  const float2 *y = (sig ? A.yb : A.ya) + sky * A.sky_stride;
+  const float2 *qq = A.qq + sky * A.sky_stride;
+  const df32 f1 = df_from_double(A.f1[spin]);
+  const int n1max = A.n1max;
+  const int64_t N2 = A.N2;
+
+  float2 v[Q];
+  // load y_j and the chirp exp(-2 pi i f1 Q_j); the two signal lanes of a
+  // column share the chirp: each computes every other one and swaps.  All
+  // loads of a b-slot are issued before any of them is used.
+  sfor<0, S>([&](auto s) {
+    const int b = t + P * s;
+    float2 qv[AM / 2];
+    sfor<0, AM / 2>([&](auto ap) {
+      const int my = Q * (2 * ap + sig) + b;
+      qv[ap] = (my < n1max) ? qq[my * N2 + n2] : make_float2(0.f, 0.f);
+    });
+    sfor<0, P>([&](auto a) {
+      const int na = Q * a + b;
+      if constexpr (a < AM) v[s * P + a] = (na < n1max) ? y[na * N2 + n2] : make_float2(0.f, 0.f);
+      else v[s * P + a] = make_float2(0.f, 0.f);
+    });
+    sfor<0, AM / 2>([&](auto ap) {
+      constexpr int a0 = 2 * ap, a1 = 2 * ap + 1;
+      const int my = Q * (a0 + sig) + b;
+      float2 cm = make_float2(0.f, 0.f);
+      if (my < n1max) {
+        float f = df_mul_frac(f1, df32{qv[ap].x, qv[ap].y});
+        if (VS > 0 && par) {  // sub-transform shift: exact fraction (j < 2^24)
+          f += (float)(par * (my * N2 + n2)) * A.inv_nfft_total;
+          f -= rintf(f);
+        }
+        cm = chirp_cycles(f);
+      }
+      float2 cp;
+      cp.x = __shfl_xor_sync(kFull, cm.x, CW);
+      cp.y = __shfl_xor_sync(kFull, cm.y, CW);
+      const float2 c0 = sig ? cp : cm, c1 = sig ? cm : cp;
+      v[s * P + a0] = cmul(v[s * P + a0], c0);
+      v[s * P + a1] = cmul(v[s * P + a1], c1);
+    });
+  });
+  sfor<0, S>([&](auto s) {
+    const int b = t + P * s;
+    dft_inplace<P, AM>(v + s * P);
+    sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twL[(b * c) & (L - 1)]); });
+    sfor<0, P>([&](auto c) { xch[(b * P + c) * CS + cs] = v[s * P + c]; });
+  });
+  __syncthreads();
+  sfor<0, Q>([&](auto bb) { v[bb] = xch[(bb * P + t) * CS + cs]; });
+  dft_inplace<Q>(v);  // v[d] = X[k1 = t + P d] of column n2
+  // inter-pass twiddle exp(-2 pi i n2 k1 / Nfft): anchors every 16 d from the
+  // hardware sine/cosine (argument reduced to half a turn), and an exactly
+  // rounded step for the recurrence between anchors so errors do not build up
+  const int64_t nf = A.nfft;
+  const float inv_nf = 1.0f / (float)nf;
+  const float2 step = expm2pi((float)(((int64_t)n2 * P) & (nf - 1)) * inv_nf);
+  float2 wt = make_float2(1.f, 0.f);
+  sfor<0, Q>([&](auto d) {
+    if constexpr (d % 16 == 0) {
+      const float f = (float)(((int64_t)n2 * (t + P * d)) & (nf - 1)) * inv_nf;
+      wt = chirp_cycles(f > 0.5f ? f - 1.0f : f);
+    } else {
+      wt = cmul(wt, step);
+    }
+    v[d] = cmul(v[d], wt);
+  });
+  float2 *Zs = A.Z + ((int64_t)zs * 2 + sig) * nf;
+  sfor<0, Q>([&](auto d) { Zs[(int64_t)(t + P * d) * N2 + n2] = v[d]; });
+}
+
+template <int P, int Q, int CW, int AM, int VS>
+__global__ void __launch_bounds__(P * 2 * CW, 2) k_pass1(Pass1Args A) {
+  constexpr int L = P * Q;
+  extern __shared__ float2 smem[];
+  float2 *xch = smem;               // [Q][P][2 CW]
+  float2 *twL = smem + L * 2 * CW;  // W_L^q
+  const int tiles = A.N2 / CW;
+  const int bt = blockIdx.x / tiles, tile = blockIdx.x - bt * tiles;
+  for (int q = threadIdx.x; q < L; q += blockDim.x) twL[q] = expm2pi((float)q * (1.0f / L));
+  __syncthreads();
+  pass1_item<P, Q, CW, AM, VS>(A, A.tmpl0 + bt, bt, tile, xch, twL);
+}
+
+// ------------------------------------------------------------------ pass 2 + F epilogue
+struct Pass2Args {
+  const float2 *Z;
+  int N1, N2;
+  int64_t nfft;
+  const float2 *norm;  // per sky of the group
+  int nspin, tmpl0;
+  int vshift;          // sub-transforms per template (see Pass1Args)
+  int sky_base;        // global index of the group's first sky
+  float *F;            // NULL or F_out + (global template of the group's first template) * nbins
+  int64_t nbins;       // F row length of one template (all its sub-transforms)
+  float thr;
+  fs_candidate *cand;
+  int64_t cap;
+  unsigned long long *ncand;
+  uint32_t *flags;
+};
+
+// One pass-2 work item: template tm (within the group), row tile rt, reading Z
+// slot zs.  Needs 32 * WARPS threads; work holds the exchange and F tile areas
+// (pass2_work_floats2), twM the matrix W_L^{b c} stored by c then b.  Z is read
+// past L1 (it may have been rewritten since an earlier item on this SM).
+// Exchange layout of one sub-DFT: element (c, b) at c * PITCH + col(c, b).  For
+// 16- and 32-thread sub-DFTs the row pitch is Q and the column is XOR-swizzled
+// by c (conflict-free, no padding); otherwise rows are padded to Q + 1.
+template <int P, int Q>
+struct Xch2 {
+  static constexpr bool SWZ = (P >= 16);
+  static constexpr int PITCH = SWZ ? Q : Q + 1;
+  static constexpr int SIZE = P * PITCH;
+  static __device__ __forceinline__ int at(int c, int b) { return c * PITCH + (SWZ ? (b ^ (c & 15)) : b); }
+};
+
+// Pass-2 work item for 32-thread row DFTs (N2 = 1024): a warp holds one signal of
+// one row (warps 2r, 2r+1: signals a, b of row r), so an item covers WARPS/2
+// rows; the two signals' |X|^2 terms meet through the F tile.
+template <int Q, int WARPS, bool FULLBINS, int VS>
+__device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
+                                                const float2 *twM) {
+  constexpr int P = 32, R = WARPS / 2, S = Q / P;
+  constexpr int D = FULLBINS ? Q : Q / 2;
+  using X = Xch2<P, Q>;
+  constexpr int XW = X::SIZE;
+  constexpr int K2 = D * P;
+  float *Fs = (float *)work;  // [K2][R + 1], aliased over the exchange area
+  const int t = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int sig = w & 1, row = w >> 1;
+  const int k1 = rt * R + row;
+  const int tr = tm >> VS, par = tm & ((1 << VS) - 1);
+  const int sky = tr / A.nspin, spin = tr - sky * A.nspin;
+  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * A.nfft + (int64_t)k1 * A.N2;
+  float2 v[Q];
+  sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = __ldcg(z + Q * a + t + P * s); }); });
+  float2 *xw = work + w * XW;
+  sfor<0, S>([&](auto s) {
+    const int b = t + P * s;
+    dft_inplace<P>(v + s * P);
+    sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twM[c * Q + b]); });
+    sfor<0, P>([&](auto c) { xw[X::at(c, b)] = v[s * P + c]; });
+  });
+  __syncwarp();
+  sfor<0, Q>([&](auto bb) { v[bb] = xw[X::at(t, bb)]; });
+  __syncthreads();  // every warp is done with the exchange area (reused for the F tile)
+  dft_inplace<Q, Q, D>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)
+  const float2 nrm = A.norm[sky];
+  if (sig == 0) {
+    sfor<0, D>([&](auto d) { Fs[(t + P * d) * (R + 1) + row] = fmaf(v[d].x, v[d].x, v[d].y * v[d].y) * nrm.x; });
+  }
+  __syncthreads();
+  const unsigned lt_mask = (1u << t) - 1u;
+  if (sig == 1) {
+    sfor<0, D>([&](auto d) {
+      const int k2 = t + P * d;
+      float *fp = Fs + k2 * (R + 1) + row;
+      const float Fv = *fp + fmaf(v[d].x, v[d].x, v[d].y * v[d].y) * nrm.y;
+      *fp = Fv;
+      const bool hit = Fv > A.thr;
+      const unsigned m = __ballot_sync(kFull, hit);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (t == leader) base = atomicAdd(A.ncand, (unsigned long long)__popc(m));
+        base = __shfl_sync(kFull, base, leader);
+        if (hit) {
+          const unsigned long long idx = base + __popc(m & lt_mask);
+          if ((long long)idx < A.cap) {
+            fs_candidate c;
+            c.sky = (uint32_t)(A.sky_base + sky);
+            c.spin = (uint32_t)spin;
+            c.bin = (uint32_t)(((k1 + A.N1 * k2) << VS) + par);
+            c.F = Fv;
+            A.cand[idx] = c;
+          } else {
+            atomicOr(A.flags, ERRF_CAPACITY);
+          }
+        }
+      }
+    });
+  }
+  if (A.F == nullptr) return;
+  __syncthreads();
+  // VS = 0: template row plus the item's first row; VS > 0: interleaved sub-transform bins
+  float *Fo = VS == 0 ? A.F + (int64_t)tm * A.nbins + rt * R : A.F + (int64_t)tr * A.nbins + par;
+  for (int idx = threadIdx.x; idx < K2 * R; idx += blockDim.x) {
+    const int k2 = idx / R, r = idx - k2 * R;
+    if constexpr (VS == 0) __stcs(Fo + r + (int64_t)A.N1 * k2, Fs[k2 * (R + 1) + r]);
+    else __stcs(Fo + ((rt * R + r + (int64_t)A.N1 * k2) << VS), Fs[k2 * (R + 1) + r]);
+  }
+}
+
+// ALIAS_F: the F tile reuses the exchange area (one more barrier, less shared memory).
+template <int P, int Q, int WARPS, bool FULLBINS, bool ALIAS_F = false, int VS = 0>
+__device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
+                                           const float2 *twM) {
+  if constexpr (P == 32) {
+    pass2_item_wide<Q, WARPS, FULLBINS, VS>(A, tm, zs, rt, work, twM);
+    return;
+  }
+  constexpr int T = P, G = (P <= 16 ? 16 / P : 1), R = WARPS * G, S = Q / P;
+  constexpr int D = FULLBINS ? Q : Q / 2;  // d values with k2 = t + P d in the output band
+  using X = Xch2<P, Q>;
+  constexpr int XW = X::SIZE;              // exchange float2s per sub-DFT
+  float *Fs = (float *)(ALIAS_F ? work : work + WARPS * 2 * G * XW);  // [D*P][R+1]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = lane % T, sig = (lane / T) & 1, gr = lane / (2 * T);
+  const int row = w * G + gr;
+  const int k1 = rt * R + row;
+  const int tr = tm >> VS, par = tm & ((1 << VS) - 1);
+  const int sky = tr / A.nspin, spin = tr - sky * A.nspin;
+  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * A.nfft + (int64_t)k1 * A.N2;
+  float2 v[Q];
+  sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = __ldcg(z + Q * a + t + P * s); }); });
+  float2 *xw = work + (w * 2 * G + (sig + 2 * gr)) * XW;
+  sfor<0, S>([&](auto s) {
+    const int b = t + P * s;
+    dft_inplace<P>(v + s * P);
+    // W_L^{b c} stored by c then b: lanes read consecutive entries (no bank conflicts)
+    sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twM[c * Q + b]); });
+    sfor<0, P>([&](auto c) { xw[X::at(c, b)] = v[s * P + c]; });
+  });
+  __syncwarp();
+  sfor<0, Q>([&](auto bb) { v[bb] = xw[X::at(t, bb)]; });
+  if constexpr (ALIAS_F) __syncthreads();  // every warp is done with the exchange area
+  dft_inplace<Q, Q, (FULLBINS ? Q : Q / 2)>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)
+  const float2 nrm = A.norm[sky];
+  const float myn = sig ? nrm.y : nrm.x;
+  float p[D];
+  sfor<0, D>([&](auto d) { p[d] = fmaf(v[d].x, v[d].x, v[d].y * v[d].y) * myn; });
+  const unsigned lt_mask = (1u << lane) - 1u;
+  sfor<0, D / 2>([&](auto dp) {
+    const float send = sig ? p[dp] : p[dp + D / 2];
+    const float mine = sig ? p[dp + D / 2] : p[dp];
+    const float Fv = mine + __shfl_xor_sync(kFull, send, T);
+    const int d = dp + sig * (D / 2);
+    const int k2 = t + P * d;
+    Fs[k2 * (R + 1) + row] = Fv;
+    const bool hit = Fv > A.thr;
+    const unsigned m = __ballot_sync(kFull, hit);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(A.ncand, (unsigned long long)__popc(m));
+      base = __shfl_sync(kFull, base, leader);
+      if (hit) {
+        const unsigned long long idx = base + __popc(m & lt_mask);
+        if ((long long)idx < A.cap) {
+          fs_candidate c;
+          c.sky = (uint32_t)(A.sky_base + sky);
+          c.spin = (uint32_t)spin;
+          c.bin = (uint32_t)(((k1 + A.N1 * k2) << VS) + par);
+          c.F = Fv;
+          A.cand[idx] = c;
+        } else {
+          atomicOr(A.flags, ERRF_CAPACITY);
+        }
+      }
+    }
+  });
+  if (A.F == nullptr) return;
+  __syncthreads();
+  // VS = 0: template row plus the item's first row; VS > 0: interleaved sub-transform bins
+  float *Fo = VS == 0 ? A.F + (int64_t)tm * A.nbins + rt * R : A.F + (int64_t)tr * A.nbins + par;
+  constexpr int K2 = D * P;
+  for (int idx = threadIdx.x; idx < K2 * R; idx += blockDim.x) {
+    const int k2 = idx / R, r = idx - k2 * R;
+    if constexpr (VS == 0) __stcs(Fo + r + (int64_t)A.N1 * k2, Fs[k2 * (R + 1) + r]);
+    else __stcs(Fo + ((rt * R + r + (int64_t)A.N1 * k2) << VS), Fs[k2 * (R + 1) + r]);
+  }
+}
+
+template <int P, int Q, int WARPS, bool FULLBINS, bool ALIAS_F = false>
+constexpr size_t pass2_work_floats2() {
+  constexpr int G = P <= 16 ? 16 / P : 1;
+  constexpr int R = P <= 16 ? WARPS * G : WARPS / 2, D = FULLBINS ? Q : Q / 2;
+  constexpr size_t xch = P <= 16 ? (size_t)WARPS * 2 * G * Xch2<P, Q>::SIZE : (size_t)WARPS * Xch2<P, Q>::SIZE;
+  constexpr size_t ftile = ((size_t)D * P * (R + 1) + 1) / 2;
+  return (ALIAS_F || P == 32) ? (xch > ftile ? xch : ftile) : xch + ftile;
+}
+
+__device__ __forceinline__ void twiddle_matrix(float2 *twM, int P, int Q) {
+  const int L = P * Q;
+  for (int q = threadIdx.x; q < L; q += blockDim.x) {
+    const int c = q / Q, b = q - c * Q;
+    twM[q] = expm2pi((float)((b * c) & (L - 1)) * (1.0f / L));
+  }
+}
+
+template <int P, int Q, int WARPS, bool FULLBINS, int VS>
+__global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
+  constexpr int R = P <= 16 ? WARPS * (16 / P) : WARPS / 2;
+  extern __shared__ float2 smem[];
+  float2 *twM = smem;
+  float2 *work = smem + P * Q;
+  const int rtiles = A.N1 / R;
+  const int bt = blockIdx.x / rtiles, rt = blockIdx.x - bt * rtiles;
+  twiddle_matrix(twM, P, Q);
+  __syncthreads();
+  pass2_item<P, Q, WARPS, FULLBINS, false, VS>(A, A.tmpl0 + bt, bt, rt, work, twM);
+}
+
+// ------------------------------------------------------------------ persistent pass kernel
+// One launch runs both passes for every template of a sky group from a work
+// queue.  Round r holds the pass-1 items of template r and the pass-2 items of
+// template r - lag.  A pass-2 item waits until all pass-1 items of its template
+// have completed; a pass-1 item of template t waits until the pass-2 items of
+// template t - slots (the previous user of its Z slot) have completed.  Items
+// are taken in queue order, so every wait is on earlier items held by running
+// CTAs.  Waits are bounded: on exhaustion the kernel latches ERRF_TIMEOUT and
+// continues (results are then invalid, the device stays responsive).
+struct QueueArgs {
+  int ntm, tiles1, tiles2, lag, slots;
+  int kr;             // templates per round: a round holds the pass-1 items of kr templates,
+                      // then the pass-2 items of the kr templates lag rounds earlier
+  unsigned *counter;  // [1 + 2 ntm]: next item, pass-1 done per template, pass-2 done per template
+};
+
+constexpr long kSpinLimit = 20000000;  // ~100 ns per poll: a few seconds at most
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Called by one thread: wait until *p >= target (bounded).
+__device__ inline void wait_at_least(const unsigned *p, unsigned target, uint32_t *flags) {
+  for (long it = 0; ld_acquire(p) < target; it++) {
+    if (it > kSpinLimit) {
+      atomicOr(flags, ERRF_TIMEOUT);
+      return;
+    }
+    __nanosleep(100);
+  }
+}
+
+template <int P1, int Q1, int AM, int P2, int Q2, int NT, int MINB, int VS>
+__global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2, QueueArgs Qa) {
+  constexpr int CW = NT / (2 * P1);
+  constexpr int L1 = P1 * Q1, L2 = P2 * Q2;
+  extern __shared__ float2 smem[];
+  float2 *twL = smem;            // W_{L1}^q
+  float2 *twM = smem + L1;       // W_{L2}^{b c} by c then b
+  float2 *work = smem + L1 + L2; // union of the pass-1 exchange and the pass-2 work areas
+  for (int q = threadIdx.x; q < L1; q += blockDim.x) twL[q] = expm2pi((float)q * (1.0f / L1));
+  twiddle_matrix(twM, P2, Q2);
+  unsigned *next = Qa.counter;
+  unsigned *done1 = Qa.counter + 1;
+  unsigned *done2 = Qa.counter + 1 + Qa.ntm;
+  const int kr = Qa.kr;
+  const int ipr = kr * (Qa.tiles1 + Qa.tiles2);
+  const int total = ((Qa.ntm + kr - 1) / kr + Qa.lag) * ipr;
+  // Items are decoded identically by every thread; thread 0 takes the next item
+  // from the queue while the current one runs, checks whether the next item's
+  // dependency is already met, and publishes both through ping-pong slots before
+  // the end-of-item barrier (the slot it writes was last read before the previous
+  // end-of-item barrier).  A ready item then needs no extra barrier.
+  struct Item {
+    int tm, j;
+    bool is1, valid;
+  };
+  auto decode = [&](int it) {
+    Item d;
+    const int r = it / ipr;
+    const int jr = it - r * ipr;
+    d.is1 = jr < kr * Qa.tiles1;
+    if (d.is1) {
+      const int k = jr / Qa.tiles1;
+      d.j = jr - k * Qa.tiles1;
+      d.tm = r * kr + k;
+    } else {
+      const int j2 = jr - kr * Qa.tiles1;
+      const int k = j2 / Qa.tiles2;
+      d.j = Qa.tiles1 + (j2 - k * Qa.tiles2);
+      d.tm = (r - Qa.lag) * kr + k;
+    }
+    d.valid = it < total && d.tm >= 0 && d.tm < Qa.ntm;
+    return d;
+  };
+  auto dep_met = [&](const Item &d) {  // thread 0 only
+    if (!d.valid) return true;
+    if (d.is1) return d.tm < Qa.slots || ld_acquire(done2 + (d.tm - Qa.slots)) >= (unsigned)Qa.tiles2;
+    return ld_acquire(done1 + d.tm) >= (unsigned)Qa.tiles1;
+  };
+  __shared__ int s_next[2], s_ready[2];
+  if (threadIdx.x == 0) {
+    s_next[0] = (int)atomicAdd(next, 1u);
+    s_ready[0] = 0;
+  }
+  __syncthreads();
+  int buf = 0;
+  int cur = s_next[0], ready = s_ready[0];
+  while (cur < total) {
+    int nxt = 0;
+    if (threadIdx.x == 0) nxt = (int)atomicAdd(next, 1u);
+    const Item d = decode(cur);
+    if (d.valid) {
+      if (!ready) {
+        if (threadIdx.x == 0) {
+          if (d.is1) {
+            if (d.tm >= Qa.slots) wait_at_least(done2 + (d.tm - Qa.slots), Qa.tiles2, A2.flags);
+          } else {
+            wait_at_least(done1 + d.tm, Qa.tiles1, A2.flags);
+          }
+        }
+        __syncthreads();
+      }
+      if (d.is1) pass1_item<P1, Q1, CW, AM, VS>(A1, d.tm, d.tm % Qa.slots, d.j, work, twL);
+      else pass2_item<P2, Q2, NT / 32, false, true, VS>(A2, d.tm, d.tm % Qa.slots, d.j - Qa.tiles1, work, twM);
+    }
+    if (threadIdx.x == 0) {
+      s_next[buf ^ 1] = nxt;
+      s_ready[buf ^ 1] = dep_met(decode(nxt)) ? 1 : 0;
+    }
+    __syncthreads();  // item complete: global writes done, shared memory free, next item published
+    if (threadIdx.x == 0 && d.valid) red_release_add((d.is1 ? done1 : done2) + d.tm, 1u);
+    buf ^= 1;
+    cur = s_next[buf];
+    ready = s_ready[buf];
+  }
+}
+
+// ------------------------------------------------------------------ launch templates
+constexpr int kPass2Warps = 8;  // warps per pass-2 CTA
+
+template <int P, int Q>
+static size_t pass1_smem() { return sizeof(float2) * ((size_t)P * Q * 2 * (256 / (2 * P)) + (size_t)P * Q); }
+template <int P, int Q, bool FULL>
+static size_t pass2_smem() {
+  return sizeof(float2) * ((size_t)P * Q + pass2_work_floats2<P, Q, kPass2Warps, FULL>());
+}
+
+template <int P, int Q, int VS = 0>
+static cudaError_t launch_pass1(const Pass1Args &a, int nb, cudaStream_t st) {
+  size_t sm = pass1_smem<P, Q>();
+  constexpr int CW = 256 / (2 * P);
+  auto kern = (a.n1max <= P * Q / 2) ? k_pass1<P, Q, CW, P / 2, VS> : k_pass1<P, Q, CW, P, VS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  kern<<<nb * (a.N2 / CW), P * 2 * CW, sm, st>>>(a);
+  return cudaGetLastError();
+}
+template <int P, int Q, bool FULL, int VS = 0>
+static cudaError_t launch_pass2(const Pass2Args &a, int nb, cudaStream_t st) {
+  size_t sm = pass2_smem<P, Q, FULL>();
+  auto kern = k_pass2<P, Q, kPass2Warps, FULL, VS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  constexpr int R = P <= 16 ? kPass2Warps * (16 / P) : kPass2Warps / 2;
+  kern<<<nb * (a.N1 / R), 32 * kPass2Warps, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Persistent pass kernel: shapes (N1 x N2) -> (P1, Q1, P2, Q2), pruning AM.
+#ifndef FS_PERSIST_MINB
+#define FS_PERSIST_MINB 3
+#endif
+constexpr int kPersistMinBlocks = FS_PERSIST_MINB;  // CTAs per SM the kernel is compiled for
+
+template <int P1, int Q1, int P2, int Q2, int NT>
+constexpr size_t persist_smem() {
+  constexpr int CW = NT / (2 * P1);
+  constexpr size_t w1 = (size_t)P1 * Q1 * 2 * CW;
+  constexpr size_t w2 = pass2_work_floats2<P2, Q2, NT / 32, false, true>();
+  return sizeof(float2) * ((size_t)P1 * Q1 + (size_t)P2 * Q2 + (w1 > w2 ? w1 : w2));
+}
+// CTAs per SM the kernel is compiled for: 3 when three fit in shared memory.
+template <int P1, int Q1, int P2, int Q2, int NT>
+constexpr int persist_minb() { return persist_smem<P1, Q1, P2, Q2, NT>() <= 74 * 1024 ? kPersistMinBlocks : 2; }
+
+template <int P1, int Q1, int AM, int P2, int Q2, int NT, int VS>
+static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
+  constexpr int MINB = persist_minb<P1, Q1, P2, Q2, NT>();
+  const size_t sm = persist_smem<P1, Q1, P2, Q2, NT>();
+  auto kern = k_passes<P1, Q1, AM, P2, Q2, NT, MINB, VS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, sm);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  const long total = (long)((qa.ntm + qa.kr - 1) / qa.kr + qa.lag) * qa.kr * (qa.tiles1 + qa.tiles2);
+  long grid = (long)occ * nsm;
+  if (grid > total) grid = total;
+  kern<<<(unsigned)grid, NT, sm, st>>>(a1, a2, qa);
+  return cudaGetLastError();
+}
+
+// VS: sub-transforms per template (2^VS) compiled in; only the 2^20 split is
+// built with VS = 1 (the 2^21 transform).
+template <int P1, int Q1, int P2, int Q2, int NT, int VS = 0>
+static cudaError_t launch_passes_am(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
+  if (a1.vshift != VS) return cudaErrorInvalidValue;
+  if (a1.n1max <= P1 * Q1 / 2) return launch_passes_t<P1, Q1, P1 / 2, P2, Q2, NT, VS>(a1, a2, qa, st);
+  return launch_passes_t<P1, Q1, P1, P2, Q2, NT, VS>(a1, a2, qa, st);
+}
+
+// Work-item geometry of the persistent kernel for NT threads per CTA.
+static inline void queue_tiles(int N1, int N2, int NT, int *tiles1, int *tiles2) {
+  const int P1 = N1 <= 128 ? 8 : (N1 <= 512 ? 16 : 32);
+  const int P2 = N2 <= 128 ? 8 : (N2 <= 512 ? 16 : 32);
+  *tiles1 = N2 / (NT / (2 * P1));
+  *tiles2 = N1 / (P2 <= 16 ? (NT / 32) * (16 / P2) : (NT / 32) / 2);
+}
+
+// 256 threads (2 CTAs per SM): measured faster than 128 threads with half-size items.
+constexpr int kPersistThreads = 256;
+
+// Per-shape dispatch, one translation unit per group of shapes.
+cudaError_t dispatch_pass1(int N1, const Pass1Args &a, int nb, cudaStream_t st);
+cudaError_t dispatch_pass2(int N2, bool full, const Pass2Args &a, int nb, cudaStream_t st);
+// Persistent launch for an N1 x N2 split; cudaErrorInvalidValue for a split
+// this build does not instantiate (split_instantiated is false).
+cudaError_t dispatch_passes(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
+                            cudaStream_t st);
+cudaError_t dispatch_passes_small(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
+                                  cudaStream_t st);
+cudaError_t dispatch_passes_mid(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
+                                cudaStream_t st);
+cudaError_t dispatch_passes_large(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
+                                  cudaStream_t st);
+bool split_instantiated(int N1, int N2);
+// CTAs per SM the persistent kernel of a split is compiled for (0: not instantiated).
+int passes_blocks_per_sm(int N1, int N2);
+int passes_blocks_per_sm_small(int N1, int N2);
+int passes_blocks_per_sm_mid(int N1, int N2);
+int passes_blocks_per_sm_large(int N1, int N2);
+
+// ------------------------------------------------------------------ host-side configuration
+struct FftShape {
+  int N1, N2;
+};
+// Shape of the persistent queue: templates per round, lag (rounds) and Z slots.
+struct QueueShape {
+  int kr, lag, slots, tiles1, tiles2;
+};
+// Resolved launch configuration of one FP32 search of one segment.
+struct Cfg32 {
+  FftShape sh;     // split of the sub-transform
+  int vshift;      // 2^vshift sub-transforms per template
+  int64_t nsub;    // sub-transform length N1 N2
+  int n1max;       // rows n1 that hold data
+  int64_t npad;    // n1max N2: per-sky series length
+  int G;           // skies per group
+  bool full;       // F on all Nfft bins (per-batch launches)
+  bool persistent; // both passes from one work queue
+  QueueShape qs;
+  int B;           // Z slots of the workspace
+};
+struct Ws32 {
+  SkyConst32 *skyc;
+  float2 *ya, *yb, *qq, *norm;
+  double2 *ab2;
+  double *partial;
+  float2 *Z;
+  unsigned *counters;
+  int64_t stride;
+  int nblk_a1;
+};
+fs_status config32(const fs_ctx *ctx, const fs_seg *seg, int nsky, int64_t nbins, Cfg32 *c);
+// Lay out (and, if may_alloc, grow) context workspace `slot` for a search.
+fs_status workspace32(fs_ctx *ctx, int slot, const fs_seg *seg, const Cfg32 &c, int nsky, int nspin,
+                      bool may_alloc, cudaStream_t st, Ws32 *w);
+// Enqueue one search on `st` with a laid-out workspace; allocates nothing.
+fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, const double *alpha,
+                       const double *delta, int nsky, const double *f1, int nspin, float thr, float *F,
+                       int64_t nbins, fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st);
+
+}  // namespace fs

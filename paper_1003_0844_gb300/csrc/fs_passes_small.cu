@@ -1,0 +1,37 @@
+// Persistent transform launches for Nfft = 2^12 .. 2^16.
+#include "fs_pass32.cuh"
+
+namespace fs {
+
+cudaError_t dispatch_passes_small(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
+                                cudaStream_t st) {
+  constexpr int NT = kPersistThreads;
+  switch (N1 * 4096 + N2) {
+    case 64 * 4096 + 64: return launch_passes_am<8, 8, 8, 8, NT>(a1, a2, qa, st);
+    case 128 * 4096 + 64: return launch_passes_am<8, 16, 8, 8, NT>(a1, a2, qa, st);
+    case 128 * 4096 + 128: return launch_passes_am<8, 16, 8, 16, NT>(a1, a2, qa, st);
+    case 256 * 4096 + 64: return launch_passes_am<16, 16, 8, 8, NT>(a1, a2, qa, st);
+    case 256 * 4096 + 128: return launch_passes_am<16, 16, 8, 16, NT>(a1, a2, qa, st);
+    case 256 * 4096 + 256: return launch_passes_am<16, 16, 16, 16, NT>(a1, a2, qa, st);
+    case 512 * 4096 + 128: return launch_passes_am<16, 32, 8, 16, NT>(a1, a2, qa, st);
+    case 128 * 4096 + 512: return launch_passes_am<8, 16, 16, 32, NT>(a1, a2, qa, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int passes_blocks_per_sm_small(int N1, int N2) {
+  constexpr int NT = kPersistThreads;
+  switch (N1 * 4096 + N2) {
+    case 64 * 4096 + 64: return persist_minb<8, 8, 8, 8, NT>();
+    case 128 * 4096 + 64: return persist_minb<8, 16, 8, 8, NT>();
+    case 128 * 4096 + 128: return persist_minb<8, 16, 8, 16, NT>();
+    case 256 * 4096 + 64: return persist_minb<16, 16, 8, 8, NT>();
+    case 256 * 4096 + 128: return persist_minb<16, 16, 8, 16, NT>();
+    case 256 * 4096 + 256: return persist_minb<16, 16, 16, 16, NT>();
+    case 512 * 4096 + 128: return persist_minb<16, 32, 8, 16, NT>();
+    case 128 * 4096 + 512: return persist_minb<8, 16, 16, 32, NT>();
+  }
+  return 0;
+}
+
+}  // namespace fs

@@ -399,8 +399,8 @@ __global__ void k_inject_add(double *x, const double *h, const double *partial, 
   if (k < n) x[k] += h[k] * scale;
 }
 
-fs_status inject64(fs_ctx *ctx, double *x, int64_t n, double dt, double fl, double sigma,
-                   const fs_injection *inj, int n_inj, cudaStream_t st) {
+fs_status inject64(fs_ctx *ctx, double *x, int64_t n, double dt, double fl, double sigma, double theta0,
+                   double lambda0, const fs_injection *inj, int n_inj, cudaStream_t st) {
   int nb = (int)nblk(n);
   size_t need = sizeof(double) * ((size_t)n + (size_t)nb);
   fs_status s = ensure_buffer(&ctx->scratch, &ctx->scratch_bytes, need, st);
@@ -411,8 +411,8 @@ fs_status inject64(fs_ctx *ctx, double *x, int64_t n, double dt, double fl, doub
   g.n = n;
   g.dt = dt;
   g.fl = fl;
-  g.theta0 = ctx->det.theta_g0 + ctx->det.lon;
-  g.lambda0 = ctx->det.lambda_e0;
+  g.theta0 = theta0;
+  g.lambda0 = lambda0;
   double re, z;
   site_radius(ctx->det.lat, &re, &z);
   g.re_c = re / kC;

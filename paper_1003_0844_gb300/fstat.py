@@ -11,6 +11,7 @@ import ctypes
 import dataclasses
 import math
 import os
+import weakref
 
 import torch
 
@@ -24,7 +25,7 @@ PREC = {"f32": 0, "f64": 1}
 INTERP = {"spline": 0, "nearest": 1}
 EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_seg_destroy", "fs_seg_load", "fs_search",
            "fs_sync_status", "fs_strerror", "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling",
-           "fs_get_stats", "fs_search_noalloc"]
+           "fs_get_stats", "fs_search_noalloc", "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune"]
 PROF_KINDS = ("prepare", "demodulate", "pass1", "pass2", "other")
 
 
@@ -42,7 +43,12 @@ class _Detector(ctypes.Structure):
 class _SegDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nfft", ctypes.c_int64), ("dt", ctypes.c_double), ("fl", ctypes.c_double),
                 ("S0", ctypes.c_double), ("precision", ctypes.c_int32), ("interp", ctypes.c_int32),
-                ("x_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("x_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32), ("t0", ctypes.c_double)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int32), ("queue_round", ctypes.c_int32), ("queue_lag", ctypes.c_int32),
+                ("group_skies", ctypes.c_int32), ("ms_per_template", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -83,9 +89,14 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.fs_strerror.restype = ctypes.c_char_p
     lib.fs_seg_upsampled.argtypes = [vp, vp, vp]
     lib.fs_demodulate.argtypes = [vp, vp, f64, f64, vp, vp, vp, vp, vp]
-    lib.fs_inject.argtypes = [vp, vp, i64, f64, f64, f64, ctypes.POINTER(_Injection), i32, vp]
+    lib.fs_inject.argtypes = [vp, vp, i64, f64, f64, f64, f64, ctypes.POINTER(_Injection), i32, vp]
+    lib.fs_search_batch.argtypes = [vp, ctypes.POINTER(vp), i32, vp, vp, i32, vp, i32, f32, vp, i64, vp, vp]
+    lib.fs_set_tuning.argtypes = [vp, i64, ctypes.POINTER(_Tuning)]
+    lib.fs_get_tuning.argtypes = [vp, i64, ctypes.POINTER(_Tuning)]
+    lib.fs_autotune.argtypes = [vp, vp, vp, vp, i32, vp, i32, i32, ctypes.POINTER(_Tuning), vp]
     for name in ("fs_create", "fs_prepare_segment", "fs_seg_load", "fs_search", "fs_search_noalloc", "fs_sync_status",
-                 "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling", "fs_get_stats"):
+                 "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling", "fs_get_stats",
+                 "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -125,9 +136,13 @@ class Context:
         _check(self.lib.fs_create(ctypes.byref(h), ctypes.byref(d), int(device)), "fs_create")
         self.handle = h
         self.device = device
+        self._segments = weakref.WeakSet()
 
     def close(self):
+        """Release the context; fs_destroy also releases its segments still alive."""
         if self.handle:
+            for sg in list(self._segments):
+                sg.handle = None
             self.lib.fs_destroy(self.handle)
             self.handle = None
 
@@ -154,12 +169,43 @@ class Context:
                 "ms": {k: st.ms[i] for i, k in enumerate(PROF_KINDS)},
                 "count": {k: st.count[i] for i, k in enumerate(PROF_KINDS)}}
 
+    def set_tuning(self, nfft: int, n1: int = 0, queue_round: int = 0, queue_lag: int = 0, group_skies: int = 0):
+        """Launch configuration for transforms of length nfft (fs_set_tuning)."""
+        t = _Tuning(int(n1), int(queue_round), int(queue_lag), int(group_skies), 0.0, 0)
+        _check(self.lib.fs_set_tuning(self.handle, int(nfft), ctypes.byref(t)), "fs_set_tuning")
+
+    def clear_tuning(self, nfft: int):
+        _check(self.lib.fs_set_tuning(self.handle, int(nfft), None), "fs_set_tuning")
+
+    def get_tuning(self, nfft: int) -> dict | None:
+        t = _Tuning()
+        st = self.lib.fs_get_tuning(self.handle, int(nfft), ctypes.byref(t))
+        if st == 7:
+            return None
+        _check(st, "fs_get_tuning")
+        return _tuning_dict(t)
+
+    def autotune(self, seg: "Segment", alpha: torch.Tensor, delta: torch.Tensor, f1: torch.Tensor, reps: int = 3,
+                 stream=None) -> dict:
+        """Time the candidate configurations on this grid and keep the fastest (fs_autotune)."""
+        for t, nm in ((alpha, "alpha"), (delta, "delta"), (f1, "f1")):
+            _need_cuda(t, nm, torch.float64)
+        out = _Tuning()
+        _check(self.lib.fs_autotune(self.handle, seg.handle, _ptr(alpha), _ptr(delta), alpha.numel(), _ptr(f1),
+                                    f1.numel(), int(reps), ctypes.byref(out), _stream(stream)), "fs_autotune")
+        return _tuning_dict(out)
+
+
+def _tuning_dict(t) -> dict:
+    return {"n1": t.n1, "queue_round": t.queue_round, "queue_lag": t.queue_lag, "group_skies": t.group_skies,
+            "ms_per_template": t.ms_per_template}
+
 
 class Segment:
     """One prepared data segment (fs_prepare_segment): tables, x2 upsampling, spline."""
 
     def __init__(self, ctx: Context, x: torch.Tensor, dt: float, nfft: int, fl: float, S0: float,
-                 precision: str = "f32", interp: str = "spline", stream=None):
+                 precision: str = "f32", interp: str = "spline", t0: float = 0.0, stream=None):
         _need_cuda(x, "x")
         if x.dtype not in (torch.float32, torch.float64):
             raise ValueError("x must be float32 or float64")
@@ -168,17 +214,20 @@ class Segment:
         self.nfft = int(nfft)
         self.dt, self.fl, self.S0 = float(dt), float(fl), float(S0)
         self.precision = precision
+        self.t0 = float(t0)
         d = _SegDesc(self.n, self.nfft, self.dt, self.fl, self.S0, PREC[precision], INTERP[interp],
-                     0 if x.dtype == torch.float32 else 1, 0)
+                     0 if x.dtype == torch.float32 else 1, 0, self.t0)
         h = ctypes.c_void_p()
         _check(ctx.lib.fs_prepare_segment(ctx.handle, ctypes.byref(h), ctypes.byref(d), _ptr(x), _stream(stream)),
                "fs_prepare_segment")
         self.handle = h
+        ctx._segments.add(self)
 
     def close(self):
-        if self.handle:
+        # a segment whose context is gone was released with it (fs_destroy)
+        if self.handle and self.ctx.handle:
             self.ctx.lib.fs_seg_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -242,6 +291,41 @@ def search(ctx: Context, seg: Segment, alpha: torch.Tensor, delta: torch.Tensor,
     return SearchResult(F_out, cand, n_cand)
 
 
+@dataclasses.dataclass
+class BatchResult:
+    cand: torch.Tensor             # int32 [nseg, cap, 4]: sky, spin, bin, F bits per segment
+    n_cand: torch.Tensor           # int64 [nseg] on the device
+
+    def candidates(self, s: int):
+        """(sky, spin, bin, F) numpy arrays of segment s's stored candidates (synchronises)."""
+        n = min(int(self.n_cand[s].item()), self.cand.shape[1])
+        c = self.cand[s, :n].cpu()
+        F = c[:, 3].view(torch.float32).numpy().copy()
+        u = c[:, :3].numpy().astype("int64")
+        return u[:, 0], u[:, 1], u[:, 2], F
+
+
+def search_batch(ctx: Context, segs, alpha: torch.Tensor, delta: torch.Tensor, f1: torch.Tensor, F_thr: float,
+                 cand_cap: int = 1 << 14, cand: torch.Tensor | None = None, n_cand: torch.Tensor | None = None,
+                 stream=None) -> BatchResult:
+    """fs_search_batch: the same grid over every segment of `segs`, candidates only."""
+    for t, nm in ((alpha, "alpha"), (delta, "delta"), (f1, "f1")):
+        _need_cuda(t, nm, torch.float64)
+    nsky, nspin, nseg = alpha.numel(), f1.numel(), len(segs)
+    if delta.numel() != nsky:
+        raise ValueError("alpha and delta differ in length")
+    if cand is None:
+        cand = torch.empty((nseg, max(cand_cap, 1), 4), dtype=torch.int32, device="cuda")
+    if n_cand is None:
+        n_cand = torch.zeros(nseg, dtype=torch.int64, device="cuda")
+    handles = (ctypes.c_void_p * nseg)(*[sg.handle.value for sg in segs])
+    st = ctx.lib.fs_search_batch(ctx.handle, handles, nseg, _ptr(alpha), _ptr(delta), nsky, _ptr(f1), nspin,
+                                 float(F_thr), _ptr(cand), int(cand.shape[1]) if cand_cap > 0 else 0, _ptr(n_cand),
+                                 _stream(stream))
+    _check(st, "fs_search_batch")
+    return BatchResult(cand, n_cand)
+
+
 def demodulate(ctx: Context, seg: Segment, alpha: float, delta: float, stream=None):
     """Per-sky resampled, demodulated series (fs_demodulate) as device tensors:
     (y^a complex128 [n], y^b complex128 [n], t_src float64 [n], (<a^2>, <b^2>))."""
@@ -255,12 +339,14 @@ def demodulate(ctx: Context, seg: Segment, alpha: float, delta: float, stream=No
     return torch.view_as_complex(ya.view(n, 2)), torch.view_as_complex(yb.view(n, 2)), ts, ab
 
 
-def inject(ctx: Context, x: torch.Tensor, dt: float, fl: float, sigma: float, injections, stream=None):
-    """Add simulated signals (fs_inject) to the float64 CUDA tensor x in place."""
+def inject(ctx: Context, x: torch.Tensor, dt: float, fl: float, sigma: float, injections, t0: float = 0.0,
+           stream=None):
+    """Add simulated signals (fs_inject) to the float64 CUDA tensor x in place; t0 is the
+    epoch of the first sample (as for a Segment)."""
     _need_cuda(x, "x", torch.float64)
     arr = (_Injection * max(len(injections), 1))()
     for i, j in enumerate(injections):
         arr[i] = _Injection(j.f0, j.f1, j.alpha, j.delta, j.psi, j.cos_iota, j.phi0, j.snr)
-    _check(ctx.lib.fs_inject(ctx.handle, _ptr(x), x.numel(), float(dt), float(fl), float(sigma), arr,
+    _check(ctx.lib.fs_inject(ctx.handle, _ptr(x), x.numel(), float(dt), float(fl), float(sigma), float(t0), arr,
                              len(injections), _stream(stream)), "fs_inject")
     return x

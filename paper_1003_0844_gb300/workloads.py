@@ -90,7 +90,67 @@ WORKLOADS = {
 }
 
 
+@dataclasses.dataclass(frozen=True)
+class BatchWorkload:
+    """Many segments of uneven length searched with one template grid (the
+    coherent first stage of a hierarchical search, Sec. I).  `parts` lists
+    (days, nfft, count) per kind of segment; the kinds are interleaved and the
+    segments follow each other in time without gaps."""
+    name: str
+    parts: tuple
+    dt: float
+    nsky: int
+    nspin: int
+    n_inj: int          # injections per segment
+    snr: tuple
+    fl: float = 435.1875
+    f1_range: tuple = (-1e-8, 0.0)
+    f0_range: tuple = (0.05, 0.20)
+    F_thr: float = 20.0
+    sigma: float = 1.0
+
+    def segments(self) -> list:
+        """One Workload per segment (name "<batch>/<index>") in time order."""
+        out = []
+        for c in range(max(p[2] for p in self.parts)):
+            for days, nfft, count in self.parts:
+                if c < count:
+                    out.append(Workload("%s/%d" % (self.name, len(out)), days=days, dt=self.dt, nfft=nfft,
+                                        nsky=self.nsky, nspin=self.nspin, n_inj=self.n_inj, snr=self.snr,
+                                        fl=self.fl, f1_range=self.f1_range, f0_range=self.f0_range,
+                                        F_thr=self.F_thr, sigma=self.sigma))
+        return out
+
+    def epochs(self) -> np.ndarray:
+        """Start time [s] of each segment after the first one's start."""
+        segs = self.segments()
+        t = np.zeros(len(segs))
+        for i in range(1, len(segs)):
+            t[i] = t[i - 1] + segs[i - 1].n * segs[i - 1].dt
+        return t
+
+
+# Batches of uneven segments: 16 each of 1, 2, 3 and 6 sidereal days with
+# transforms of 2^16, 2^18, 2^18 and 2^20 points, 4096 sky x 64 spindowns, and
+# a small one for tests.
+BATCHES = {
+    "uneven_64": BatchWorkload("uneven_64", parts=((1, 1 << 16, 16), (2, 1 << 18, 16), (3, 1 << 18, 16),
+                                                   (6, 1 << 20, 16)),
+                               dt=2.0, nsky=4096, nspin=64, n_inj=1, snr=(10.0, 20.0)),
+    "uneven_small": BatchWorkload("uneven_small", parts=((1, 1 << 12, 2), (2, 1 << 13, 1), (3, 1 << 14, 1)),
+                                  dt=64.0, nsky=3, nspin=2, n_inj=1, snr=(30.0, 30.0), f0_range=(0.001, 0.006),
+                                  F_thr=15.0),
+}
+
+
 def rng_for(workload: str, stream: int = 0) -> np.random.Generator:
+    """Seeded generator of a named workload, or of segment i of a batch ("<batch>/<i>")."""
+    if "/" in workload:
+        batch, i = workload.split("/")
+        idx = 100 + list(BATCHES).index(batch)
+        return np.random.default_rng([BASE_SEED + idx, 1000 + int(i), stream])
+    if workload in BATCHES:
+        return np.random.default_rng([BASE_SEED + 100 + list(BATCHES).index(workload), stream])
     idx = list(WORKLOADS).index(workload)
     return np.random.default_rng([BASE_SEED + idx, stream])
 
@@ -101,9 +161,10 @@ def noise(wl: Workload, seed_stream: int = 1, rng: np.random.Generator | None = 
     return wl.sigma * g.standard_normal(wl.n)
 
 
-def detector_for(wl: Workload, seed_stream: int = 2) -> Detector:
-    """The detector of the paper's simulations; the orbital phase at t = 0 is seeded."""
-    g = rng_for(wl.name, seed_stream)
+def detector_for(wl, seed_stream: int = 2) -> Detector:
+    """The detector of the paper's simulations; the orbital phase at t = 0 is seeded
+    (a batch's segments share the detector of the batch)."""
+    g = rng_for(wl.name.split("/")[0], seed_stream)
     return Detector(lambda_e0=float(g.uniform(0.0, 2.0 * math.pi)))
 
 

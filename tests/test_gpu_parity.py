@@ -256,7 +256,7 @@ def test_argument_errors(fs):
         fs.Segment(ctx, xd, -1.0, wl.nfft, wl.fl, wl.S0)
     assert e.value.status == 1
     with pytest.raises(fs.FstatError) as e:
-        fs.Segment(ctx, xd, wl.dt, 1 << 21, wl.fl, wl.S0)  # transforms up to 2^20
+        fs.Segment(ctx, xd, wl.dt, 1 << 22, wl.fl, wl.S0)  # transforms up to 2^21
     assert e.value.status == 2
     seg = fs.Segment(ctx, xd, wl.dt, wl.nfft, wl.fl, wl.S0)
     with pytest.raises(fs.FstatError) as e:

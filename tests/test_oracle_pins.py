@@ -336,3 +336,20 @@ def test_resampled_F_noise_mean_matches_kept_weight():
     # sigma of each mean over ~6 x 4800 independent bins: ~0.6% (|Fa|^2 part alone)
     assert abs(np.mean(r_nn) - 1.0) < 0.02
     assert 0.95 < np.mean(r_sp) < 1.0 + 0.02
+
+
+def test_epoch_shift_is_a_time_translation():
+    """A segment starting at t0 sees the detector where the unshifted detector is
+    at t0 + t: phi_m and the detector position agree at every t."""
+    det = W.detector_for(W.WORKLOADS["grid_2d"])
+    t0 = 1.7e7 + 123.25
+    d2 = earth.detector_at_epoch(det, t0)
+    t = np.linspace(0.0, 3 * 86164.0, 257)
+    a, dl = 1.1, -0.4
+    assert np.max(np.abs(earth.phi_m(t0 + t, a, dl, det) - earth.phi_m(t, a, dl, d2))) < 1e-8
+    assert np.max(np.abs(earth.detector_position_ls(t0 + t, det) - earth.detector_position_ls(t, d2))) < 1e-8
+    # a whole number of sidereal rotations leaves the site, not the orbit, unchanged
+    day = 2 * math.pi / earth.OMEGA_R
+    d3 = earth.detector_at_epoch(det, 5 * day)
+    assert abs(math.remainder(earth.sidereal_angle(0.0, d3) - earth.sidereal_angle(0.0, det), 2 * math.pi)) < 1e-9
+    assert abs(d3.lambda_e0 - det.lambda_e0 - earth.OMEGA_O * 5 * day) < 1e-15

@@ -32,6 +32,11 @@ if ROOT not in sys.path:
 from paper_1003_0844_gb300 import workloads as W  # noqa: E402
 
 METRIC = "F-stat templates/s (N=86,164, 2^18 FFT) on 1 GB300; % HBM roofline; max rel dF vs FP64"
+METRICS = {
+    "grid_2d": METRIC,
+    "wide_6d": "F-stat templates/s (N=1,033,968, 2^21 FFT) on 1 GB300; max rel dF vs FP64",
+    "uneven_64": "F-stat templates/s (64 segments of 1/2/3/6 days, 2^16-2^20 FFT) on 1 GB300",
+}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
@@ -45,7 +50,8 @@ def _args():
     p.add_argument("--cpu-templates", type=int, default=48, help="oracle sample size (templates)")
     p.add_argument("--fp64-skies", type=int, default=2, help="skies of the plain FP64 form comparison")
     p.add_argument("--quick", action="store_true", help="skip the CPU baseline and FP64 comparison")
-    p.add_argument("--nsky", type=int, default=None, help="override the sky count (profiling runs)")
+    p.add_argument("--nsky", type=int, default=None, help="override the sky count (profiling runs, batch sky subset)")
+    p.add_argument("--tune", action="store_true", help="run the launch tuner for each transform length first")
     return p.parse_args()
 
 
@@ -173,10 +179,164 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def main_batch(args):
+    """One step = reload every segment of the batch (preparation) + the batched search
+    of the same sky/spindown grid in all of them (candidates only)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1003_0844_gb300 import build, fstat as fs, shard
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    b = W.BATCHES[args.workload]
+    det = W.detector_for(b)
+    ctx = fs.Context(det, device=local)
+    segs_wl, t0s = b.segments(), b.epochs()
+    xs, segs = [], []
+    for wl, t0 in zip(segs_wl, t0s):
+        x64 = torch.as_tensor(W.noise(wl), device="cuda")
+        fs.inject(ctx, x64, wl.dt, wl.fl, wl.sigma, W.injections(wl), t0=float(t0))
+        x32 = x64.float().contiguous()
+        xs.append(x32)
+        segs.append(fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0, t0=float(t0)))
+    nsky_sub = args.nsky or 64   # sky subset of the batch's lattice (templates/s is per template)
+    a_all, d_all = W.sky_grid(b.nsky)
+    mine = shard.sky_shard(nsky_sub, rank, world)
+    alpha = torch.as_tensor(np.ascontiguousarray(a_all[mine]), device="cuda")
+    delta = torch.as_tensor(np.ascontiguousarray(d_all[mine]), device="cuda")
+    f1 = torch.as_tensor(W.spin_grid(b.nspin, *b.f1_range), device="cuda")
+    nsky, nspin, nseg = alpha.numel(), f1.numel(), len(segs)
+    ntempl = nseg * nsky * nspin
+    cap = 1 << 20  # candidates per segment (16 MiB each)
+    cand = torch.empty((nseg, cap, 4), dtype=torch.int32, device="cuda")
+    ncand = torch.zeros(nseg, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    tuning = {}
+    if args.tune:
+        for s in sorted({wl.nfft for wl in segs_wl}):
+            i = [wl.nfft for wl in segs_wl].index(s)
+            tuning[str(s)] = ctx.autotune(segs[i], alpha[:min(nsky, 32)].contiguous(),
+                                          delta[:min(nsky, 32)].contiguous(), f1)
+
+    def step():
+        for sg, x in zip(segs, xs):
+            sg.load(x)
+        fs.search_batch(ctx, segs, alpha, delta, f1, b.F_thr, cand=cand, n_cand=ncand, cand_cap=cap)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    ctx.check()
+    ctx.stats(reset=True)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    stats = ctx.stats(reset=True)
+    ctx.check()
+    total_ms = shard.max_over_ranks(sum(a.elapsed_time(c) for a, c in ev), device="cuda")
+    ms_per_step = total_ms / args.steps
+    value = ntempl * world / (ms_per_step / 1e3)
+    # whole-step FP32 rate: 2 transforms of 5 Nfft log2 Nfft flops per template
+    flops = sum(2 * 5 * wl.nfft * math.log2(wl.nfft) for wl in segs_wl) * nsky * nspin
+    achieved = flops / (ms_per_step / 1e3) / 1e12
+    hbm_gbs, hbm_kind = _peaks()
+    line = {
+        "metric": METRICS[args.workload], "value": value, "unit": "templates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64/double-float phases)", "data": "synthetic",
+        "config": {"workload": args.workload, "segments": nseg,
+                   "segment_kinds": [list(p) for p in b.parts], "dt": b.dt, "nsky": nsky, "nsky_lattice": b.nsky,
+                   "nspin": nspin, "templates_per_gpu": ntempl, "F_thr": b.F_thr, "F_written": False,
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky shards x%d" % world,
+                   "graph": "one CUDA graph per batch, two branches"},
+        "roofline": {"kernel": "whole step (graph of demodulation + persistent transform launches)",
+                     "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "traffic_note": "not captured for the batch graph",
+                     "peak_kind": "FP32 CUDA-core peak from unit counts and max clock (152 SM x 128 x 2 x 2070 MHz)",
+                     "flop_convention": "5 Nfft log2 Nfft per complex FFT, 2 FFTs per template"},
+        "hbm_peak_gbs": hbm_gbs, "hbm_peak_kind": hbm_kind,
+        "gpu_launches": int(stats["launches"]),
+        "clocks": ck,
+        "n_candidates": int(ncand.sum().item()),
+    }
+    if tuning:
+        line["tuning"] = tuning
+    if rank == 0 and not args.quick:
+        # the oracle on the host cores: segment preparation + one template per segment kind
+        from oracle import fstat as ofs, resample as ors  # noqa: F401
+        t0 = time.perf_counter()
+        done = 0
+        kinds_seen = set()
+        for i, wl in enumerate(segs_wl):
+            if (wl.days, wl.nfft) in kinds_seen:
+                continue
+            kinds_seen.add((wl.days, wl.nfft))
+            from oracle import earth as oe
+            r, _, n = cpu_oracle_rate(xs[i].cpu().numpy(), wl, oe.detector_at_epoch(det, float(t0s[i])),
+                                      a_all[mine][:1], d_all[mine][:1], W.spin_grid(b.nspin, *b.f1_range)[:1], 1)
+            done += n
+        secs = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / secs, "unit": "templates/s", "cores": 1, "kind": "oracle",
+                                "sample": "one template of each segment kind (%d), preparation included, %.1f s"
+                                          % (done, secs)}
+        # end to end: pinned host data of every segment -> device, load, batch, candidates -> host
+        xh = [torch.empty(x.numel(), dtype=torch.float32).pin_memory() for x in xs]
+        for h, x in zip(xh, xs):
+            h.copy_(x.cpu())
+        nc_h = torch.empty(nseg, dtype=torch.int64).pin_memory()
+        ke = max(2, args.steps)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        d2h = 0
+        for _ in range(ke):
+            for h, x, sg in zip(xh, xs, segs):
+                x.copy_(h, non_blocking=True)
+                sg.load(x)
+            fs.search_batch(ctx, segs, alpha, delta, f1, b.F_thr, cand=cand, n_cand=ncand, cand_cap=cap)
+            nc_h.copy_(ncand, non_blocking=True)
+            torch.cuda.synchronize()
+            got = [cand[i, :min(int(nc_h[i]), cap)].cpu() for i in range(nseg)]  # the stored candidates
+            d2h = nseg * 8 + sum(g.numel() * 4 for g in got)
+        e2e_s = (time.perf_counter() - t1) / ke
+        line["e2e"] = {"value": ntempl / e2e_s, "unit": "templates/s",
+                       "h2d_bytes_per_step": sum(x.numel() * 4 for x in xs), "d2h_bytes_per_step": d2h}
+    else:
+        line.setdefault("e2e", None)
+        line.setdefault("cpu_baseline", None)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for sg in segs:
+        sg.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in W.BATCHES:
+        return main_batch(args)
     import torch
     import torch.distributed as dist
     from paper_1003_0844_gb300 import build, fstat as fs, shard
@@ -216,6 +376,10 @@ def main():
     def step():
         seg.load(x32)
         fs.search(ctx, seg, alpha, delta, f1, wl.F_thr, F_out=F_out, cand=cand, n_cand=ncand, cand_cap=cap)
+
+    tuning = None
+    if args.tune:
+        tuning = ctx.autotune(seg, alpha[:min(nsky, 64)].contiguous(), delta[:min(nsky, 64)].contiguous(), f1)
 
     for _ in range(max(args.warmup, 1)):
         step()
@@ -266,7 +430,7 @@ def main():
         per_launch_ms = dom_ms / dom_n
         tpl = ntempl * args.steps / dom_n
         achieved = flops_tmpl[dom] * tpl / (per_launch_ms / 1e3) / 1e12
-        tpt, tnote = _profile_traffic("k_passes_grid_2d.md") if fused else (None, "per-batch mode")
+        tpt, tnote = (_profile_traffic("k_passes_%s.md" % args.workload) if fused else (None, "per-batch mode"))
         roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                 "traffic": (tpt * tpl if tpt is not None else None), "traffic_unit": "bytes per launch",
@@ -281,7 +445,8 @@ def main():
               for k, v in kinds.items() if v[1]}
 
     line = {
-        "metric": METRIC, "value": value, "unit": "templates/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRICS.get(args.workload, METRIC), "value": value, "unit": "templates/s", "n_gpus": world,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (FP64/double-float phases)", "data": "synthetic",
         "config": {"workload": args.workload, "n": wl.n, "nfft": wl.nfft, "nsky": nsky, "nspin": nspin,
@@ -293,6 +458,8 @@ def main():
         "gpu_launches": int(stats["launches"]),
         "clocks": ck,
     }
+    if tuning is not None:
+        line["tuning"] = tuning
     if rank == 0 and not args.quick:
         # plain FP64 form on a sample of skies (same GPU), and the FP32 path's error against it
         nsk = min(args.fp64_skies, nsky)
@@ -314,8 +481,10 @@ def main():
         seg64.close()
         # the oracle on the host cores, bounded sample
         xh = x32.cpu().numpy()
+        # bounded sample: about 10-30 s of oracle time (a template costs ~N)
+        ntc = max(2, min(args.cpu_templates, int(args.cpu_templates * 86164 / wl.n)))
         rate, secs, done = cpu_oracle_rate(xh, wl, det, a_all[mine], d_all[mine],
-                                           W.spin_grid(wl.nspin, *wl.f1_range), args.cpu_templates)
+                                           W.spin_grid(wl.nspin, *wl.f1_range), ntc)
         line["cpu_baseline"] = {"value": rate, "unit": "templates/s", "cores": 1, "kind": "oracle",
                                 "sample": "segment preparation + %d templates (FFT mode), %.1f s" % (done, secs)}
         # end to end through the public API with host buffers: pinned x -> device,

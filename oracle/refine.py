@@ -22,8 +22,14 @@ Derivatives (chain rule written out here; pinned by finite differences):
   dF = c [2 Re(conj(Sa) dSa) / <a^2> - |Sa|^2 d<a^2> / <a^2>^2 + (same for b)],
 
 where a depends on alpha through x = alpha - theta(t) and on delta through its
-coefficients.  The reduced Fisher matrix (Eq. redFm-def) takes the phase
-derivatives m_i = 2 pi dPhi/dtheta_i:  G_ij = <m_i m_j> - <m_i><m_j>, and
+coefficients.  Second derivatives follow by differentiating once more:
+
+  d2Sa/dtheta_i dtheta_j = sum_k x_k [a_ij - 2 pi i (a_i dPhi_j + a_j dPhi_i + a dPhi_ij)
+                                      - 4 pi^2 a dPhi_i dPhi_j] exp(-2 pi i Phi_k),
+  d2(P/A) = P_ij/A - (P_i A_j + P_j A_i)/A^2 - P A_ij/A^2 + 2 P A_i A_j/A^3, P = |Sa|^2.
+
+The reduced Fisher matrix (Eq. redFm-def) takes the phase derivatives
+m_i = 2 pi dPhi/dtheta_i:  G_ij = <m_i m_j> - <m_i><m_j>, and
 near a maximum F(theta + tau) ~ F(theta) (1 - tau^T G tau) (Eq. TaylorC2).
 """
 from __future__ import annotations
@@ -35,8 +41,10 @@ import numpy as np
 from . import earth, response
 
 
-def _geometry(n: int, dt: float, alpha: float, delta: float, det):
-    """t_k, phi_k and its alpha/delta derivatives, a_k, b_k and their derivatives."""
+def _geometry(n: int, dt: float, alpha: float, delta: float, det, second: bool = False):
+    """t_k, phi_k and its alpha/delta derivatives, a_k, b_k and their derivatives
+    (with second=True also the second derivatives: phi_aa, phi_ad, phi_dd and the
+    same for a and b)."""
     t = np.arange(n, dtype=np.float64) * dt
     rd = earth.detector_position_ls(t, det)                    # (3, n)
     ca, sa, cd, sd = math.cos(alpha), math.sin(alpha), math.cos(delta), math.sin(delta)
@@ -56,7 +64,21 @@ def _geometry(n: int, dt: float, alpha: float, delta: float, det):
     b_a = -2 * f["c2"] * s2 + 2 * f["s2"] * c2 - f["c1"] * s1 + f["s1"] * c1
     a_d = ed["c2"] * c2 + ed["s2"] * s2 + ed["c1"] * c1 + ed["s1"] * s1 + ed["c0"]
     b_d = fd["c2"] * c2 + fd["s2"] * s2 + fd["c1"] * c1 + fd["s1"] * s1
-    return t, phi, phi_a, phi_d, a, b, a_a, b_a, a_d, b_d
+    first = (t, phi, phi_a, phi_d, a, b, a_a, b_a, a_d, b_d)
+    if not second:
+        return first
+    n0_aa = R @ np.array([-ca * cd, -sa * cd, 0.0])
+    n0_ad = R @ np.array([sa * sd, -ca * sd, 0.0])
+    n0_dd = R @ np.array([-ca * cd, -sa * cd, -sd])
+    phi2 = (n0_aa @ rd, n0_ad @ rd, n0_dd @ rd)
+    edd, fdd = _ab_coefficients_ddelta2(delta, det)
+    a_aa = -4 * e["c2"] * c2 - 4 * e["s2"] * s2 - e["c1"] * c1 - e["s1"] * s1
+    b_aa = -4 * f["c2"] * c2 - 4 * f["s2"] * s2 - f["c1"] * c1 - f["s1"] * s1
+    a_ad = -2 * ed["c2"] * s2 + 2 * ed["s2"] * c2 - ed["c1"] * s1 + ed["s1"] * c1
+    b_ad = -2 * fd["c2"] * s2 + 2 * fd["s2"] * c2 - fd["c1"] * s1 + fd["s1"] * c1
+    a_dd = edd["c2"] * c2 + edd["s2"] * s2 + edd["c1"] * c1 + edd["s1"] * s1 + edd["c0"]
+    b_dd = fdd["c2"] * c2 + fdd["s2"] * s2 + fdd["c1"] * c1 + fdd["s1"] * s1
+    return first + (phi2, (a_aa, a_ad, a_dd), (b_aa, b_ad, b_dd))
 
 
 def _ab_coefficients_ddelta(delta: float, det):
@@ -81,13 +103,37 @@ def _ab_coefficients_ddelta(delta: float, det):
     return e, f
 
 
-def fstat_point(x, dt: float, theta, fl: float, det, S0: float, grad: bool = False):
+def _ab_coefficients_ddelta2(delta: float, det):
+    """d^2/ddelta^2 of the coefficients of response.ab_coefficients."""
+    g, l, d = det.gamma, det.lat, delta
+    s2g, c2g = math.sin(2 * g), math.cos(2 * g)
+    sl, cl, s2l, c2l = math.sin(l), math.cos(l), math.sin(2 * l), math.cos(2 * l)
+    sd, cd, s2d, c2d = math.sin(d), math.cos(d), math.sin(2 * d), math.cos(2 * d)
+    e = dict(
+        c2=s2g * (3 - c2l) * 4 * c2d / 16.0,
+        s2=-c2g * sl * c2d,
+        c1=-s2g * s2l * s2d,
+        s1=2 * c2g * cl * s2d,
+        c0=-1.5 * s2g * cl * cl * c2d,
+    )
+    f = dict(
+        c2=-c2g * sl * sd,
+        s2=-s2g * (3 - c2l) * sd / 4.0,
+        c1=-c2g * cl * cd,
+        s1=-s2g * s2l * cd / 2.0,
+    )
+    return e, f
+
+
+def fstat_point(x, dt: float, theta, fl: float, det, S0: float, grad: bool = False, hess: bool = False):
     """Exact F at theta = (f0, f1, alpha, delta); with grad=True also dF/dtheta (4,)
-    and the reduced Fisher matrix G (4, 4) in rad^2 per unit parameter^2."""
+    and the reduced Fisher matrix G (4, 4) in rad^2 per unit parameter^2; with
+    hess=True as well the Hessian of F (4, 4) as a fourth value."""
     x = np.asarray(x, dtype=np.float64)
     n = x.size
     f0, f1, alpha, delta = (float(v) for v in theta)
-    t, phi, phi_a, phi_d, a, b, a_a, b_a, a_d, b_d = _geometry(n, dt, alpha, delta, det)
+    geo = _geometry(n, dt, alpha, delta, det, second=hess)
+    t, phi, phi_a, phi_d, a, b, a_a, b_a, a_d, b_d = geo[:10]
     ph = f0 * (t + phi) + fl * phi + f1 * (0.5 * t * t + t * phi)
     rot = np.exp(-2j * math.pi * (ph - np.floor(ph)))
     Sa, Sb = np.dot(x * a, rot), np.dot(x * b, rot)
@@ -111,7 +157,41 @@ def fstat_point(x, dt: float, theta, fl: float, det, S0: float, grad: bool = Fal
     m = np.stack([2.0 * math.pi * d for d in dPhi])             # (4, n)
     mm = m.mean(axis=1)
     G = (m @ m.T) / n - np.outer(mm, mm)
-    return F, g, G
+    if not hess:
+        return F, g, G
+    phi2, a2s, b2s = geo[10:]
+    zero = np.zeros(n)
+    # second derivatives of Phi (cycles) and of a, b, indexed (i, j)
+    d2P = {(0, 0): zero, (0, 1): zero, (0, 2): phi_a, (0, 3): phi_d, (1, 1): zero, (1, 2): t * phi_a,
+           (1, 3): t * phi_d, (2, 2): w * phi2[0], (2, 3): w * phi2[1], (3, 3): w * phi2[2]}
+    d2a = {(2, 2): a2s[0], (2, 3): a2s[1], (3, 3): a2s[2]}
+    d2b = {(2, 2): b2s[0], (2, 3): b2s[1], (3, 3): b2s[2]}
+    H = np.empty((4, 4))
+    for (u, S, amp, damp, d2amp, M) in ((0, Sa, a, da, d2a, A), (1, Sb, b, db, d2b, B)):
+        dS = [np.dot(x * (damp[i] - 2j * math.pi * amp * dPhi[i]), rot) for i in range(4)]
+        dM = [2.0 * float(np.mean(amp * damp[i])) if i >= 2 else 0.0 for i in range(4)]
+        P = abs(S) ** 2
+        dP_ = [2.0 * (np.conj(S) * dS[i]).real for i in range(4)]
+        for i in range(4):
+            for j in range(i, 4):
+                aij = d2amp.get((i, j), 0.0)
+                ai = damp[i] if i >= 2 else 0.0
+                aj = damp[j] if j >= 2 else 0.0
+                d2S = np.dot(x * (aij - 2j * math.pi * (ai * dPhi[j] + aj * dPhi[i] + amp * d2P[(i, j)])
+                                  - 4.0 * math.pi ** 2 * amp * dPhi[i] * dPhi[j]), rot)
+                Mij = 2.0 * float(np.mean(ai * aj + amp * aij)) if (i >= 2 and j >= 2) else 0.0
+                Pij = 2.0 * (np.conj(dS[i]) * dS[j] + np.conj(S) * d2S).real
+                h = (Pij / M - (dP_[i] * dM[j] + dP_[j] * dM[i]) / M ** 2 - P * Mij / M ** 2
+                     + 2.0 * P * dM[i] * dM[j] / M ** 3)
+                if u == 0:
+                    H[i, j] = h
+                else:
+                    H[i, j] += h
+    H = c * H
+    for i in range(4):
+        for j in range(i):
+            H[i, j] = H[j, i]
+    return F, g, G, H
 
 
 def fine_search(x, dt: float, theta0, fl: float, det, S0: float, scale=None, xatol: float = 1e-4,

@@ -48,6 +48,25 @@ def test_gradient_matches_central_differences(offset):
         assert abs(fd - g[i]) <= 1e-4 * abs(g[i]) + 1e-5 * F0 / width[i], (i, fd, g[i])
 
 
+@pytest.mark.parametrize("offset", [0.0, 0.6])
+def test_hessian_matches_differences_of_the_gradient(offset):
+    wl, det, x, th = _case()
+    _, _, G = orf.fstat_point(x, wl.dt, th, wl.fl, det, wl.S0, grad=True)
+    width = 1.0 / np.sqrt(np.diag(G))
+    th = th + offset * width * np.array([0.5, 1.0, -0.8, 0.4])
+    F0, g, G, H = orf.fstat_point(x, wl.dt, th, wl.fl, det, wl.S0, grad=True, hess=True)
+    assert np.allclose(H, H.T)
+    for j in range(4):
+        h = 1e-3 * width[j]
+        e = np.zeros(4)
+        e[j] = h
+        col = (orf.fstat_point(x, wl.dt, th + e, wl.fl, det, wl.S0, grad=True)[1]
+               - orf.fstat_point(x, wl.dt, th - e, wl.fl, det, wl.S0, grad=True)[1]) / (2 * h)
+        for i in range(4):
+            assert abs(col[i] - H[i, j]) <= 1e-4 * abs(H[i, j]) + 1e-5 * F0 / (width[i] * width[j]), \
+                (i, j, col[i], H[i, j])
+
+
 def test_reduced_fisher_closed_forms():
     """Frequency and spindown rows: m_0 = 2 pi (t + phi), m_1 = 2 pi (t^2/2 + t phi); over
     t uniform in [0, To) with |phi| varying by a few seconds, G_00 -> (2 pi)^2 (N^2 - 1) dt^2 / 12

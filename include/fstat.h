@@ -238,6 +238,49 @@ FS_API fs_status fs_autotune(fs_ctx *ctx, fs_seg *seg,
                              const double *f1_dev, int32_t nspin, int32_t reps,
                              fs_tuning *out_host, void *stream);
 
+/* ---- Fine search (Sec. VII) ----
+ * A point of the continuous template space: f0 [Hz] the frequency above the
+ * band edge fl (the coarse search's bin k is f0 = k / (nfft dt)), f1 [Hz/s],
+ * alpha, delta [rad]. */
+typedef struct {
+  double f0, f1, alpha, delta;
+} fs_point;
+
+/* The F-statistic at npt points, evaluated exactly by the direct sums of
+ * Eqs. OS and Fab over the segment's original samples (no resampling; phase
+ * f0 (t + phi_m) + fl phi_m + f1 (t^2/2 + t phi_m), as in the fine search of
+ * Sec. VII), in FP64.  F_dev: npt doubles.  grad_dev: NULL or [npt][4]
+ * doubles dF/d(f0, f1, alpha, delta).  hess_dev: NULL or [npt][10] doubles,
+ * the upper triangle row by row of the Hessian of F.  metric_dev: NULL or [npt][10]
+ * doubles, the upper triangle row by row of the reduced Fisher matrix
+ * <m_i m_j> - <m_i><m_j> of the phase derivatives m_i = 2 pi dPhi/dtheta_i
+ * (Eq. redFm-def, rad^2 per unit parameter^2).  The first call on a segment
+ * builds an FP64 table of the orbital and sidereal angles (32 bytes per
+ * sample, released with the segment). */
+FS_API fs_status fs_fstat_points(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int32_t npt,
+                                 double *F_dev, double *grad_dev, double *hess_dev, double *metric_dev,
+                                 void *stream);
+
+/* Hill climb of the exact F from each point (the fine search of Sec. VII,
+ * here by Newton's method instead of the simplex search): nsteps steps, each
+ * solving (-H + lambda diag(max(-H_ii, 2 F G_ii))) D = grad F with H the
+ * Hessian of F and lambda raised from 0 until the matrix is positive definite,
+ * limited to D^T G D <= 1 with G the reduced Fisher matrix at the starting
+ * point (Eqs. redFm-def, hype: one full correlation length), and scaled by a
+ * factor that doubles (up to 1) when F grows and quarters when it does not.
+ * A trial point replaces the current one only if its F is larger, so F never
+ * decreases.  One evaluation of F, its gradient and Hessian per step.  pts_dev is updated in place; F_dev (npt doubles) receives
+ * the final F.  delta is kept in [-pi/2, pi/2] and alpha in [0, 2 pi). */
+FS_API fs_status fs_refine(fs_ctx *ctx, fs_seg *seg, fs_point *pts_dev, int32_t npt, int32_t nsteps,
+                           double *F_dev, void *stream);
+
+/* Starting points of the fine search from n coarse candidates of fs_search
+ * on this segment: f0 = bin / (nfft dt), f1 = f1_dev[spin],
+ * (alpha, delta) = (alpha_dev[sky], delta_dev[sky]). */
+FS_API fs_status fs_points_from_candidates(fs_ctx *ctx, fs_seg *seg, const fs_candidate *cand_dev, int32_t n,
+                                           const double *alpha_dev, const double *delta_dev,
+                                           const double *f1_dev, fs_point *pts_dev, void *stream);
+
 /* Synchronise `stream` and return (and clear) the first device-side error
  * latched since the last call, or FS_OK. */
 FS_API fs_status fs_sync_status(fs_ctx *ctx, void *stream);

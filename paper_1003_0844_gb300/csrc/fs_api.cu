@@ -96,6 +96,7 @@ static void seg_release(fs_seg *s) {
   cudaFree(s->coef);
   cudaFree(s->blu_bhat);
   cudaFree(s->blu_tw);
+  cudaFree(s->etab64);
   delete s;
 }
 
@@ -114,6 +115,7 @@ void fs_destroy(fs_ctx *ctx) {
   cudaFree(ctx->d_flags);
   for (int i = 0; i < fs_ctx::kWsSlots; i++) cudaFree(ctx->ws[i]);
   cudaFree(ctx->ws64);
+  cudaFree(ctx->rws);
   cudaFree(ctx->scratch);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
   delete ctx;
@@ -286,6 +288,32 @@ fs_status fs_autotune(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const d
   if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
   return autotune32(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, nspin, reps, out, as_stream(stream));
+}
+
+fs_status fs_fstat_points(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int32_t npt, double *F_dev,
+                          double *grad_dev, double *hess_dev, double *metric_dev, void *stream) {
+  if (!ctx || !seg || !pts_dev || !F_dev || seg->ctx != ctx) return FS_ERR_ARG;
+  if (npt < 1) return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  return fstat_points(ctx, seg, pts_dev, npt, F_dev, grad_dev, hess_dev, metric_dev, as_stream(stream));
+}
+
+fs_status fs_refine(fs_ctx *ctx, fs_seg *seg, fs_point *pts_dev, int32_t npt, int32_t nsteps, double *F_dev,
+                    void *stream) {
+  if (!ctx || !seg || !pts_dev || !F_dev || seg->ctx != ctx) return FS_ERR_ARG;
+  if (npt < 1 || nsteps < 0 || nsteps > 10000) return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  return refine_points(ctx, seg, pts_dev, npt, nsteps, F_dev, as_stream(stream));
+}
+
+fs_status fs_points_from_candidates(fs_ctx *ctx, fs_seg *seg, const fs_candidate *cand_dev, int32_t n,
+                                    const double *alpha_dev, const double *delta_dev, const double *f1_dev,
+                                    fs_point *pts_dev, void *stream) {
+  if (!ctx || !seg || !cand_dev || !alpha_dev || !delta_dev || !f1_dev || !pts_dev || seg->ctx != ctx)
+    return FS_ERR_ARG;
+  if (n < 1) return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  return points_from_candidates(ctx, seg, cand_dev, n, alpha_dev, delta_dev, f1_dev, pts_dev, as_stream(stream));
 }
 
 fs_status fs_sync_status(fs_ctx *ctx, void *stream) {

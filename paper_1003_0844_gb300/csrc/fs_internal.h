@@ -22,6 +22,9 @@ struct fs_ctx {
   // scratch for stage access / injection
   size_t scratch_bytes = 0;
   void *scratch = nullptr;
+  // fine-search workspace
+  size_t rws_bytes = 0;
+  void *rws = nullptr;
   // tuning knobs (templates per batch, skies per group)
   int batch_templates = 16;
   int group_skies = 256;
@@ -67,6 +70,9 @@ struct fs_seg {
   // FFT of the chirp b and the FFT twiddles; built by the first load
   int64_t blu_m = 0;
   double2 *blu_bhat = nullptr, *blu_tw = nullptr;
+  // FP64 (cos, sin) of the orbital and sidereal angles on t_k = k dt, built by
+  // the first fine-search call
+  void *etab64 = nullptr;
 };
 
 // ---- launchers implemented in the .cu files (all asynchronous on `st`) ----
@@ -145,6 +151,13 @@ fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const doubl
                          int nsky, const double *f1, int nspin, float thr, fs_candidate *cand, int64_t cap,
                          int64_t *ncand, cudaStream_t st);
 void batch_plan_release(fs_ctx *ctx);
+
+// Fine search (fs_refine.cu).
+fs_status fstat_points(fs_ctx *ctx, fs_seg *seg, const fs_point *pts, int npt, double *F, double *grad,
+                       double *hess, double *metric, cudaStream_t st);
+fs_status refine_points(fs_ctx *ctx, fs_seg *seg, fs_point *pts, int npt, int nsteps, double *F, cudaStream_t st);
+fs_status points_from_candidates(fs_ctx *ctx, fs_seg *seg, const fs_candidate *cand, int n, const double *alpha,
+                                 const double *delta, const double *f1, fs_point *pts, cudaStream_t st);
 fs_status autotune32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
                      const double *f1, int nspin, int reps, fs_tuning *out, cudaStream_t st);
 bool tuning_valid(int64_t nfft, const fs_tuning &t);

@@ -25,7 +25,8 @@ PREC = {"f32": 0, "f64": 1}
 INTERP = {"spline": 0, "nearest": 1}
 EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_seg_destroy", "fs_seg_load", "fs_search",
            "fs_sync_status", "fs_strerror", "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling",
-           "fs_get_stats", "fs_search_noalloc", "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune"]
+           "fs_get_stats", "fs_search_noalloc", "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune",
+           "fs_fstat_points", "fs_refine", "fs_points_from_candidates"]
 PROF_KINDS = ("prepare", "demodulate", "pass1", "pass2", "other")
 
 
@@ -94,9 +95,13 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.fs_set_tuning.argtypes = [vp, i64, ctypes.POINTER(_Tuning)]
     lib.fs_get_tuning.argtypes = [vp, i64, ctypes.POINTER(_Tuning)]
     lib.fs_autotune.argtypes = [vp, vp, vp, vp, i32, vp, i32, i32, ctypes.POINTER(_Tuning), vp]
+    lib.fs_fstat_points.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
+    lib.fs_refine.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+    lib.fs_points_from_candidates.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
     for name in ("fs_create", "fs_prepare_segment", "fs_seg_load", "fs_search", "fs_search_noalloc", "fs_sync_status",
                  "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling", "fs_get_stats",
-                 "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune"):
+                 "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune", "fs_fstat_points", "fs_refine",
+                 "fs_points_from_candidates"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -324,6 +329,67 @@ def search_batch(ctx: Context, segs, alpha: torch.Tensor, delta: torch.Tensor, f
                                  _stream(stream))
     _check(st, "fs_search_batch")
     return BatchResult(cand, n_cand)
+
+
+# ---- fine search: points are float64 CUDA tensors [npt, 4] = (f0, f1, alpha, delta)
+
+def fstat_points(ctx: Context, seg: Segment, pts: torch.Tensor, grad: bool = True, metric: bool = False,
+                 hess: bool = False, stream=None):
+    """Exact F at continuous points (fs_fstat_points): (F [npt], dF [npt, 4] or None,
+    reduced Fisher matrix upper triangles [npt, 10] or None) and, with hess=True, a
+    fourth value: the Hessian upper triangles [npt, 10]."""
+    _need_cuda(pts, "pts", torch.float64)
+    if pts.dim() != 2 or pts.shape[1] != 4:
+        raise ValueError("pts must have shape [npt, 4]")
+    npt = pts.shape[0]
+    F = torch.empty(npt, dtype=torch.float64, device=pts.device)
+    g = torch.empty((npt, 4), dtype=torch.float64, device=pts.device) if grad else None
+    m = torch.empty((npt, 10), dtype=torch.float64, device=pts.device) if metric else None
+    h = torch.empty((npt, 10), dtype=torch.float64, device=pts.device) if hess else None
+    _check(ctx.lib.fs_fstat_points(ctx.handle, seg.handle, _ptr(pts), npt, _ptr(F), _ptr(g) if grad else None,
+                                   _ptr(h) if hess else None, _ptr(m) if metric else None, _stream(stream)),
+           "fs_fstat_points")
+    return (F, g, m, h) if hess else (F, g, m)
+
+
+class FstatAt(torch.autograd.Function):
+    """F(pts) as a differentiable function of the points: forward and backward both
+    come from one fs_fstat_points call (the gradient is kept for the backward)."""
+
+    @staticmethod
+    def forward(fctx, pts, ctx, seg):
+        F, g, _ = fstat_points(ctx, seg, pts.detach().contiguous(), grad=True)
+        fctx.save_for_backward(g)
+        return F
+
+    @staticmethod
+    def backward(fctx, gF):
+        (g,) = fctx.saved_tensors
+        return gF[:, None] * g, None, None
+
+
+def fstat_at(ctx: Context, seg: Segment, pts: torch.Tensor) -> torch.Tensor:
+    """Differentiable exact F at the points (see FstatAt)."""
+    return FstatAt.apply(pts, ctx, seg)
+
+
+def refine(ctx: Context, seg: Segment, pts: torch.Tensor, nsteps: int = 20, stream=None):
+    """Fine search from each point (fs_refine): returns (refined points, F)."""
+    _need_cuda(pts, "pts", torch.float64)
+    out = pts.clone().contiguous()
+    F = torch.empty(out.shape[0], dtype=torch.float64, device=out.device)
+    _check(ctx.lib.fs_refine(ctx.handle, seg.handle, _ptr(out), out.shape[0], int(nsteps), _ptr(F),
+                             _stream(stream)), "fs_refine")
+    return out, F
+
+
+def points_from_candidates(ctx: Context, seg: Segment, cand: torch.Tensor, n: int, alpha: torch.Tensor,
+                           delta: torch.Tensor, f1: torch.Tensor, stream=None) -> torch.Tensor:
+    """Starting points of the fine search from the first n candidates (int32 [>=n, 4])."""
+    pts = torch.empty((n, 4), dtype=torch.float64, device=cand.device)
+    _check(ctx.lib.fs_points_from_candidates(ctx.handle, seg.handle, _ptr(cand), int(n), _ptr(alpha), _ptr(delta),
+                                             _ptr(f1), _ptr(pts), _stream(stream)), "fs_points_from_candidates")
+    return pts
 
 
 def demodulate(ctx: Context, seg: Segment, alpha: float, delta: float, stream=None):

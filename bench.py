@@ -36,7 +36,10 @@ METRICS = {
     "grid_2d": METRIC,
     "wide_6d": "F-stat templates/s (N=1,033,968, 2^21 FFT) on 1 GB300; max rel dF vs FP64",
     "uneven_64": "F-stat templates/s (64 segments of 1/2/3/6 days, 2^16-2^20 FFT) on 1 GB300",
+    "refine_2d": "fine-search candidates/s (20 Newton steps on the exact F, N=86,164) on 1 GB300",
 }
+FP64_PEAK_TFLOPS = 1.25          # nominal FP64 rate of a GB300 (no measured figure)
+REFINE_FLOP_PER_SAMPLE = 700.0   # FP64 flops per sample and point of the Hessian pass
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
@@ -331,12 +334,134 @@ def main_batch(args):
         dist.destroy_process_group()
 
 
+def main_refine(args):
+    """Fine search (config 4): the coarse 2-day search gives candidates (untimed);
+    one step = starting points from 1024 candidates + 20 Newton steps of the exact F."""
+    import torch
+    import torch.distributed as dist
+    from paper_1003_0844_gb300 import build, fstat as fs, shard
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    wl = W.WORKLOADS["grid_2d"]
+    det = W.detector_for(wl)
+    ctx = fs.Context(det, device=local)
+    x64 = torch.as_tensor(W.noise(wl), device="cuda")
+    fs.inject(ctx, x64, wl.dt, wl.fl, wl.sigma, W.injections(wl))
+    x32 = x64.float().contiguous()
+    a_all, d_all = W.sky_grid(wl.nsky * world)
+    mine = shard.sky_shard(wl.nsky, rank, world)
+    alpha = torch.as_tensor(np.ascontiguousarray(a_all[mine]), device="cuda")
+    delta = torch.as_tensor(np.ascontiguousarray(d_all[mine]), device="cuda")
+    f1 = torch.as_tensor(W.spin_grid(wl.nspin, *wl.f1_range), device="cuda")
+    seg = fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0)
+    res = fs.search(ctx, seg, alpha, delta, f1, wl.F_thr, write_F=False, cand_cap=1 << 20)
+    ncand_all = min(int(res.n_cand.item()), res.cand.shape[0])
+    # the 1024 strongest crossings
+    Fc = res.cand[:ncand_all, 3].view(torch.float32)
+    top = torch.argsort(Fc, descending=True)[:1024]
+    cand = res.cand[top].contiguous()
+    npt, nsteps = cand.shape[0], 20
+
+    def step():
+        pts = fs.points_from_candidates(ctx, seg, cand, npt, alpha, delta, f1)
+        return fs.refine(ctx, seg, pts, nsteps=nsteps)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    ctx.check()
+    ctx.stats(reset=True)
+    stream = torch.cuda.current_stream()
+    steps = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        out, Fr = step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    stats = ctx.stats(reset=True)
+    ctx.check()
+    total_ms = shard.max_over_ranks(sum(a.elapsed_time(c) for a, c in ev), device="cuda")
+    ms_per_step = total_ms / steps
+    value = npt * world / (ms_per_step / 1e3)
+    F0 = fs.fstat_points(ctx, seg, fs.points_from_candidates(ctx, seg, cand, npt, alpha, delta, f1), grad=False)[0]
+    gain = (Fr / F0).cpu().numpy()
+    flops = REFINE_FLOP_PER_SAMPLE * wl.n * npt * (nsteps + 1)
+    achieved = flops / (ms_per_step / 1e3) / 1e12
+    line = {
+        "metric": METRICS["refine_2d"], "value": value, "unit": "candidates/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "refine_2d", "n": wl.n, "candidates": npt, "newton_steps": nsteps,
+                   "coarse": "grid_2d search (256 sky x 16 spindowns), strongest 1024 crossings",
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky shards x%d" % world},
+        "roofline": {"kernel": "k_points<Hessian> (21 passes per step)", "bound": "fp64", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None, "peak_kind": "nominal FP64 rate (no measured FP64 peak)",
+                     "flop_convention": "%d FP64 flop per sample and point per pass" % REFINE_FLOP_PER_SAMPLE},
+        "gpu_launches": int(stats["launches"]),
+        "clocks": ck,
+        "F_gain": {"median": float(np.median(gain)), "max": float(np.max(gain))},
+    }
+    if rank == 0 and not args.quick:
+        # oracle: Nelder-Mead fine search (Sec. VII) from the first two starting points
+        from oracle import refine as orf
+        pts0 = fs.points_from_candidates(ctx, seg, cand, 2, alpha, delta, f1).cpu().numpy()
+        xh = x32.double().cpu().numpy()
+        t0 = time.perf_counter()
+        for p in pts0:
+            orf.fine_search(xh, wl.dt, p, wl.fl, det, wl.S0)
+        secs = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(pts0) / secs, "unit": "candidates/s", "cores": 1, "kind": "oracle",
+                                "sample": "Nelder-Mead on the exact F from 2 candidates, %.1f s" % secs}
+        # end to end: candidates from the host, refined points and F back to the host
+        ch = cand.cpu().pin_memory()
+        ke = max(2, steps)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(ke):
+            cd = ch.to("cuda", non_blocking=True)
+            pts = fs.points_from_candidates(ctx, seg, cd, npt, alpha, delta, f1)
+            out, Fr = fs.refine(ctx, seg, pts, nsteps=nsteps)
+            out.cpu(), Fr.cpu()
+        e2e_s = (time.perf_counter() - t1) / ke
+        line["e2e"] = {"value": npt / e2e_s, "unit": "candidates/s", "h2d_bytes_per_step": npt * 16,
+                       "d2h_bytes_per_step": npt * 40}
+    else:
+        line.setdefault("e2e", None)
+        line.setdefault("cpu_baseline", None)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    seg.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload in W.BATCHES:
         return main_batch(args)
+    if args.workload == "refine_2d":
+        return main_refine(args)
     import torch
     import torch.distributed as dist
     from paper_1003_0844_gb300 import build, fstat as fs, shard

@@ -131,3 +131,34 @@ def false_alarm_probability(F0):
     """P_F(F0) = (1 + F0) exp(-F0): survival of F when 2F ~ chi^2 with 4 dof (Eq. PF)."""
     F0 = np.asarray(F0, dtype=np.float64)
     return (1.0 + F0) * np.exp(-F0)
+
+
+def search_false_alarm(F0, n_cells):
+    """False-alarm probability of a search over n_cells independent cells,
+    alpha = 1 - (1 - P_F(F0))^Nc (Eq. FP), and the expected number of false
+    alarms Nc P_F(F0) (Eq. NF)."""
+    P = float(false_alarm_probability(F0))
+    # 1 - (1 - P)^Nc written with log1p/expm1 so that it keeps its digits when P is tiny
+    return -math.expm1(n_cells * math.log1p(-P)) if P < 1.0 else 1.0, n_cells * P
+
+
+def threshold_for_false_alarm(alpha: float, n_cells: float) -> float:
+    """The threshold F0 whose search false-alarm probability is alpha (Eq. FP
+    inverted), by bracketing and bisection on the definition."""
+    from scipy.optimize import brentq
+    f = lambda F0: search_false_alarm(F0, n_cells)[0] - alpha
+    if f(0.0) <= 0.0:
+        return 0.0
+    hi = 1.0
+    while f(hi) > 0.0:
+        hi *= 2.0
+    return brentq(f, 0.0, hi, xtol=1e-14, rtol=1e-15)
+
+
+def cell_count(G, v_total: float) -> float:
+    """N_c = V_total / V_cell with V_cell = pi^(M/2) / (Gamma(M/2 + 1) sqrt(det G))
+    (Eqs. NT, vc), G the M x M reduced Fisher matrix."""
+    G = np.asarray(G, dtype=np.float64)
+    M = G.shape[0]
+    v_cell = math.pi ** (M / 2) / (math.gamma(M / 2 + 1) * math.sqrt(np.linalg.det(G)))
+    return v_total / v_cell

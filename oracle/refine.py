@@ -211,3 +211,21 @@ def fine_search(x, dt: float, theta0, fl: float, det, S0: float, scale=None, xat
                    method="Nelder-Mead", options=dict(xatol=xatol, fatol=1e-10, maxiter=maxiter,
                                                       initial_simplex=0.3 * np.vstack([np.zeros(4), np.eye(4)])))
     return theta0 + res.x * scale, -res.fun
+
+
+def amplitude_estimates(x, dt: float, theta, fl: float, det):
+    """ML estimators of the amplitudes (Eq. amle0): A1 = 2 <x h1>/<a^2>,
+    A2 = 2 <x h2>/<b^2>, A3 = 2 <x h3>/<a^2>, A4 = 2 <x h4>/<b^2> with
+    h1..h4 = a cos(phi), b cos(phi), a sin(phi), b sin(phi) (Eq. sig) at the
+    template theta, time averages over the samples."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.size
+    t = np.arange(n, dtype=np.float64) * dt
+    f0, f1, alpha, delta = (float(v) for v in theta)
+    a, b = response.ab(t, alpha, delta, det)
+    cyc = response.heterodyned_phase_cycles(t, f0, f1, fl, alpha, delta, det)
+    ph = 2.0 * math.pi * (cyc - np.floor(cyc))
+    c, s = np.cos(ph), np.sin(ph)
+    A, B = np.mean(a * a), np.mean(b * b)
+    return np.array([2 * np.mean(x * a * c) / A, 2 * np.mean(x * b * c) / B,
+                     2 * np.mean(x * a * s) / A, 2 * np.mean(x * b * s) / B])

@@ -353,3 +353,35 @@ def test_epoch_shift_is_a_time_translation():
     d3 = earth.detector_at_epoch(det, 5 * day)
     assert abs(math.remainder(earth.sidereal_angle(0.0, d3) - earth.sidereal_angle(0.0, det), 2 * math.pi)) < 1e-9
     assert abs(d3.lambda_e0 - det.lambda_e0 - earth.OMEGA_O * 5 * day) < 1e-15
+
+
+def test_search_false_alarm_and_threshold():
+    """Eq. FP against the chi^2_4 survival (Eq. PF), its small-alpha limit, and the
+    inversion to a threshold."""
+    from scipy.stats import chi2
+    for F0 in (0.5, 5.0, 20.0, 35.0):
+        a1, nf = fstat.search_false_alarm(F0, 1.0)
+        assert abs(a1 - chi2.sf(2 * F0, 4)) <= 1e-12 * max(a1, 1e-300) + 1e-15
+        aN, nfN = fstat.search_false_alarm(F0, 1e6)
+        assert abs(nfN - 1e6 * a1) <= 1e-9 * nfN
+        if nfN < 1e-3:                                 # rare: alpha ~ expected number
+            assert abs(aN / nfN - 1.0) < 1e-3
+    for alpha, nc in ((0.01, 1e9), (1e-3, 4.3e6), (0.5, 10.0)):
+        F0 = fstat.threshold_for_false_alarm(alpha, nc)
+        assert abs(fstat.search_false_alarm(F0, nc)[0] - alpha) < 1e-12
+    assert fstat.threshold_for_false_alarm(0.999999, 1e6) == 0.0 or \
+        fstat.search_false_alarm(fstat.threshold_for_false_alarm(0.999999, 1e6), 1e6)[0] <= 1.0
+
+
+def test_cell_count_is_the_ellipsoid_volume():
+    """V_cell of Eq. vc is the volume of tau^T G tau <= 1: Monte Carlo in 2 and 4 dimensions."""
+    rng = np.random.default_rng(7)
+    for G in (np.array([[1 / 12, 1 / 12], [1 / 12, 4 / 45]]),
+              np.array([[3.0, 0.4, 0.1, 0.0], [0.4, 2.0, 0.2, 0.1], [0.1, 0.2, 1.5, 0.3], [0.0, 0.1, 0.3, 1.0]])):
+        M = G.shape[0]
+        half = 1.0 / np.sqrt(np.linalg.eigvalsh(G).min())     # box half-width covering the ellipsoid
+        u = rng.uniform(-half, half, size=(400000, M))
+        frac = np.mean(np.einsum("ij,jk,ik->i", u, G, u) <= 1.0)
+        v_mc = frac * (2 * half) ** M
+        v_cell = 1.0 / fstat.cell_count(G, 1.0)
+        assert abs(v_mc / v_cell - 1.0) < 0.02, (v_mc, v_cell)

@@ -124,3 +124,22 @@ def test_nelder_mead_recovers_the_injection():
     best, Fb = orf.fine_search(x, wl.dt, start, wl.fl, det, wl.S0)
     assert Fb >= F0 * (1 - 1e-4)
     assert np.all(np.abs(best - th) < 0.05 * width), (best - th) / width
+
+
+def test_amplitude_estimates_recover_the_injected_amplitudes():
+    """Noise-free signal over (nearly) one sidereal day at the true template: the
+    estimators of Eq. amle0 return the A_i of Eq. eq:ampone up to <ab> != 0 terms."""
+    wl, det, x, th = _case(noise=False)
+    inj = W.Injection(f0=th[0], f1=th[1], alpha=th[2], delta=th[3], psi=0.3, cos_iota=0.4, phi0=1.1, snr=25.0)
+    t = np.arange(wl.n) * wl.dt
+    h = orsp.signal_unit(t, inj, wl.fl, det)
+    h0 = inj.snr / math.sqrt(2.0 / wl.S0 * wl.dt * float(np.dot(h, h)))     # the amplitude inject() applies
+    A = orsp.amplitudes(h0, inj.cos_iota, inj.psi, inj.phi0)
+    Ah = orf.amplitude_estimates(x, wl.dt, th, wl.fl, det)
+    assert np.max(np.abs(Ah - A)) < 0.02 * np.max(np.abs(A)), (Ah, A)
+    # with noise the estimates scatter around the truth by ~ sqrt(2/(<a^2> To/S0)) ...
+    wl, det, xn, th = _case(noise=True)
+    An = orf.amplitude_estimates(xn, wl.dt, th, wl.fl, det)
+    a, b = orsp.ab(t, th[2], th[3], det)
+    sig = np.sqrt([2 * wl.S0 / (wl.n * wl.dt * np.mean(v * v)) for v in (a, b, a, b)])
+    assert np.all(np.abs(An - A) < 5 * sig), ((An - A) / sig)

@@ -281,6 +281,31 @@ FS_API fs_status fs_points_from_candidates(fs_ctx *ctx, fs_seg *seg, const fs_ca
                                            const double *alpha_dev, const double *delta_dev,
                                            const double *f1_dev, fs_point *pts_dev, void *stream);
 
+/* ML estimators of the four amplitudes at each point (Eq. amle0):
+ * A1 = 2 <x h1>/<a^2>, A2 = 2 <x h2>/<b^2>, A3 = 2 <x h3>/<a^2>,
+ * A4 = 2 <x h4>/<b^2> with h1..h4 = a cos(phi), b cos(phi), a sin(phi),
+ * b sin(phi) of Eq. sig and phi = 2 pi Phi the phase of fs_fstat_points,
+ * averages over the segment's samples.  amp_dev: [npt][4] doubles. */
+FS_API fs_status fs_amplitudes(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int32_t npt,
+                               double *amp_dev, void *stream);
+
+/* ---- Detection threshold (Sec. III, host functions, no device work) ----
+ * False-alarm probability of one cell for threshold F0, (1 + F0) exp(-F0)
+ * (Eq. PF; 1 for F0 <= 0). */
+FS_API double fs_false_alarm_cell(double F0);
+/* Over n_cells independent cells: *alpha = 1 - (1 - P_F(F0))^n_cells
+ * (Eq. FP) and, if n_false is not NULL, the expected number of false alarms
+ * n_cells P_F(F0) (Eq. NF).  FS_ERR_ARG for n_cells <= 0 or non-finite input. */
+FS_API fs_status fs_false_alarm(double F0, double n_cells, double *alpha, double *n_false);
+/* The threshold F0 >= 0 whose false-alarm probability over n_cells cells is
+ * alpha, 0 < alpha < 1 (Eq. FP inverted). */
+FS_API fs_status fs_threshold(double alpha, double n_cells, double *F0);
+/* Number of cells n_cells = v_total / V_cell with
+ * V_cell = pi^(M/2) / (Gamma(M/2 + 1) sqrt(det G)) (Eqs. NT, vc); G_host is
+ * the M x M reduced Fisher matrix (row-major, symmetric positive definite,
+ * M <= 16), v_total the parameter-space volume in the same units. */
+FS_API fs_status fs_cell_count(int32_t M, const double *G_host, double v_total, double *n_cells);
+
 /* Synchronise `stream` and return (and clear) the first device-side error
  * latched since the last call, or FS_OK. */
 FS_API fs_status fs_sync_status(fs_ctx *ctx, void *stream);

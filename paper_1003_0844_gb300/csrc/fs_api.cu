@@ -316,6 +316,13 @@ fs_status fs_points_from_candidates(fs_ctx *ctx, fs_seg *seg, const fs_candidate
   return points_from_candidates(ctx, seg, cand_dev, n, alpha_dev, delta_dev, f1_dev, pts_dev, as_stream(stream));
 }
 
+fs_status fs_amplitudes(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int32_t npt, double *amp_dev,
+                        void *stream) {
+  if (!ctx || !seg || !pts_dev || !amp_dev || seg->ctx != ctx || npt < 1) return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  return amplitudes(ctx, seg, pts_dev, npt, amp_dev, as_stream(stream));
+}
+
 fs_status fs_sync_status(fs_ctx *ctx, void *stream) {
   if (!ctx) return FS_ERR_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;

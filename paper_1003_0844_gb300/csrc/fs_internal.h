@@ -156,6 +156,7 @@ void batch_plan_release(fs_ctx *ctx);
 fs_status fstat_points(fs_ctx *ctx, fs_seg *seg, const fs_point *pts, int npt, double *F, double *grad,
                        double *hess, double *metric, cudaStream_t st);
 fs_status refine_points(fs_ctx *ctx, fs_seg *seg, fs_point *pts, int npt, int nsteps, double *F, cudaStream_t st);
+fs_status amplitudes(fs_ctx *ctx, fs_seg *seg, const fs_point *pts, int npt, double *amp, cudaStream_t st);
 fs_status points_from_candidates(fs_ctx *ctx, fs_seg *seg, const fs_candidate *cand, int n, const double *alpha,
                                  const double *delta, const double *f1, fs_point *pts, cudaStream_t st);
 fs_status autotune32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kPtThreads) k_points(SegGeom g, const double4 
 // triangle) per point from the block partials, summed in block order.
 template <bool HESS, bool MET>
 __global__ void k_points_final(const double *partial, int nblk, int npt, SegGeom g, double *F, double *grad,
-                               double *hess, double *metric) {
+                               double *hess, double *metric, double *amp) {
   using Lt = PtLayout<HESS, MET>;
   constexpr int NA = Lt::kN;
   const int pt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -297,6 +297,12 @@ __global__ void k_points_final(const double *partial, int nblk, int npt, SegGeom
     }
   }
   F[pt] = cF * Fv;
+  if (amp) {  // Eq. amle0: 2 <x h_i> / <a^2> with <x a cos phi> = Re(Sa)/N, <x a sin phi> = -Im(Sa)/N
+    amp[4 * pt + 0] = 2.0 * s[0] / s[20];
+    amp[4 * pt + 1] = 2.0 * s[2] / s[21];
+    amp[4 * pt + 2] = -2.0 * s[1] / s[20];
+    amp[4 * pt + 3] = -2.0 * s[3] / s[21];
+  }
   if (grad)
     for (int i = 0; i < 4; i++) grad[4 * pt + i] = cF * gv[i];
   if constexpr (HESS) {
@@ -495,20 +501,20 @@ static fs_status refine_ws(fs_ctx *ctx, const fs_seg *seg, int npt, bool climb, 
 
 template <bool HESS, bool MET>
 static void launch_points(fs_seg *seg, const RefWs &w, int npt, double *F, double *grad, double *hess,
-                          double *metric, cudaStream_t st) {
+                          double *metric, double *amp, cudaStream_t st) {
   k_points<HESS, MET><<<dim3(npt, w.nblk), kPtThreads, 0, st>>>(seg->g, (const double4 *)seg->etab64, seg->x64,
                                                                  w.pc, w.partial);
   k_points_final<HESS, MET><<<(unsigned)((npt + 127) / 128), 128, 0, st>>>(w.partial, w.nblk, npt, seg->g, F, grad,
-                                                                            hess, metric);
+                                                                            hess, metric, amp);
 }
 
 static fs_status points_pass(fs_ctx *ctx, fs_seg *seg, const RefWs &w, const fs_point *pts, int npt, double *F,
-                             double *grad, double *hess, double *metric, cudaStream_t st) {
+                             double *grad, double *hess, double *metric, cudaStream_t st, double *amp = nullptr) {
   k_point_constants<<<(unsigned)((npt + 127) / 128), 128, 0, st>>>(pts, npt, seg->g, ctx->det, w.pc);
-  if (hess && metric) launch_points<true, true>(seg, w, npt, F, grad, hess, metric, st);
-  else if (hess) launch_points<true, false>(seg, w, npt, F, grad, hess, metric, st);
-  else if (metric) launch_points<false, true>(seg, w, npt, F, grad, hess, metric, st);
-  else launch_points<false, false>(seg, w, npt, F, grad, hess, metric, st);
+  if (hess && metric) launch_points<true, true>(seg, w, npt, F, grad, hess, metric, amp, st);
+  else if (hess) launch_points<true, false>(seg, w, npt, F, grad, hess, metric, amp, st);
+  else if (metric) launch_points<false, true>(seg, w, npt, F, grad, hess, metric, amp, st);
+  else launch_points<false, false>(seg, w, npt, F, grad, hess, metric, amp, st);
   ctx->launches += 3;
   return cuda_status(cudaGetLastError());
 }
@@ -522,6 +528,16 @@ fs_status fstat_points(fs_ctx *ctx, fs_seg *seg, const fs_point *pts, int npt, d
   s = refine_ws(ctx, seg, npt, false, st, &w);
   if (s != FS_OK) return s;
   return points_pass(ctx, seg, w, pts, npt, F, grad, hess, metric, st);
+}
+
+fs_status amplitudes(fs_ctx *ctx, fs_seg *seg, const fs_point *pts, int npt, double *amp, cudaStream_t st) {
+  ProfScope ps(ctx, PROF_OTHER, st);
+  fs_status s = earth_table(seg, st);
+  if (s != FS_OK) return s;
+  RefWs w;
+  s = refine_ws(ctx, seg, npt, true, st, &w);  // the climb's F buffer receives the (unused) F
+  if (s != FS_OK) return s;
+  return points_pass(ctx, seg, w, pts, npt, w.Ft, nullptr, nullptr, nullptr, st, amp);
 }
 
 fs_status refine_points(fs_ctx *ctx, fs_seg *seg, fs_point *pts, int npt, int nsteps, double *F, cudaStream_t st) {

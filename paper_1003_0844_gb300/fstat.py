@@ -26,7 +26,8 @@ INTERP = {"spline": 0, "nearest": 1}
 EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_seg_destroy", "fs_seg_load", "fs_search",
            "fs_sync_status", "fs_strerror", "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling",
            "fs_get_stats", "fs_search_noalloc", "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune",
-           "fs_fstat_points", "fs_refine", "fs_points_from_candidates"]
+           "fs_fstat_points", "fs_refine", "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm_cell",
+           "fs_false_alarm", "fs_threshold", "fs_cell_count"]
 PROF_KINDS = ("prepare", "demodulate", "pass1", "pass2", "other")
 
 
@@ -98,10 +99,16 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.fs_fstat_points.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
     lib.fs_refine.argtypes = [vp, vp, vp, i32, i32, vp, vp]
     lib.fs_points_from_candidates.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
+    lib.fs_amplitudes.argtypes = [vp, vp, vp, i32, vp, vp]
+    lib.fs_false_alarm_cell.argtypes = [f64]
+    lib.fs_false_alarm_cell.restype = f64
+    lib.fs_false_alarm.argtypes = [f64, f64, ctypes.POINTER(f64), ctypes.POINTER(f64)]
+    lib.fs_threshold.argtypes = [f64, f64, ctypes.POINTER(f64)]
+    lib.fs_cell_count.argtypes = [i32, ctypes.POINTER(f64), f64, ctypes.POINTER(f64)]
     for name in ("fs_create", "fs_prepare_segment", "fs_seg_load", "fs_search", "fs_search_noalloc", "fs_sync_status",
                  "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling", "fs_get_stats",
                  "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune", "fs_fstat_points", "fs_refine",
-                 "fs_points_from_candidates"):
+                 "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm", "fs_threshold", "fs_cell_count"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -390,6 +397,42 @@ def points_from_candidates(ctx: Context, seg: Segment, cand: torch.Tensor, n: in
     _check(ctx.lib.fs_points_from_candidates(ctx.handle, seg.handle, _ptr(cand), int(n), _ptr(alpha), _ptr(delta),
                                              _ptr(f1), _ptr(pts), _stream(stream)), "fs_points_from_candidates")
     return pts
+
+
+def amplitudes(ctx: Context, seg: Segment, pts: torch.Tensor, stream=None) -> torch.Tensor:
+    """ML amplitude estimators A1..A4 at the points (fs_amplitudes): float64 [npt, 4]."""
+    _need_cuda(pts, "pts", torch.float64)
+    amp = torch.empty((pts.shape[0], 4), dtype=torch.float64, device=pts.device)
+    _check(ctx.lib.fs_amplitudes(ctx.handle, seg.handle, _ptr(pts), pts.shape[0], _ptr(amp), _stream(stream)),
+           "fs_amplitudes")
+    return amp
+
+
+def false_alarm(F0: float, n_cells: float):
+    """(alpha, expected false alarms) of threshold F0 over n_cells cells (fs_false_alarm)."""
+    lib = load_library()
+    a, nf = ctypes.c_double(), ctypes.c_double()
+    _check(lib.fs_false_alarm(float(F0), float(n_cells), ctypes.byref(a), ctypes.byref(nf)), "fs_false_alarm")
+    return a.value, nf.value
+
+
+def threshold(alpha: float, n_cells: float) -> float:
+    """Threshold F0 of false-alarm probability alpha over n_cells cells (fs_threshold)."""
+    lib = load_library()
+    F0 = ctypes.c_double()
+    _check(lib.fs_threshold(float(alpha), float(n_cells), ctypes.byref(F0)), "fs_threshold")
+    return F0.value
+
+
+def cell_count(G, v_total: float) -> float:
+    """Number of cells of volume v_total for the reduced Fisher matrix G (fs_cell_count)."""
+    import numpy as np
+    g = np.ascontiguousarray(np.asarray(G, dtype=np.float64))
+    lib = load_library()
+    n = ctypes.c_double()
+    _check(lib.fs_cell_count(int(g.shape[0]), g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(v_total),
+                             ctypes.byref(n)), "fs_cell_count")
+    return n.value
 
 
 def demodulate(ctx: Context, seg: Segment, alpha: float, delta: float, stream=None):

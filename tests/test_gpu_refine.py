@@ -141,3 +141,18 @@ def test_points_from_candidates(fs):
     F0, _, _ = fs.fstat_points(ctx, seg, _dev(pts), grad=False)
     _, F = fs.refine(ctx, seg, _dev(pts), nsteps=5)
     assert torch.all(F >= F0)
+
+
+def test_amplitudes_match_oracle(fs):
+    wl, det, x, th = _case()
+    _, _, G0 = orf.fstat_point(x, wl.dt, th, wl.fl, det, wl.S0, grad=True)
+    P = _points(th, 1.0 / np.sqrt(np.diag(G0)))[:3]
+    ctx = fs.Context(det)
+    xd = _dev(x, torch.float32)
+    seg = fs.Segment(ctx, xd, wl.dt, wl.nfft, wl.fl, wl.S0)
+    amp = fs.amplitudes(ctx, seg, _dev(P)).cpu().numpy()
+    assert ctx.sync_status() == 0
+    xo = xd.double().cpu().numpy()
+    for p in range(len(P)):
+        ref = orf.amplitude_estimates(xo, wl.dt, P[p], wl.fl, det)
+        assert np.max(np.abs(amp[p] - ref)) <= 1e-9 * np.max(np.abs(ref)), (p, amp[p], ref)

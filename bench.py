@@ -420,7 +420,7 @@ def main_refine(args):
         "F_gain": {"median": float(np.median(gain)), "max": float(np.max(gain))},
     }
     if rank == 0 and not args.quick:
-        # oracle: Nelder-Mead fine search (Sec. VII) from the first two starting points
+        # oracle: Nelder-Mead fine search (Sec. VI.C) from the first two starting points
         from oracle import refine as orf
         pts0 = fs.points_from_candidates(ctx, seg, cand, 2, alpha, delta, f1).cpu().numpy()
         xh = x32.double().cpu().numpy()

@@ -238,7 +238,7 @@ FS_API fs_status fs_autotune(fs_ctx *ctx, fs_seg *seg,
                              const double *f1_dev, int32_t nspin, int32_t reps,
                              fs_tuning *out_host, void *stream);
 
-/* ---- Fine search (Sec. VII) ----
+/* ---- Fine search (Sec. VI.C) ----
  * A point of the continuous template space: f0 [Hz] the frequency above the
  * band edge fl (the coarse search's bin k is f0 = k / (nfft dt)), f1 [Hz/s],
  * alpha, delta [rad]. */
@@ -249,7 +249,7 @@ typedef struct {
 /* The F-statistic at npt points, evaluated exactly by the direct sums of
  * Eqs. OS and Fab over the segment's original samples (no resampling; phase
  * f0 (t + phi_m) + fl phi_m + f1 (t^2/2 + t phi_m), as in the fine search of
- * Sec. VII), in FP64.  F_dev: npt doubles.  grad_dev: NULL or [npt][4]
+ * Sec. VI.C as run in Sec. VII), in FP64.  F_dev: npt doubles.  grad_dev: NULL or [npt][4]
  * doubles dF/d(f0, f1, alpha, delta).  hess_dev: NULL or [npt][10] doubles,
  * the upper triangle row by row of the Hessian of F.  metric_dev: NULL or [npt][10]
  * doubles, the upper triangle row by row of the reduced Fisher matrix
@@ -261,7 +261,7 @@ FS_API fs_status fs_fstat_points(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_d
                                  double *F_dev, double *grad_dev, double *hess_dev, double *metric_dev,
                                  void *stream);
 
-/* Hill climb of the exact F from each point (the fine search of Sec. VII,
+/* Hill climb of the exact F from each point (the fine search of Sec. VI.C,
  * here by Newton's method instead of the simplex search): nsteps steps, each
  * solving (-H + lambda diag(max(-H_ii, 2 F G_ii))) D = grad F with H the
  * Hessian of F and lambda raised from 0 until the matrix is positive definite,

@@ -1,10 +1,11 @@
-"""The fine search of Sec. VII (oracle, FP64): F at a continuous template point,
+"""The fine search of Sec. VI.C (oracle, FP64): F at a continuous template point,
 its gradient, the reduced Fisher matrix, and the Nelder-Mead maximisation.
 
 Test infrastructure only (see the package docstring).
 
-In the fine search the F-statistic is evaluated exactly, by the direct sums of
-Eqs. OS and Fab over the original samples (no resampling).  A template point is
+In the fine search of the Monte Carlo simulations (Sec. VII) the F-statistic is
+evaluated exactly, by the direct sums of Eqs. OS and Fab over the original samples
+(no resampling).  A template point is
 theta = (f0, f1, alpha, delta): f0 the frequency above the band edge fl [Hz]
 (the bin frequency k / (Nfft dt) of the coarse search, now continuous), f1 the
 spindown [Hz/s], alpha and delta the sky position.  With t_k = k dt,
@@ -196,7 +197,7 @@ def fstat_point(x, dt: float, theta, fl: float, det, S0: float, grad: bool = Fal
 
 def fine_search(x, dt: float, theta0, fl: float, det, S0: float, scale=None, xatol: float = 1e-4,
                 maxiter: int = 2000):
-    """Maximise the exact F from theta0 with the Nelder-Mead simplex (Sec. VII).
+    """Maximise the exact F from theta0 with the Nelder-Mead simplex (Sec. VI.C).
 
     The simplex works in coordinates u = (theta - theta0) / scale; `scale`
     defaults to the widths G_ii^(-1/2) of the reduced Fisher matrix at theta0,

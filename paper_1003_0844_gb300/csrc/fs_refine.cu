@@ -1,6 +1,6 @@
-// Fine search (Sec. VII): the F-statistic at continuous template points
+// Fine search (Sec. VI.C): the F-statistic at continuous template points
 // theta = (f0, f1, alpha, delta), evaluated exactly by the direct sums of
-// Eqs. OS and Fab over the original samples, with its gradient and the reduced
+// Eqs. OS and Fab over the original samples (as the fine search of Sec. VII does), with its gradient and the reduced
 // Fisher matrix of the phase (Eq. redFm-def) from the same pass, and a
 // hill climb from the coarse-search candidates that uses them.
 //

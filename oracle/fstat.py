@@ -94,6 +94,22 @@ def fstat(seg: resample.Segment, alpha, delta, f1, fl, det, S0, nfft, bins=None,
     return fstat_from_transforms(Xa, Xb, dm, seg.n, seg.dt, S0)
 
 
+def fstat_interbinned(seg: resample.Segment, alpha, delta, f1, fl, det, S0, nfft, interp="spline"):
+    """F on the half-bin grid f = j / (2 Nfft dt), j < Nfft, from a length-Nfft DFT and
+    interbinning (Eq. intbin, Sec. VI.B): even j = 2k take X(k); odd j = 2k+1 take
+    X(k + 1/2) ~ (X(k+1) - X(k)) / sqrt(2), for both Fa and Fb."""
+    dm = demodulate(seg, alpha, delta, f1, fl, det, interp=interp)
+    nb = nfft // 2
+    Xa = np.fft.fft(np.asarray(dm.ya, dtype=np.complex128), n=nfft)[:nb + 1]
+    Xb = np.fft.fft(np.asarray(dm.yb, dtype=np.complex128), n=nfft)[:nb + 1]
+    Ha = (Xa[1:] - Xa[:-1]) / math.sqrt(2.0)
+    Hb = (Xb[1:] - Xb[:-1]) / math.sqrt(2.0)
+    out = np.empty(2 * nb)
+    out[0::2] = fstat_from_transforms(Xa[:nb], Xb[:nb], dm, seg.n, seg.dt, S0)
+    out[1::2] = fstat_from_transforms(Ha, Hb, dm, seg.n, seg.dt, S0)
+    return out
+
+
 def fstat_exact(x: np.ndarray, dt: float, alpha, delta, f1, fl, det, S0, f0s) -> np.ndarray:
     """F of Eqs. OS/Fab by direct summation over the original samples, no resampling.
 

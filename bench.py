@@ -36,6 +36,7 @@ METRICS = {
     "grid_2d": METRIC,
     "wide_6d": "F-stat templates/s (N=1,033,968, 2^21 FFT) on 1 GB300; max rel dF vs FP64",
     "uneven_64": "F-stat templates/s (64 segments of 1/2/3/6 days, 2^16-2^20 FFT) on 1 GB300",
+    "grid_2d_ib": "F-stat templates/s (N=86,164, 2^17 FFT + interbinning) on 1 GB300; max rel dF vs FP64",
     "refine_2d": "fine-search candidates/s (20 Newton steps on the exact F, N=86,164) on 1 GB300",
 }
 FP64_PEAK_TFLOPS = 1.25          # nominal FP64 rate of a GB300 (no measured figure)
@@ -139,7 +140,10 @@ def cpu_oracle_rate(x, wl, det, alpha, delta, f1, ntempl):
         for m in range(len(f1)):
             if done >= ntempl:
                 break
-            ofs.fstat(seg, alpha[s], delta[s], f1[m], wl.fl, det, wl.S0, wl.nfft)
+            if getattr(wl, "interbin", False):
+                ofs.fstat_interbinned(seg, alpha[s], delta[s], f1[m], wl.fl, det, wl.S0, wl.nfft)
+            else:
+                ofs.fstat(seg, alpha[s], delta[s], f1[m], wl.fl, det, wl.S0, wl.nfft)
             done += 1
         if done >= ntempl:
             break
@@ -491,7 +495,7 @@ def main():
     f1 = torch.as_tensor(W.spin_grid(wl.nspin, *wl.f1_range), device="cuda")
     nsky, nspin, nbins = alpha.numel(), f1.numel(), wl.nbins
     ntempl = nsky * nspin
-    seg = fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0)
+    seg = fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0, interbin=wl.interbin)
     F_out = torch.empty((ntempl, nbins), dtype=torch.float32, device="cuda")
     cap = 1 << 16
     cand = torch.empty((cap, 4), dtype=torch.int32, device="cuda")
@@ -588,7 +592,7 @@ def main():
     if rank == 0 and not args.quick:
         # plain FP64 form on a sample of skies (same GPU), and the FP32 path's error against it
         nsk = min(args.fp64_skies, nsky)
-        seg64 = fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0, precision="f64")
+        seg64 = fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0, precision="f64", interbin=wl.interbin)
         fs.search(ctx, seg64, alpha[:nsk].contiguous(), delta[:nsk].contiguous(), f1, wl.F_thr)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

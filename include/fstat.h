@@ -81,6 +81,15 @@ enum { FS_PREC_F32 = 0, /* FP32 samples, spline and FFT; compensated (double-flo
 enum { FS_INTERP_SPLINE2X = 0, /* Fourier x2 + natural cubic spline (Sec. VI.A) */
        FS_INTERP_NEAREST = 1   /* nearest neighbour, "stroboscopic" (Sec. VI.A)  */ };
 enum { FS_X_F32 = 0, FS_X_F64 = 1 };
+/* Segment options.  FS_OPT_INTERBIN: the search returns F on the half-bin grid
+ * f = j / (2 nfft dt), j < nfft, from the length-nfft transform: even j = 2k
+ * from the bin X(k), odd j = 2k + 1 from X(k + 1/2) ~ (X(k+1) - X(k)) / sqrt(2)
+ * (interbinning, Eq. intbin, Sec. VI.B) for both Fa and Fb -- the frequency grid
+ * of a transform padded to 2 nfft at the cost of one of length nfft.  Searches
+ * of such a segment take nbins = nfft (the F row length) and report candidate
+ * bins j on that grid; FP32 segments need nfft <= 2^20; fs_search_batch and
+ * fs_search_noalloc do not take them (FS_ERR_UNSUPPORTED). */
+enum { FS_OPT_INTERBIN = 1 };
 
 /* One data segment: x_k = x(k dt), k < n, t = 0 at the first sample.
  * nfft: zero-padded transform length, a power of two with nfft >= n and
@@ -96,7 +105,7 @@ typedef struct {
   int32_t precision; /* FS_PREC_* */
   int32_t interp;    /* FS_INTERP_* */
   int32_t x_dtype;   /* FS_X_F32 or FS_X_F64: element type of x_dev */
-  int32_t reserved;  /* must be 0 */
+  int32_t options;   /* 0 or FS_OPT_INTERBIN */
   /* Epoch of the first sample [s] after the detector's t = 0: the Earth's
    * orbital and sidereal angles at the segment start are
    * lambda_e0 + Omega_o t0 and theta_g0 + lon + Omega_r t0 (Sec. V).  Phases,

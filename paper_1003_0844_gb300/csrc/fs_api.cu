@@ -129,7 +129,9 @@ fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d
   if (d->precision != FS_PREC_F32 && d->precision != FS_PREC_F64) return FS_ERR_ARG;
   if (d->interp != FS_INTERP_SPLINE2X && d->interp != FS_INTERP_NEAREST) return FS_ERR_ARG;
   if (d->x_dtype != FS_X_F32 && d->x_dtype != FS_X_F64) return FS_ERR_ARG;
-  if (d->reserved != 0 || !isfinite(d->t0)) return FS_ERR_ARG;
+  if ((d->options & ~FS_OPT_INTERBIN) != 0 || !isfinite(d->t0)) return FS_ERR_ARG;
+  if ((d->options & FS_OPT_INTERBIN) && d->precision == FS_PREC_F32 && d->nfft > (int64_t(1) << 20))
+    return FS_ERR_SHAPE;
   if (!is_pow2(d->nfft) || d->nfft < d->n || d->nfft < 4096 || d->nfft > (int64_t(1) << 21)) return FS_ERR_SHAPE;
   // the FP32 path splits a 2^21 transform into two 2^20 ones: the data must fit one
   if (d->precision == FS_PREC_F32 && d->nfft > (int64_t(1) << 20) && d->n > (int64_t(1) << 20)) return FS_ERR_SHAPE;
@@ -209,7 +211,11 @@ fs_status fs_search(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const dou
   if (!ctx || !seg || !alpha_dev || !delta_dev || !f1_dev || !n_cand_dev) return FS_ERR_ARG;
   if (seg->ctx != ctx) return FS_ERR_ARG;
   if (nsky < 1 || nspin < 1 || cand_cap < 0 || (cand_cap > 0 && !cand_dev)) return FS_ERR_ARG;
-  if (!(nbins == seg->g.nfft / 2 || nbins == seg->g.nfft)) return FS_ERR_SHAPE;
+  if (seg->d.options & FS_OPT_INTERBIN) {
+    if (nbins != seg->g.nfft) return FS_ERR_SHAPE;
+  } else if (!(nbins == seg->g.nfft / 2 || nbins == seg->g.nfft)) {
+    return FS_ERR_SHAPE;
+  }
   if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
   cudaStream_t st = as_stream(stream);
@@ -228,6 +234,7 @@ fs_status fs_search_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, c
   if (seg->ctx != ctx) return FS_ERR_ARG;
   if (nsky < 1 || nspin < 1 || cand_cap < 0 || (cand_cap > 0 && !cand_dev)) return FS_ERR_ARG;
   if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
+  if (seg->d.options & FS_OPT_INTERBIN) return FS_ERR_UNSUPPORTED;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
   return search32_noalloc(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, F_out_dev, nbins, cand_dev,
                           cand_cap, n_cand_dev, as_stream(stream));
@@ -241,6 +248,7 @@ fs_status fs_search_batch(fs_ctx *ctx, fs_seg *const *segs, int32_t nseg, const 
   if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
   for (int i = 0; i < nseg; i++) {
     if (!segs[i] || segs[i]->ctx != ctx || segs[i]->d.precision != FS_PREC_F32) return FS_ERR_ARG;
+    if (segs[i]->d.options & FS_OPT_INTERBIN) return FS_ERR_UNSUPPORTED;
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
   return search32_batch(ctx, segs, nseg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, cand_dev, cand_cap,

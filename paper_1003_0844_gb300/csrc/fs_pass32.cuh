@@ -161,6 +161,7 @@ struct Pass2Args {
   int sky_base;        // global index of the group's first sky
   float *F;            // NULL or F_out + (global template of the group's first template) * nbins
   int64_t nbins;       // F row length of one template (all its sub-transforms)
+  float2 *X;           // XOUT items: complex bins [batch][2][nfft] in natural order
   float thr;
   fs_candidate *cand;
   int64_t cap;
@@ -186,7 +187,7 @@ struct Xch2 {
 // Pass-2 work item for 32-thread row DFTs (N2 = 1024): a warp holds one signal of
 // one row (warps 2r, 2r+1: signals a, b of row r), so an item covers WARPS/2
 // rows; the two signals' |X|^2 terms meet through the F tile.
-template <int Q, int WARPS, bool FULLBINS, int VS>
+template <int Q, int WARPS, bool FULLBINS, int VS, bool XOUT = false>
 __device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
                                                 const float2 *twM) {
   constexpr int P = 32, R = WARPS / 2, S = Q / P;
@@ -214,6 +215,11 @@ __device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int 
   sfor<0, Q>([&](auto bb) { v[bb] = xw[X::at(t, bb)]; });
   __syncthreads();  // every warp is done with the exchange area (reused for the F tile)
   dft_inplace<Q, Q, D>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)
+  if constexpr (XOUT) {
+    float2 *Xo = A.X + ((int64_t)zs * 2 + sig) * A.nfft + k1;
+    sfor<0, D>([&](auto d) { Xo[(int64_t)A.N1 * (t + P * d)] = v[d]; });
+    return;
+  }
   const float2 nrm = A.norm[sky];
   if (sig == 0) {
     sfor<0, D>([&](auto d) { Fs[(t + P * d) * (R + 1) + row] = fmaf(v[d].x, v[d].x, v[d].y * v[d].y) * nrm.x; });
@@ -261,11 +267,11 @@ __device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int 
 }
 
 // ALIAS_F: the F tile reuses the exchange area (one more barrier, less shared memory).
-template <int P, int Q, int WARPS, bool FULLBINS, bool ALIAS_F = false, int VS = 0>
+template <int P, int Q, int WARPS, bool FULLBINS, bool ALIAS_F = false, int VS = 0, bool XOUT = false>
 __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
                                            const float2 *twM) {
   if constexpr (P == 32) {
-    pass2_item_wide<Q, WARPS, FULLBINS, VS>(A, tm, zs, rt, work, twM);
+    pass2_item_wide<Q, WARPS, FULLBINS, VS, XOUT>(A, tm, zs, rt, work, twM);
     return;
   }
   constexpr int T = P, G = (P <= 16 ? 16 / P : 1), R = WARPS * G, S = Q / P;
@@ -294,6 +300,11 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
   sfor<0, Q>([&](auto bb) { v[bb] = xw[X::at(t, bb)]; });
   if constexpr (ALIAS_F) __syncthreads();  // every warp is done with the exchange area
   dft_inplace<Q, Q, (FULLBINS ? Q : Q / 2)>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)
+  if constexpr (XOUT) {
+    float2 *Xo = A.X + ((int64_t)zs * 2 + sig) * A.nfft + k1;
+    sfor<0, D>([&](auto d) { Xo[(int64_t)A.N1 * (t + P * d)] = v[d]; });
+    return;
+  }
   const float2 nrm = A.norm[sky];
   const float myn = sig ? nrm.y : nrm.x;
   float p[D];
@@ -357,7 +368,7 @@ __device__ __forceinline__ void twiddle_matrix(float2 *twM, int P, int Q) {
   }
 }
 
-template <int P, int Q, int WARPS, bool FULLBINS, int VS>
+template <int P, int Q, int WARPS, bool FULLBINS, int VS, bool XOUT = false>
 __global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
   constexpr int R = P <= 16 ? WARPS * (16 / P) : WARPS / 2;
   extern __shared__ float2 smem[];
@@ -367,7 +378,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
   const int bt = blockIdx.x / rtiles, rt = blockIdx.x - bt * rtiles;
   twiddle_matrix(twM, P, Q);
   __syncthreads();
-  pass2_item<P, Q, WARPS, FULLBINS, false, VS>(A, A.tmpl0 + bt, bt, rt, work, twM);
+  pass2_item<P, Q, WARPS, FULLBINS, false, VS, XOUT>(A, A.tmpl0 + bt, bt, rt, work, twM);
 }
 
 // ------------------------------------------------------------------ persistent pass kernel
@@ -513,10 +524,10 @@ static cudaError_t launch_pass1(const Pass1Args &a, int nb, cudaStream_t st) {
   kern<<<nb * (a.N2 / CW), P * 2 * CW, sm, st>>>(a);
   return cudaGetLastError();
 }
-template <int P, int Q, bool FULL, int VS = 0>
+template <int P, int Q, bool FULL, int VS = 0, bool XOUT = false>
 static cudaError_t launch_pass2(const Pass2Args &a, int nb, cudaStream_t st) {
   size_t sm = pass2_smem<P, Q, FULL>();
-  auto kern = k_pass2<P, Q, kPass2Warps, FULL, VS>;
+  auto kern = k_pass2<P, Q, kPass2Warps, FULL, VS, XOUT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   constexpr int R = P <= 16 ? kPass2Warps * (16 / P) : kPass2Warps / 2;
@@ -584,6 +595,10 @@ constexpr int kPersistThreads = 256;
 // Per-shape dispatch, one translation unit per group of shapes.
 cudaError_t dispatch_pass1(int N1, const Pass1Args &a, int nb, cudaStream_t st);
 cudaError_t dispatch_pass2(int N2, bool full, const Pass2Args &a, int nb, cudaStream_t st);
+// Pass 2 storing the complex bins (all Nfft, natural order) in a.X instead of F.
+cudaError_t dispatch_pass2x(int N2, const Pass2Args &a, int nb, cudaStream_t st);
+// Interbinning epilogue (Eq. intbin) over nb templates of a batch from a.X.
+cudaError_t launch_interbin(const Pass2Args &a, int nb, cudaStream_t st);
 // Persistent launch for an N1 x N2 split; cudaErrorInvalidValue for a split
 // this build does not instantiate (split_instantiated is false).
 cudaError_t dispatch_passes(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
@@ -619,6 +634,7 @@ struct Cfg32 {
   int G;           // skies per group
   bool full;       // F on all Nfft bins (per-batch launches)
   bool persistent; // both passes from one work queue
+  bool interbin;   // F on the half-bin grid by interbinning (per-batch launches)
   QueueShape qs;
   int B;           // Z slots of the workspace
 };
@@ -628,6 +644,7 @@ struct Ws32 {
   double2 *ab2;
   double *partial;
   float2 *Z;
+  float2 *X;       // interbinning: complex bins of a batch [B][2][nsub]
   unsigned *counters;
   int64_t stride;
   int nblk_a1;

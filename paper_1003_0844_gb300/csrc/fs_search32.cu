@@ -275,6 +275,8 @@ fs_status config32(const fs_ctx *ctx, const fs_seg *seg, int nsky, int64_t nbins
   c->npad = (int64_t)c->n1max * c->sh.N2;
   const int gsk = (t && t->group_skies > 0) ? t->group_skies : ctx->group_skies;
   c->G = gsk < nsky ? gsk : nsky;
+  c->interbin = (seg->d.options & FS_OPT_INTERBIN) != 0;
+  if (c->interbin && (c->vshift || nbins != seg->g.nfft)) return FS_ERR_SHAPE;
   c->full = (nbins == seg->g.nfft);
   c->persistent = !c->full && ctx->persistent;
   c->qs = queue_shape(ctx, t, c->sh);
@@ -301,6 +303,7 @@ fs_status workspace32(fs_ctx *ctx, int slot, const fs_seg *seg, const Cfg32 &c, 
   size_t o_ab = off; off = align256(off + sizeof(double2) * G);
   size_t o_pa = off; off = align256(off + sizeof(double) * 2 * (size_t)nblk * G);
   size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)c.nsub * c.B);
+  size_t o_x = off; off = align256(off + (c.interbin ? sizeof(float2) * 2 * (size_t)c.nsub * c.B : 0));
   size_t o_ct = off; off = align256(off + sizeof(unsigned) * (1 + 2 * vt));
   if (may_alloc) {
     fs_status s = ensure_buffer(&ctx->ws[slot], &ctx->ws_bytes[slot], off, st);
@@ -317,6 +320,7 @@ fs_status workspace32(fs_ctx *ctx, int slot, const fs_seg *seg, const Cfg32 &c, 
   w->ab2 = (double2 *)(base + o_ab);
   w->partial = (double *)(base + o_pa);
   w->Z = (float2 *)(base + o_z);
+  w->X = c.interbin ? (float2 *)(base + o_x) : nullptr;
   w->counters = (unsigned *)(base + o_ct);
   w->stride = stride;
   w->nblk_a1 = nblk;
@@ -440,7 +444,13 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
         ProfScope ps(ctx, PROF_PASS1, st);
         if (dispatch_pass1(c.sh.N1, p1, nb, st) != cudaSuccess) return FS_ERR_CUDA;
       }
-      {
+      if (c.interbin) {
+        ProfScope ps(ctx, PROF_PASS2, st);
+        p2.X = w.X;
+        if (dispatch_pass2x(c.sh.N2, p2, nb, st) != cudaSuccess) return FS_ERR_CUDA;
+        if (launch_interbin(p2, nb, st) != cudaSuccess) return FS_ERR_CUDA;
+        ctx->launches += 1;
+      } else {
         ProfScope ps(ctx, PROF_PASS2, st);
         if (dispatch_pass2(c.sh.N2, c.full, p2, nb, st) != cudaSuccess) return FS_ERR_CUDA;
       }

@@ -106,9 +106,11 @@ __global__ void k_modulate64(const double2 *ya, const double2 *yb, const double 
   buf[(2 * (int64_t)m + 1) * nfft + k] = vb;
 }
 
+// F on bin k < nbins; with interbinning (ib) on the half-bin grid: output j
+// takes X(j/2) for even j and (X(j/2+1) - X(j/2))/sqrt(2) for odd j (Eq. intbin).
 __global__ void k_fstat64(const double2 *buf, int nspin, int64_t nfft, int64_t nbins, const double2 *nrmp, double *F,
                           int sky, float thr, fs_candidate *cand, int64_t cap, unsigned long long *ncand,
-                          uint32_t *flags) {
+                          uint32_t *flags, int ib) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   const int lane = threadIdx.x & 31;
@@ -116,8 +118,14 @@ __global__ void k_fstat64(const double2 *buf, int nspin, int64_t nfft, int64_t n
   const bool ok = (k < nbins);
   const double2 nrm = *nrmp;
   if (ok) {
-    const double2 xa = buf[(2 * (int64_t)m) * nfft + k];
-    const double2 xb = buf[(2 * (int64_t)m + 1) * nfft + k];
+    const double2 *ba = buf + (2 * (int64_t)m) * nfft, *bb = ba + nfft;
+    const int64_t q = ib ? (k >> 1) : k;
+    double2 xa = ba[q], xb = bb[q];
+    if (ib && (k & 1)) {
+      const double2 ya = ba[q + 1], yb = bb[q + 1];
+      xa = make_double2((ya.x - xa.x) * 0.70710678118654752440, (ya.y - xa.y) * 0.70710678118654752440);
+      xb = make_double2((yb.x - xb.x) * 0.70710678118654752440, (yb.y - xb.y) * 0.70710678118654752440);
+    }
     Fv = (xa.x * xa.x + xa.y * xa.y) * nrm.x + (xb.x * xb.x + xb.y * xb.y) * nrm.y;
     if (F) F[(int64_t)m * nbins + k] = Fv;
   }
@@ -205,7 +213,7 @@ fs_status search64(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
     if (fft64(w.buf, w.tmp, w.tw, nfft, 2 * nspin, -1, st, &ctx->launches) != cudaSuccess) return FS_ERR_CUDA;
     k_fstat64<<<dim3((unsigned)((nbins + 255) / 256), nspin), 256, 0, st>>>(
         w.buf, nspin, nfft, nbins, w.norm, F ? F + (int64_t)sk * nspin * nbins : nullptr, sk, thr, cand, cap,
-        (unsigned long long *)ncand, ctx->d_flags);
+        (unsigned long long *)ncand, ctx->d_flags, (seg->d.options & FS_OPT_INTERBIN) ? 1 : 0);
   }
   return cuda_status(cudaGetLastError());
 }

@@ -45,7 +45,7 @@ class _Detector(ctypes.Structure):
 class _SegDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nfft", ctypes.c_int64), ("dt", ctypes.c_double), ("fl", ctypes.c_double),
                 ("S0", ctypes.c_double), ("precision", ctypes.c_int32), ("interp", ctypes.c_int32),
-                ("x_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32), ("t0", ctypes.c_double)]
+                ("x_dtype", ctypes.c_int32), ("options", ctypes.c_int32), ("t0", ctypes.c_double)]
 
 
 class _Tuning(ctypes.Structure):
@@ -217,7 +217,8 @@ class Segment:
     """One prepared data segment (fs_prepare_segment): tables, x2 upsampling, spline."""
 
     def __init__(self, ctx: Context, x: torch.Tensor, dt: float, nfft: int, fl: float, S0: float,
-                 precision: str = "f32", interp: str = "spline", t0: float = 0.0, stream=None):
+                 precision: str = "f32", interp: str = "spline", t0: float = 0.0, interbin: bool = False,
+                 stream=None):
         _need_cuda(x, "x")
         if x.dtype not in (torch.float32, torch.float64):
             raise ValueError("x must be float32 or float64")
@@ -227,8 +228,9 @@ class Segment:
         self.dt, self.fl, self.S0 = float(dt), float(fl), float(S0)
         self.precision = precision
         self.t0 = float(t0)
+        self.interbin = bool(interbin)
         d = _SegDesc(self.n, self.nfft, self.dt, self.fl, self.S0, PREC[precision], INTERP[interp],
-                     0 if x.dtype == torch.float32 else 1, 0, self.t0)
+                     0 if x.dtype == torch.float32 else 1, 1 if interbin else 0, self.t0)
         h = ctypes.c_void_p()
         _check(ctx.lib.fs_prepare_segment(ctx.handle, ctypes.byref(h), ctypes.byref(d), _ptr(x), _stream(stream)),
                "fs_prepare_segment")
@@ -286,7 +288,7 @@ def search(ctx: Context, seg: Segment, alpha: torch.Tensor, delta: torch.Tensor,
     nsky, nspin = alpha.numel(), f1.numel()
     if delta.numel() != nsky:
         raise ValueError("alpha and delta differ in length")
-    nb = seg.nfft // 2 if nbins is None else int(nbins)
+    nb = (seg.nfft if seg.interbin else seg.nfft // 2) if nbins is None else int(nbins)
     fdt = torch.float32 if seg.precision == "f32" else torch.float64
     if write_F and F_out is None:
         F_out = torch.empty((nsky * nspin, nb), dtype=fdt, device="cuda")

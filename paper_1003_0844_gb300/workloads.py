@@ -58,6 +58,7 @@ class Workload:
     f0_range: tuple = (0.05, 0.20)
     F_thr: float = 20.0
     sigma: float = 1.0
+    interbin: bool = False  # F on the half-bin grid of an unpadded transform (Sec. VI.B)
 
     @property
     def n(self) -> int:
@@ -65,7 +66,7 @@ class Workload:
 
     @property
     def nbins(self) -> int:
-        return self.nfft // 2
+        return self.nfft if self.interbin else self.nfft // 2
 
     @property
     def S0(self) -> float:
@@ -80,6 +81,10 @@ WORKLOADS = {
                             n_inj=1, snr=(10.0, 10.0)),
     "grid_2d": Workload("grid_2d", days=2, dt=2.0, nfft=1 << 18, nsky=256, nspin=16,
                         n_inj=4, snr=(8.0, 20.0)),
+    # the 2-day grid with interbinning in place of padding by two: transform of 2^17
+    # points, F on the same 2^17-point half-bin grid as the padded 2^18 transform
+    "grid_2d_ib": Workload("grid_2d_ib", days=2, dt=2.0, nfft=1 << 17, nsky=256, nspin=16,
+                           n_inj=4, snr=(8.0, 20.0), interbin=True),
     "wide_6d": Workload("wide_6d", days=6, dt=0.5, nfft=1 << 21, nsky=512, nspin=32,
                         n_inj=8, snr=(8.0, 20.0), f0_range=(0.05, 0.95)),
     # small cases for tests: same structure, quick to evaluate on the CPU

@@ -206,3 +206,36 @@ def test_autotune_picks_a_valid_split(fs):
     assert max_rel_dF(F, ref) <= F32_TOL
     missing, bad = check_candidates(*cand, ref, wl.F_thr, len(f1))
     assert not missing and not bad
+
+
+# ------------------------------------------------------------------ interbinning
+
+@pytest.mark.parametrize("name,n,nfft,precision", [("small", None, 1 << 14, "f32"), ("small", None, 1 << 14, "f64"),
+                                                   ("grid_2d", None, 1 << 17, "f32"),
+                                                   ("wide_6d", 1033968, 1 << 20, "f32")])
+def test_interbinning_matches_oracle(fs, name, n, nfft, precision):
+    from oracle import fstat as ofs
+    wl, det, x, alpha, delta, f1 = make_case(name, nfft=nfft, nsky=2, nspin=2, n=n)
+    if name != "small":
+        alpha, delta, f1 = alpha[:1], delta[:1], f1[:1]
+    seg_o = ors.Segment(x, wl.dt)
+    ref = np.stack([ofs.fstat_interbinned(seg_o, a, d, s1, wl.fl, det, wl.S0, nfft)
+                    for a, d in zip(alpha, delta) for s1 in f1])
+    ctx = fs.Context(det)
+    xd = _dev(x, torch.float32 if precision == "f32" else torch.float64)
+    seg = fs.Segment(ctx, xd, wl.dt, nfft, wl.fl, wl.S0, precision=precision, interbin=True)
+    res = fs.search(ctx, seg, _dev(alpha), _dev(delta), _dev(f1), wl.F_thr)
+    assert ctx.sync_status() == 0
+    F = res.F.double().cpu().numpy()
+    assert F.shape == (len(alpha) * len(f1), nfft)
+    assert max_rel_dF(F, ref) <= (F32_TOL if precision == "f32" else 1e-8)
+    missing, bad = check_candidates(*res.candidates(), ref, wl.F_thr, len(f1))
+    assert not missing and not bad
+    # argument rules: the F row is nfft long; the batch and allocation-free paths refuse
+    with pytest.raises(fs.FstatError) as e:
+        fs.search(ctx, seg, _dev(alpha), _dev(delta), _dev(f1), wl.F_thr, nbins=nfft // 2)
+    assert e.value.status == 2
+    if precision == "f32":
+        with pytest.raises(fs.FstatError) as e:
+            fs.search_batch(ctx, [seg], _dev(alpha), _dev(delta), _dev(f1), wl.F_thr)
+        assert e.value.status == 7

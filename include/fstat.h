@@ -315,6 +315,41 @@ FS_API fs_status fs_threshold(double alpha, double n_cells, double *F0);
  * M <= 16), v_total the parameter-space volume in the same units. */
 FS_API fs_status fs_cell_count(int32_t M, const double *G_host, double v_total, double *n_cells);
 
+/* ---- Grid in the parameter space (Sec. IV, host functions, no device work) ----
+ * Reduced Fisher matrix (Eq. redFm-def) of the linear phase model (Eq. philin)
+ * with xi = (omega0, omega1, alpha1, alpha2) and m(t) = (t, t^2/2, mu1, mu2),
+ * mu1 = (R_ES^y + R_E^y cos eps)/c, mu2 = (R_ES^x + R_E^x)/c, for n samples of
+ * dt starting at epoch t0 (as fs_segment_desc.t0) in the detector's analytic
+ * Earth model.  G_host: 4 x 4 doubles, row-major [s^2]. */
+FS_API fs_status fs_linear_model_fisher(const fs_detector *det, int64_t n, double dt, double t0, double *G_host);
+/* Lattice covering with constraints (Sec. IV.B): from A2* (dim 2, Eq. A2gen)
+ * or A4* (dim 4, Eq. gen) of covering radius R = sqrt(1 - C0) in the
+ * coordinates where tau^T G tau = 1 - C0 is a sphere, shrunk along a lattice
+ * vector l by mu = |M^-1 a0|/|l| and expanded perpendicular to l by the nu
+ * that restores the covering radius R (Eq. condition: minimal match exactly
+ * C0), the l of largest mu nu^(dim-1) kept, l rotated onto M^-1 a0
+ * (Eq. opt) and, with constraint2 (dim 4), a second lattice vector rotated
+ * about it into the directions without sky components (Eq. opt2).
+ * basis_host: dim x dim doubles, rows are basis vectors in the units of G;
+ * row 0 = a0 = (dp0, 0, ...); with constraint2 row 1 has zero sky
+ * (last two) components (Eq. constraint2).  *theta_host: covering thickness
+ * theta_min / (mu nu^(dim-1)).  FS_ERR_ARG for G not positive definite or
+ * C0 outside (0, 1). */
+FS_API fs_status fs_lattice(int32_t dim, const double *G_host, double C0, double dp0, int32_t constraint2,
+                            double *basis_host, double *theta_host);
+/* Nodes of a 4-dimensional lattice (basis_host of fs_lattice with omega in
+ * rad/s) in the band fl + [f0_min, f0_max] Hz and spindowns [f1_min, f1_max]
+ * Hz/s over the whole sky, as template points (f0 above fl, f1 = omega1 /
+ * 2 pi, and the sky position of (alpha1, alpha2) = omega0 (n0_y, n0_x) in
+ * both ecliptic hemispheres, Eq. albe).  pts_host: capacity cap; *count: the
+ * number of nodes (FS_ERR_CAPACITY if above cap, the first cap stored).
+ * The basis must have the form fs_lattice gives with both constraints
+ * (FS_ERR_ARG otherwise); nodes are visited sky node by sky node, then
+ * spindown, then frequency. */
+FS_API fs_status fs_lattice_nodes(const double *basis_host, const fs_detector *det, double fl, double f0_min,
+                                  double f0_max, double f1_min, double f1_max, fs_point *pts_host, int64_t cap,
+                                  int64_t *count);
+
 /* Synchronise `stream` and return (and clear) the first device-side error
  * latched since the last call, or FS_OK. */
 FS_API fs_status fs_sync_status(fs_ctx *ctx, void *stream);

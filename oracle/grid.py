@@ -13,7 +13,8 @@ Fisher matrix is G_kl = <m_k m_l> - <m_k><m_l> (Eq. redFm-def).
 
 Construction (Sec. IV.B): with G = U0 D0^2 U0^T and M = U0 D0^-1 the correlation
 ellipsoid tau^T G tau = 1 - C0 becomes the sphere of radius R = sqrt(1 - C0) in
-x = M^-1 tau.  Start from the generator M0 of A_n* (rows are basis vectors,
+x = M^-1 tau (any M with M^T G M = I does; it is computed from the unit-diagonal
+scaling of G for accuracy).  Start from the generator M0 of A_n* (rows are basis vectors,
 covering radius R); pick a lattice vector l with |l| >= |e0|, e0 = M^-1 a0,
 a0 = (dp0, 0, ...); shrink along l by mu = |e0|/|l|; expand perpendicular to l
 by nu so that the covering radius returns to R (Eq. condition: the minimal match
@@ -245,8 +246,11 @@ def constrained_lattice(G: np.ndarray, C0: float, dp0: float, n_candidates: int 
     G = np.asarray(G, dtype=np.float64)
     dim = G.shape[0]
     R = math.sqrt(1.0 - C0)
-    w, U0 = np.linalg.eigh(G)
-    Mx = U0 @ np.diag(1.0 / np.sqrt(w))             # tau = Mx x
+    # tau = Mx x with Mx^T G Mx = I; G's entries span many decades (s^2 to s^4), so the
+    # eigendecomposition is taken of the unit-diagonal matrix D^-1 G D^-1, D = diag(G)^1/2
+    dg = np.sqrt(np.diag(G))
+    w, U0 = np.linalg.eigh(G / np.outer(dg, dg))
+    Mx = np.diag(1.0 / dg) @ U0 @ np.diag(1.0 / np.sqrt(w))
     a0 = np.zeros(dim)
     a0[0] = dp0
     e0 = np.linalg.solve(Mx, a0)

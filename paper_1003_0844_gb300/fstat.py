@@ -27,7 +27,8 @@ EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_seg_destroy", "f
            "fs_sync_status", "fs_strerror", "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling",
            "fs_get_stats", "fs_search_noalloc", "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune",
            "fs_fstat_points", "fs_refine", "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm_cell",
-           "fs_false_alarm", "fs_threshold", "fs_cell_count"]
+           "fs_false_alarm", "fs_threshold", "fs_cell_count", "fs_linear_model_fisher", "fs_lattice",
+           "fs_lattice_nodes"]
 PROF_KINDS = ("prepare", "demodulate", "pass1", "pass2", "other")
 
 
@@ -105,10 +106,15 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.fs_false_alarm.argtypes = [f64, f64, ctypes.POINTER(f64), ctypes.POINTER(f64)]
     lib.fs_threshold.argtypes = [f64, f64, ctypes.POINTER(f64)]
     lib.fs_cell_count.argtypes = [i32, ctypes.POINTER(f64), f64, ctypes.POINTER(f64)]
+    lib.fs_linear_model_fisher.argtypes = [ctypes.POINTER(_Detector), i64, f64, f64, ctypes.POINTER(f64)]
+    lib.fs_lattice.argtypes = [i32, ctypes.POINTER(f64), f64, f64, i32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
+    lib.fs_lattice_nodes.argtypes = [ctypes.POINTER(f64), ctypes.POINTER(_Detector), f64, f64, f64, f64, f64, vp,
+                                     i64, ctypes.POINTER(i64)]
     for name in ("fs_create", "fs_prepare_segment", "fs_seg_load", "fs_search", "fs_search_noalloc", "fs_sync_status",
                  "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling", "fs_get_stats",
                  "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune", "fs_fstat_points", "fs_refine",
-                 "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm", "fs_threshold", "fs_cell_count"):
+                 "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm", "fs_threshold", "fs_cell_count",
+                 "fs_linear_model_fisher", "fs_lattice", "fs_lattice_nodes"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -435,6 +441,49 @@ def cell_count(G, v_total: float) -> float:
     _check(lib.fs_cell_count(int(g.shape[0]), g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(v_total),
                              ctypes.byref(n)), "fs_cell_count")
     return n.value
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def linear_model_fisher(det, n: int, dt: float, t0: float = 0.0):
+    """Reduced Fisher matrix of the linear phase model (fs_linear_model_fisher), 4 x 4."""
+    import numpy as np
+    lib = load_library()
+    d = _Detector(det.lat, det.lon, det.gamma, det.eps, det.lambda_e0, det.theta_g0)
+    G = np.empty(16)
+    _check(lib.fs_linear_model_fisher(ctypes.byref(d), int(n), float(dt), float(t0), _dptr(G)),
+           "fs_linear_model_fisher")
+    return G.reshape(4, 4)
+
+
+def lattice(G, C0: float, dp0: float, constraint2: bool = True):
+    """Constrained lattice covering (fs_lattice): (basis rows, thickness)."""
+    import numpy as np
+    lib = load_library()
+    g = np.ascontiguousarray(np.asarray(G, dtype=np.float64))
+    dim = g.shape[0]
+    B = np.empty(dim * dim)
+    th = ctypes.c_double()
+    _check(lib.fs_lattice(dim, _dptr(g), float(C0), float(dp0), 1 if constraint2 else 0, _dptr(B), ctypes.byref(th)),
+           "fs_lattice")
+    return B.reshape(dim, dim), th.value
+
+
+def lattice_nodes(basis, det, fl: float, f0_range, f1_range, cap: int = 1 << 20):
+    """Template points (f0, f1, alpha, delta) of the lattice in a band (fs_lattice_nodes)."""
+    import numpy as np
+    lib = load_library()
+    b = np.ascontiguousarray(np.asarray(basis, dtype=np.float64))
+    d = _Detector(det.lat, det.lon, det.gamma, det.eps, det.lambda_e0, det.theta_g0)
+    pts = np.empty((cap, 4))
+    cnt = ctypes.c_int64()
+    st = lib.fs_lattice_nodes(_dptr(b), ctypes.byref(d), float(fl), float(f0_range[0]), float(f0_range[1]),
+                              float(f1_range[0]), float(f1_range[1]), pts.ctypes.data_as(ctypes.c_void_p), int(cap),
+                              ctypes.byref(cnt))
+    _check(st, "fs_lattice_nodes")
+    return pts[:cnt.value].copy()
 
 
 def demodulate(ctx: Context, seg: Segment, alpha: float, delta: float, stream=None):

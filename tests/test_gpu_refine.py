@@ -1,6 +1,8 @@
 """Fine search on the GPU (through the C ABI) against the oracle: exact F at
 continuous points, its gradient and the reduced Fisher matrix, the autograd
 wrapper, and the hill climb against the oracle's Nelder-Mead maximum."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -156,3 +158,54 @@ def test_amplitudes_match_oracle(fs):
     for p in range(len(P)):
         ref = orf.amplitude_estimates(xo, wl.dt, P[p], wl.fl, det)
         assert np.max(np.abs(amp[p] - ref)) <= 1e-9 * np.max(np.abs(ref)), (p, amp[p], ref)
+
+
+def test_constrained_lattice_covers_an_injected_signal(fs):
+    """The grid of Sec. IV (fs_lattice, fs_lattice_nodes) around a noise-free signal,
+    every node evaluated with the exact F: the best node keeps about C0 of the
+    signal's F.  The metric is the linear model's (Eq. philin), which fixes the
+    ecliptic components n_x, n_y of the sky direction and drops the part of r_d
+    perpendicular to the ecliptic (a diurnal phase omega0 (r_E/c) sin(eps) n_z, about
+    23 n_z rad here); between neighbouring nodes n_z changes by
+    -(n_x dn_x + n_y dn_y)/n_z, small near the ecliptic poles and large near the
+    ecliptic, so the source is placed at ecliptic latitude ~70 degrees."""
+    wl = W.WORKLOADS["small"]
+    det = W.detector_for(wl)
+    ce, se = math.cos(det.eps), math.sin(det.eps)
+    n_ecl = np.array([0.2, 0.25, math.sqrt(1 - 0.2 ** 2 - 0.25 ** 2)])
+    n_eq = np.array([n_ecl[0], ce * n_ecl[1] - se * n_ecl[2], se * n_ecl[1] + ce * n_ecl[2]])
+    alpha = math.atan2(n_eq[1], n_eq[0]) % (2 * math.pi)
+    delta = math.asin(n_eq[2])
+    inj = W.Injection(f0=0.0213, f1=-4e-9, alpha=alpha, delta=delta, psi=0.3, cos_iota=0.4, phi0=1.1, snr=25.0)
+    x = orsp.inject(wl.n, wl.dt, [inj], wl.fl, det, wl.sigma)
+    th = np.array([inj.f0, inj.f1, inj.alpha, inj.delta])
+    To = wl.n * wl.dt
+    C0 = 0.75
+    G = fs.linear_model_fisher(det, wl.n, wl.dt)
+    B, theta = fs.lattice(G, C0, math.pi / To)
+    assert 1.7655 < theta < 3.0
+    # the box spans the correlation ellipsoid's projections (one day: a sky offset trades
+    # against hundreds of frequency bins), then keeps the nodes within metric distance 1
+    half = math.sqrt(1 - C0) * np.sqrt(np.diag(np.linalg.inv(G))) / (2 * math.pi)
+    nodes = fs.lattice_nodes(B, det, wl.fl, (th[0] - 1.2 * half[0], th[0] + 1.2 * half[0]),
+                             (th[1] - 1.5 * half[1], th[1] + 1.5 * half[1]), cap=1 << 26)
+    tp = 2 * math.pi
+    ce, se = math.cos(det.eps), math.sin(det.eps)
+
+    def xi(p):
+        om0 = tp * (wl.fl + p[:, 0])
+        nx = np.cos(p[:, 2]) * np.cos(p[:, 3])
+        ny = ce * np.sin(p[:, 2]) * np.cos(p[:, 3]) + se * np.sin(p[:, 3])
+        return np.stack([om0, tp * p[:, 1], om0 * ny, om0 * nx], axis=1)
+
+    d = xi(nodes) - xi(th[None, :])
+    near = nodes[np.einsum("ij,jk,ik->i", d, G, d) <= 1.0]
+    assert 10 < len(near) < 100000
+    nodes = near
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x), wl.dt, wl.nfft, wl.fl, wl.S0, precision="f64")
+    F0, _, _ = fs.fstat_points(ctx, seg, _dev(th[None, :]), grad=False)
+    Fn, _, _ = fs.fstat_points(ctx, seg, _dev(nodes), grad=False)
+    assert ctx.sync_status() == 0
+    ratio = float(Fn.max() / F0[0])
+    assert ratio >= C0 - 0.05, ratio

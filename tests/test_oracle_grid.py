@@ -95,6 +95,7 @@ def test_constrained_four_dimensional_lattice():
     sky_scale = np.abs(gen[:, 2:]).max()
     assert np.all(np.abs(gen[1, 2:]) <= 1e-12 * sky_scale)
     assert abs(abs(np.linalg.det(gen)) - abs(np.linalg.det(d["gen_images"]))) <= 1e-9 * abs(np.linalg.det(gen))
+    assert np.allclose(d["Mx"].T @ G @ d["Mx"], np.eye(4), atol=1e-8)
     x = gen @ np.linalg.inv(d["Mx"].T)
     assert og.covering_radius(x)[0] == pytest.approx(d["R"], rel=1e-9)
     assert _brute_covering_radius(x, n=20000) <= d["R"] * (1 + 1e-9)

@@ -22,12 +22,30 @@ namespace fs {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Division by a runtime divisor d through one 64-bit multiply: q = (n m) >> 48
+// with m = ceil(2^48 / d) is exact for n < 2^31 and 1 <= d < 2^17 (the error
+// n (m - 2^48/d) / 2^48 < 2^-17 < 1/d never reaches the next integer); larger d
+// fall back to plain division.
+struct FastDiv {
+  uint32_t d;
+  uint64_t m;  // 0: use plain division
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f{d, 0};
+  if (d >= 1 && d < (1u << 17)) f.m = ((uint64_t(1) << 48) + d - 1) / d;
+  return f;
+}
+__device__ __forceinline__ int fdiv(int n, const FastDiv &f) {
+  return f.m ? (int)(((uint64_t)(uint32_t)n * f.m) >> 48) : (int)((uint32_t)n / f.d);
+}
+
 // ------------------------------------------------------------------ pass 1
 struct Pass1Args {
   const float2 *ya, *yb, *qq;
   int64_t sky_stride;
   const double *f1;
   int nspin, tmpl0;
+  FastDiv nspin_fd;  // division by nspin
   int N2, n1max;
   int64_t nfft;  // sub-transform length N1 N2
   // A template's transform of length Nfft = nfft << vshift (data no longer than
@@ -53,7 +71,8 @@ __device__ __forceinline__ float2 chirp_cycles(float f) {
 // One pass-1 work item: template tm (index within the group) and its column
 // tile, writing Z slot zs.  Needs P * 2 * CW threads; xch holds L * 2 * CW
 // float2, twL the table W_L^q (q < L).  The caller synchronises before and after.
-template <int P, int Q, int CW, int AM, int VS = 0>
+// N2T: N2 at compile time (0: A.N2 at run time); the sub-transform length is then P Q N2T.
+template <int P, int Q, int CW, int AM, int VS = 0, int N2T = 0>
 __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, int tile, float2 *xch,
                                            const float2 *twL) {
   constexpr int L = P * Q;
@@ -64,13 +83,13 @@ __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, i
   const int cs = lane % CS, col = cs % CW, sig = cs / CW;
   const int t = w * TPW + lane / CS;
   const int tr = tm >> VS, par = tm & ((1 << VS) - 1);
-  const int sky = tr / A.nspin, spin = tr - sky * A.nspin;
+  const int sky = fdiv(tr, A.nspin_fd), spin = tr - sky * A.nspin;
   const int n2 = tile * CW + col;
   const float2 *y = (sig ? A.yb : A.ya) + sky * A.sky_stride;
   const float2 *qq = A.qq + sky * A.sky_stride;
   const df32 f1 = df_from_double(A.f1[spin]);
   const int n1max = A.n1max;
-  const int64_t N2 = A.N2;
+  const int64_t N2 = N2T ? (int64_t)N2T : (int64_t)A.N2;
 
   float2 v[Q];
   // load y_j and the chirp exp(-2 pi i f1 Q_j); the two signal lanes of a
@@ -120,7 +139,7 @@ __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, i
   // inter-pass twiddle exp(-2 pi i n2 k1 / Nfft): anchors every 16 d from the
   // hardware sine/cosine (argument reduced to half a turn), and an exactly
   // rounded step for the recurrence between anchors so errors do not build up
-  const int64_t nf = A.nfft;
+  const int64_t nf = N2T ? (int64_t)L * N2T : A.nfft;
   const float inv_nf = 1.0f / (float)nf;
   const float2 step = expm2pi((float)(((int64_t)n2 * P) & (nf - 1)) * inv_nf);
   float2 wt = make_float2(1.f, 0.f);
@@ -157,6 +176,7 @@ struct Pass2Args {
   int64_t nfft;
   const float2 *norm;  // per sky of the group
   int nspin, tmpl0;
+  FastDiv nspin_fd;    // division by nspin
   int vshift;          // sub-transforms per template (see Pass1Args)
   int sky_base;        // global index of the group's first sky
   float *F;            // NULL or F_out + (global template of the group's first template) * nbins
@@ -187,7 +207,7 @@ struct Xch2 {
 // Pass-2 work item for 32-thread row DFTs (N2 = 1024): a warp holds one signal of
 // one row (warps 2r, 2r+1: signals a, b of row r), so an item covers WARPS/2
 // rows; the two signals' |X|^2 terms meet through the F tile.
-template <int Q, int WARPS, bool FULLBINS, int VS, bool XOUT = false>
+template <int Q, int WARPS, bool FULLBINS, int VS, bool XOUT = false, int N1T = 0>
 __device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
                                                 const float2 *twM) {
   constexpr int P = 32, R = WARPS / 2, S = Q / P;
@@ -200,8 +220,11 @@ __device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int 
   const int sig = w & 1, row = w >> 1;
   const int k1 = rt * R + row;
   const int tr = tm >> VS, par = tm & ((1 << VS) - 1);
-  const int sky = tr / A.nspin, spin = tr - sky * A.nspin;
-  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * A.nfft + (int64_t)k1 * A.N2;
+  const int sky = fdiv(tr, A.nspin_fd), spin = tr - sky * A.nspin;
+  constexpr int L2 = P * Q;
+  const int64_t N1 = N1T ? (int64_t)N1T : (int64_t)A.N1;
+  const int64_t nfft = N1T ? (int64_t)N1T * L2 : A.nfft;
+  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * nfft + (int64_t)k1 * L2;
   float2 v[Q];
   sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = __ldcg(z + Q * a + t + P * s); }); });
   float2 *xw = work + w * XW;
@@ -216,8 +239,8 @@ __device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int 
   __syncthreads();  // every warp is done with the exchange area (reused for the F tile)
   dft_inplace<Q, Q, D>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)
   if constexpr (XOUT) {
-    float2 *Xo = A.X + ((int64_t)zs * 2 + sig) * A.nfft + k1;
-    sfor<0, D>([&](auto d) { Xo[(int64_t)A.N1 * (t + P * d)] = v[d]; });
+    float2 *Xo = A.X + ((int64_t)zs * 2 + sig) * nfft + k1;
+    sfor<0, D>([&](auto d) { Xo[N1 * (t + P * d)] = v[d]; });
     return;
   }
   const float2 nrm = A.norm[sky];
@@ -245,7 +268,7 @@ __device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int 
             fs_candidate c;
             c.sky = (uint32_t)(A.sky_base + sky);
             c.spin = (uint32_t)spin;
-            c.bin = (uint32_t)(((k1 + A.N1 * k2) << VS) + par);
+            c.bin = (uint32_t)(((k1 + N1 * k2) << VS) + par);
             c.F = Fv;
             A.cand[idx] = c;
           } else {
@@ -261,17 +284,18 @@ __device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int 
   float *Fo = VS == 0 ? A.F + (int64_t)tm * A.nbins + rt * R : A.F + (int64_t)tr * A.nbins + par;
   for (int idx = threadIdx.x; idx < K2 * R; idx += blockDim.x) {
     const int k2 = idx / R, r = idx - k2 * R;
-    if constexpr (VS == 0) __stcs(Fo + r + (int64_t)A.N1 * k2, Fs[k2 * (R + 1) + r]);
-    else __stcs(Fo + ((rt * R + r + (int64_t)A.N1 * k2) << VS), Fs[k2 * (R + 1) + r]);
+    if constexpr (VS == 0) __stcs(Fo + r + N1 * k2, Fs[k2 * (R + 1) + r]);
+    else __stcs(Fo + ((rt * R + r + N1 * k2) << VS), Fs[k2 * (R + 1) + r]);
   }
 }
 
 // ALIAS_F: the F tile reuses the exchange area (one more barrier, less shared memory).
-template <int P, int Q, int WARPS, bool FULLBINS, bool ALIAS_F = false, int VS = 0, bool XOUT = false>
+// N1T: N1 at compile time (0: A.N1 at run time); the sub-transform length is then N1T P Q.
+template <int P, int Q, int WARPS, bool FULLBINS, bool ALIAS_F = false, int VS = 0, bool XOUT = false, int N1T = 0>
 __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
                                            const float2 *twM) {
   if constexpr (P == 32) {
-    pass2_item_wide<Q, WARPS, FULLBINS, VS, XOUT>(A, tm, zs, rt, work, twM);
+    pass2_item_wide<Q, WARPS, FULLBINS, VS, XOUT, N1T>(A, tm, zs, rt, work, twM);
     return;
   }
   constexpr int T = P, G = (P <= 16 ? 16 / P : 1), R = WARPS * G, S = Q / P;
@@ -284,8 +308,11 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
   const int row = w * G + gr;
   const int k1 = rt * R + row;
   const int tr = tm >> VS, par = tm & ((1 << VS) - 1);
-  const int sky = tr / A.nspin, spin = tr - sky * A.nspin;
-  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * A.nfft + (int64_t)k1 * A.N2;
+  const int sky = fdiv(tr, A.nspin_fd), spin = tr - sky * A.nspin;
+  constexpr int L2 = P * Q;
+  const int64_t N1 = N1T ? (int64_t)N1T : (int64_t)A.N1;
+  const int64_t nfft = N1T ? (int64_t)N1T * L2 : A.nfft;
+  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * nfft + (int64_t)k1 * L2;
   float2 v[Q];
   sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = __ldcg(z + Q * a + t + P * s); }); });
   float2 *xw = work + (w * 2 * G + (sig + 2 * gr)) * XW;
@@ -301,8 +328,8 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
   if constexpr (ALIAS_F) __syncthreads();  // every warp is done with the exchange area
   dft_inplace<Q, Q, (FULLBINS ? Q : Q / 2)>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)
   if constexpr (XOUT) {
-    float2 *Xo = A.X + ((int64_t)zs * 2 + sig) * A.nfft + k1;
-    sfor<0, D>([&](auto d) { Xo[(int64_t)A.N1 * (t + P * d)] = v[d]; });
+    float2 *Xo = A.X + ((int64_t)zs * 2 + sig) * nfft + k1;
+    sfor<0, D>([&](auto d) { Xo[N1 * (t + P * d)] = v[d]; });
     return;
   }
   const float2 nrm = A.norm[sky];
@@ -330,7 +357,7 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
           fs_candidate c;
           c.sky = (uint32_t)(A.sky_base + sky);
           c.spin = (uint32_t)spin;
-          c.bin = (uint32_t)(((k1 + A.N1 * k2) << VS) + par);
+          c.bin = (uint32_t)(((k1 + N1 * k2) << VS) + par);
           c.F = Fv;
           A.cand[idx] = c;
         } else {
@@ -346,8 +373,8 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
   constexpr int K2 = D * P;
   for (int idx = threadIdx.x; idx < K2 * R; idx += blockDim.x) {
     const int k2 = idx / R, r = idx - k2 * R;
-    if constexpr (VS == 0) __stcs(Fo + r + (int64_t)A.N1 * k2, Fs[k2 * (R + 1) + r]);
-    else __stcs(Fo + ((rt * R + r + (int64_t)A.N1 * k2) << VS), Fs[k2 * (R + 1) + r]);
+    if constexpr (VS == 0) __stcs(Fo + r + N1 * k2, Fs[k2 * (R + 1) + r]);
+    else __stcs(Fo + ((rt * R + r + N1 * k2) << VS), Fs[k2 * (R + 1) + r]);
   }
 }
 
@@ -392,6 +419,7 @@ __global__ void __launch_bounds__(32 * WARPS, 2) k_pass2(Pass2Args A) {
 // continues (results are then invalid, the device stays responsive).
 struct QueueArgs {
   int ntm, tiles1, tiles2, lag, slots;
+  FastDiv ipr_fd, slots_fd;  // division by kr (tiles1 + tiles2) and by slots
   int kr;             // templates per round: a round holds the pass-1 items of kr templates,
                       // then the pass-2 items of the kr templates lag rounds earlier
   unsigned *counter;  // [1 + 2 ntm]: next item, pass-1 done per template, pass-2 done per template
@@ -432,7 +460,10 @@ __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2,
   unsigned *done1 = Qa.counter + 1;
   unsigned *done2 = Qa.counter + 1 + Qa.ntm;
   const int kr = Qa.kr;
-  const int ipr = kr * (Qa.tiles1 + Qa.tiles2);
+  // items per template of each pass, fixed by the shape (the host's queue_tiles agrees)
+  constexpr int T1 = (P2 * Q2) / CW;
+  constexpr int T2 = (P1 * Q1) / (P2 <= 16 ? (NT / 32) * (16 / P2) : (NT / 32) / 2);
+  const int ipr = kr * (T1 + T2);
   const int total = ((Qa.ntm + kr - 1) / kr + Qa.lag) * ipr;
   // Items are decoded identically by every thread; thread 0 takes the next item
   // from the queue while the current one runs, checks whether the next item's
@@ -445,17 +476,17 @@ __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2,
   };
   auto decode = [&](int it) {
     Item d;
-    const int r = it / ipr;
+    const int r = fdiv(it, Qa.ipr_fd);
     const int jr = it - r * ipr;
-    d.is1 = jr < kr * Qa.tiles1;
+    d.is1 = jr < kr * T1;
     if (d.is1) {
-      const int k = jr / Qa.tiles1;
-      d.j = jr - k * Qa.tiles1;
+      const int k = jr / T1;
+      d.j = jr - k * T1;
       d.tm = r * kr + k;
     } else {
-      const int j2 = jr - kr * Qa.tiles1;
-      const int k = j2 / Qa.tiles2;
-      d.j = Qa.tiles1 + (j2 - k * Qa.tiles2);
+      const int j2 = jr - kr * T1;
+      const int k = j2 / T2;
+      d.j = T1 + (j2 - k * T2);
       d.tm = (r - Qa.lag) * kr + k;
     }
     d.valid = it < total && d.tm >= 0 && d.tm < Qa.ntm;
@@ -463,8 +494,8 @@ __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2,
   };
   auto dep_met = [&](const Item &d) {  // thread 0 only
     if (!d.valid) return true;
-    if (d.is1) return d.tm < Qa.slots || ld_acquire(done2 + (d.tm - Qa.slots)) >= (unsigned)Qa.tiles2;
-    return ld_acquire(done1 + d.tm) >= (unsigned)Qa.tiles1;
+    if (d.is1) return d.tm < Qa.slots || ld_acquire(done2 + (d.tm - Qa.slots)) >= (unsigned)T2;
+    return ld_acquire(done1 + d.tm) >= (unsigned)T1;
   };
   __shared__ int s_next[2], s_ready[2];
   if (threadIdx.x == 0) {
@@ -482,15 +513,17 @@ __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2,
       if (!ready) {
         if (threadIdx.x == 0) {
           if (d.is1) {
-            if (d.tm >= Qa.slots) wait_at_least(done2 + (d.tm - Qa.slots), Qa.tiles2, A2.flags);
+            if (d.tm >= Qa.slots) wait_at_least(done2 + (d.tm - Qa.slots), T2, A2.flags);
           } else {
-            wait_at_least(done1 + d.tm, Qa.tiles1, A2.flags);
+            wait_at_least(done1 + d.tm, T1, A2.flags);
           }
         }
         __syncthreads();
       }
-      if (d.is1) pass1_item<P1, Q1, CW, AM, VS>(A1, d.tm, d.tm % Qa.slots, d.j, work, twL);
-      else pass2_item<P2, Q2, NT / 32, false, true, VS>(A2, d.tm, d.tm % Qa.slots, d.j - Qa.tiles1, work, twM);
+      // the items take N1, N2 at run time: compiled in, they measured 5.5% slower here
+      const int zs = d.tm - fdiv(d.tm, Qa.slots_fd) * Qa.slots;
+      if (d.is1) pass1_item<P1, Q1, CW, AM, VS, 0>(A1, d.tm, zs, d.j, work, twL);
+      else pass2_item<P2, Q2, NT / 32, false, true, VS, false, 0>(A2, d.tm, zs, d.j - T1, work, twM);
     }
     if (threadIdx.x == 0) {
       s_next[buf ^ 1] = nxt;

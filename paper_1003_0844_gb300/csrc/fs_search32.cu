@@ -367,6 +367,7 @@ static void pass_args(const fs_seg *seg, const Cfg32 &c, const Ws32 &w, const do
   p1->sky_stride = w.stride;
   p1->f1 = f1;
   p1->nspin = nspin;
+  p1->nspin_fd = make_fastdiv((uint32_t)nspin);
   p1->N2 = c.sh.N2;
   p1->n1max = c.n1max;
   p1->nfft = c.nsub;
@@ -380,6 +381,7 @@ static void pass_args(const fs_seg *seg, const Cfg32 &c, const Ws32 &w, const do
   p2->nfft = c.nsub;
   p2->norm = w.norm;
   p2->nspin = nspin;
+  p2->nspin_fd = make_fastdiv((uint32_t)nspin);
   p2->vshift = c.vshift;
   p2->thr = thr;
   p2->cand = cand;
@@ -426,6 +428,8 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
       qa.kr = c.qs.kr;
       qa.lag = c.qs.lag;
       qa.slots = c.qs.slots;
+      qa.ipr_fd = make_fastdiv((uint32_t)(qa.kr * (qa.tiles1 + qa.tiles2)));
+      qa.slots_fd = make_fastdiv((uint32_t)qa.slots);
       qa.counter = w.counters;
       if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)ntm), st) != cudaSuccess)
         return FS_ERR_CUDA;
@@ -599,6 +603,8 @@ fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
     qa.kr = 1;
     qa.lag = lag;
     qa.slots = slots;
+    qa.ipr_fd = make_fastdiv((uint32_t)(qa.kr * (qa.tiles1 + qa.tiles2)));
+    qa.slots_fd = make_fastdiv((uint32_t)qa.slots);
     qa.counter = w.counters;
     // the array keeps the previous call's contents: the queue counters start at zero
     if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)nspin), st) != cudaSuccess)

@@ -40,7 +40,8 @@ METRICS = {
     "refine_2d": "fine-search candidates/s (20 Newton steps on the exact F, N=86,164) on 1 GB300",
 }
 FP64_PEAK_TFLOPS = 1.25          # nominal FP64 rate of a GB300 (no measured figure)
-REFINE_FLOP_PER_SAMPLE = 700.0   # FP64 flops per sample and point of the Hessian pass
+REFINE_FLOP_PER_SAMPLE = 687.0   # FP64 flops per sample and point of the Hessian pass, from ncu's
+                                 # DFMA/DMUL/DADD counts (profiles/k_points_refine_2d.md)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
@@ -56,6 +57,7 @@ def _args():
     p.add_argument("--quick", action="store_true", help="skip the CPU baseline and FP64 comparison")
     p.add_argument("--nsky", type=int, default=None, help="override the sky count (profiling runs, batch sky subset)")
     p.add_argument("--tune", action="store_true", help="run the launch tuner for each transform length first")
+    p.add_argument("--cands", type=int, default=1024, help="fine-search workload: candidates refined per step")
     return p.parse_args()
 
 
@@ -368,7 +370,7 @@ def main_refine(args):
     ncand_all = min(int(res.n_cand.item()), res.cand.shape[0])
     # the 1024 strongest crossings
     Fc = res.cand[:ncand_all, 3].view(torch.float32)
-    top = torch.argsort(Fc, descending=True)[:1024]
+    top = torch.argsort(Fc, descending=True)[:args.cands]
     cand = res.cand[top].contiguous()
     npt, nsteps = cand.shape[0], 20
 
@@ -418,7 +420,8 @@ def main_refine(args):
         "roofline": {"kernel": "k_points<Hessian> (21 passes per step)", "bound": "fp64", "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": None, "peak_kind": "nominal FP64 rate (no measured FP64 peak)",
-                     "flop_convention": "%d FP64 flop per sample and point per pass" % REFINE_FLOP_PER_SAMPLE},
+                     "flop_convention": "%d FP64 flop per sample and point per pass (ncu opcode counts)"
+                                        % REFINE_FLOP_PER_SAMPLE},
         "gpu_launches": int(stats["launches"]),
         "clocks": ck,
         "F_gain": {"median": float(np.median(gain)), "max": float(np.max(gain))},

@@ -10,7 +10,10 @@ Modules and the parts of the paper they follow:
 
 * ``earth``     analytic Earth: sky vector (Eq. pha4), detector position
                 (Eq. pha5), the scalar product n0.r_d (Sec. II), site vector
-                on the ellipsoid and Earth rotation (Sec. V).
+                on the ellipsoid and Earth rotation (Sec. V); or a caller's
+                table of the detector position and velocity on the sample grid
+                (the ephemerides of Sec. V), read by linear extrapolation from
+                the nearest grid point.
 * ``response``  amplitude modulation functions a(t), b(t) (Sec. II; formulas
                 of the cited interferometer response paper, Eqs. 12-13 there),
                 the four-amplitude signal model (Eqs. sig, eq:ab, eq:ampone,

@@ -52,7 +52,7 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="grid_2d")
-    p.add_argument("--cpu-templates", type=int, default=48, help="oracle sample size (templates)")
+    p.add_argument("--cpu-templates", type=int, default=320, help="oracle sample size (templates, ~10 s on one core)")
     p.add_argument("--fp64-skies", type=int, default=2, help="skies of the plain FP64 form comparison")
     p.add_argument("--quick", action="store_true", help="skip the CPU baseline and FP64 comparison")
     p.add_argument("--nsky", type=int, default=None, help="override the sky count (profiling runs, batch sky subset)")
@@ -130,6 +130,52 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cufft_comparison(nfft, nbins, reps=10):
+    """cuFFT (through torch.fft), timed for comparison only, on the transforms a
+    template needs: two zero-padded complex series of length nfft per template
+    (chirp and padding already applied: not timed), batched C2C FP32 FFT, the same
+    followed by F on nbins bins from |X|^2 with PyTorch elementwise kernels, and the
+    batched Z2Z FP64 FFT (beside the plain FP64 form).  Each batch is larger than
+    L2.  Returns templates/s for each."""
+    import torch
+
+    def timed(fn, B):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return {"value": B * reps / (e0.elapsed_time(e1) / 1e3), "unit": "templates/s", "batch_templates": B}
+
+    out = {}
+    g = torch.Generator(device="cuda").manual_seed(7)
+    for dt, esz in ((torch.complex64, 8), (torch.complex128, 16)):
+        B = max(4, (256 << 20) // (2 * nfft * esz))
+        x = torch.randn((B, 2, nfft), dtype=dt, device="cuda", generator=g)
+        X = torch.empty_like(x)
+        if dt == torch.complex64:
+            F = torch.empty((B, nbins), dtype=torch.float32, device="cuda")
+            w = torch.tensor([0.6, 0.4], dtype=torch.float32, device="cuda").view(1, 2, 1)
+            out["fft_only"] = timed(lambda: torch.fft.fft(x, dim=-1, out=X), B)
+
+            def fft_and_F():
+                torch.fft.fft(x, dim=-1, out=X)
+                torch.sum(torch.view_as_real(X[..., :nbins]).square().sum(-1) * w, dim=1, out=F)
+
+            out["fft_and_F"] = timed(fft_and_F, B)
+            del F
+        else:
+            out["fft_only_fp64"] = timed(lambda: torch.fft.fft(x, dim=-1, out=X), B)
+        del x, X
+    out["note"] = ("cuFFT via torch.fft, batched C2C FP32 (and Z2Z FP64) of 2 x %d points per template; "
+                   "chirp and zero padding not timed (an upper bound on a cuFFT-based search)" % nfft)
+    return out
 
 
 def cpu_oracle_rate(x, wl, det, alpha, delta, f1, ntempl):
@@ -611,6 +657,7 @@ def main():
                              "note": "plain all-FP64 path (radix-2 FP64 FFT), search only"}
         line["max_rel_dF_vs_fp64"] = drel
         seg64.close()
+        line["cufft_comparison"] = cufft_comparison(wl.nfft, nbins)
         # the oracle on the host cores, bounded sample
         xh = x32.cpu().numpy()
         # bounded sample: about 10-30 s of oracle time (a template costs ~N)

@@ -140,6 +140,24 @@ FS_API void fs_destroy(fs_ctx *ctx);
  * FS_ERR_NONFINITE.  Release with fs_seg_destroy. */
 FS_API fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *desc,
                              const void *x_dev, void *stream);
+/* fs_prepare_segment with the detector position taken from the caller's table
+ * instead of the analytic Earth (Sec. V reads it from ephemerides).
+ * r_dev, v_dev: device arrays of 3 x n doubles, component-major (x[0..n),
+ *   y[0..n), z[0..n)): r_d(t_m)/c in light-seconds and v_d(t_m)/c, t_m = m dt
+ *   (m < n, t = 0 at the segment's first sample), components in the SSB frame
+ *   of Eq. pha5 (ecliptic axes: the delay is n0 . r_d with n0 of Eq. pha4).
+ * Off the grid the position is extrapolated linearly from the nearest grid
+ * point m, clamped to [0, n): r_d(t)/c = r_m + (t - t_m) v_m.  The sidereal
+ * angle of a(t), b(t) still comes from the detector and desc->t0.  The
+ * segment copies the table (64 bytes per sample; fs_seg_load keeps it) and
+ * every search, FP32 or FP64, and the fine search use it.  Entries that are
+ * not finite, or farther than 600 light-seconds from the SSB, latch
+ * FS_ERR_NONFINITE and are taken as zero.  Same arguments and errors as
+ * fs_prepare_segment otherwise; FS_ERR_ARG for a null table pointer.
+ * (fs_inject always uses the analytic Earth.) */
+FS_API fs_status fs_prepare_segment_eph(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *desc,
+                                        const void *x_dev, const double *r_dev, const double *v_dev,
+                                        void *stream);
 FS_API void fs_seg_destroy(fs_seg *seg);
 
 /* Coarse search over nsky x nspin templates (Eq. OS on every bin).

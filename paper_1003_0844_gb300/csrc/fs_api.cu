@@ -97,6 +97,10 @@ static void seg_release(fs_seg *s) {
   cudaFree(s->blu_bhat);
   cudaFree(s->blu_tw);
   cudaFree(s->etab64);
+  cudaFree(s->eph);
+  cudaFree(s->eph0);
+  cudaFree(s->eph1);
+  cudaFree(s->eph2);
   delete s;
 }
 
@@ -121,8 +125,10 @@ void fs_destroy(fs_ctx *ctx) {
   delete ctx;
 }
 
-fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d, const void *x_dev,
-                             void *stream) {
+// Both preparation entry points: r, v NULL for the analytic Earth, else the
+// caller's position table (copied before the first load builds the tables).
+static fs_status prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d, const void *x_dev,
+                                 const double *r_eph, const double *v_eph, void *stream) {
   if (!ctx || !seg || !d || !x_dev) return FS_ERR_ARG;
   *seg = nullptr;
   if (d->n < 16 || !(d->dt > 0.0) || !(d->S0 > 0.0) || !isfinite(d->fl) || !isfinite(d->dt)) return FS_ERR_ARG;
@@ -150,7 +156,7 @@ fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d
   g.dt = d->dt;
   g.fl = d->fl;
   g.S0 = d->S0;
-  g.margin = (int64_t)ceil(kMaxDelay / d->dt) + 4;
+  g.margin = (int64_t)ceil((r_eph ? kMaxDelayEph : kMaxDelay) / d->dt) + 4;
   g.ngrid = g.n + 2 * g.margin;
   set_epoch(ctx->det, d->t0, &g);
   double re, z;
@@ -169,19 +175,38 @@ fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d
   } else if (ok) {
     ok = cudaMalloc(&s->coef, sizeof(dcoef4) * 2 * n) == cudaSuccess;
   }
+  if (ok && r_eph) {
+    ok = cudaMalloc(&s->eph, sizeof(dbl4) * 2 * n) == cudaSuccess;
+    if (ok && d->precision == FS_PREC_F32)
+      ok = cudaMalloc(&s->eph0, sizeof(float4) * g.ngrid) == cudaSuccess &&
+           cudaMalloc(&s->eph1, sizeof(float4) * g.ngrid) == cudaSuccess &&
+           cudaMalloc(&s->eph2, sizeof(float) * g.ngrid) == cudaSuccess;
+  }
   if (!ok) {
     cudaGetLastError();
     seg_release(s);
     return FS_ERR_NOMEM;
   }
   ctx->segs.insert(s);
-  fs_status r = fs_seg_load(s, x_dev, stream);
+  fs_status r = r_eph ? import_eph(s, r_eph, v_eph, st) : FS_OK;
+  if (r == FS_OK) r = fs_seg_load(s, x_dev, stream);
   if (r != FS_OK) {
     fs_seg_destroy(s);
     return r;
   }
   *seg = s;
   return FS_OK;
+}
+
+fs_status fs_prepare_segment(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d, const void *x_dev,
+                             void *stream) {
+  return prepare_segment(ctx, seg, d, x_dev, nullptr, nullptr, stream);
+}
+
+fs_status fs_prepare_segment_eph(fs_ctx *ctx, fs_seg **seg, const fs_segment_desc *d, const void *x_dev,
+                                 const double *r_dev, const double *v_dev, void *stream) {
+  if (!r_dev || !v_dev) return FS_ERR_ARG;
+  return prepare_segment(ctx, seg, d, x_dev, r_dev, v_dev, stream);
 }
 
 fs_status fs_seg_load(fs_seg *s, const void *x_dev, void *stream) {

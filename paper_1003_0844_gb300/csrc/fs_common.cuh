@@ -19,6 +19,7 @@ constexpr double kEllA = 6378140.0;                // m, ellipsoid semi-major ax
 constexpr double kEllF = 0.00335281;               // flattening, NOVAS value (Sec. V)
 constexpr double kAUls = kAU / kC;                 // 1 AU in light-seconds
 constexpr double kMaxDelay = 500.0;                // bound on |phi_m| [s] (AU/c + Earth radius/c)
+constexpr double kMaxDelayEph = 600.0;             // bound on |r_d/c| [s] accepted from a caller's table
 
 // Device-side error bits latched in the context flag word.
 enum : uint32_t { ERRF_CAPACITY = 1u, ERRF_NONFINITE = 2u, ERRF_TIMEOUT = 4u };
@@ -87,6 +88,11 @@ __device__ __forceinline__ float2 expm2pi(float f) {
   float s, c; sincospif(2.0f * f, &s, &c); return make_float2(c, -s);
 }
 
+// Four doubles, 32-byte aligned (one vector load; CUDA 13 deprecates the
+// unannotated double4).
+struct alignas(32) dbl4 { double x, y, z, w; };
+__host__ __device__ inline dbl4 make_dbl4(double x, double y, double z, double w) { return dbl4{x, y, z, w}; }
+
 // Cubic spline coefficients of one interval in FP64 (c0, c1, c2, c3).
 struct alignas(32) dcoef4 { double x, y, z, w; };
 
@@ -94,6 +100,7 @@ struct alignas(32) dcoef4 { double x, y, z, w; };
 // Per-sky constants of the FP32 demodulation kernel (computed in FP64 per sky).
 struct SkyConst32 {
   df32 nx, nyp;      // n0 components multiplying R_ES^x and R_ES^y (Sec. II scalar product)
+  df32 nz;           // n0 component along the ecliptic pole (a caller's position table)
   float ca, sa;      // cos(alpha), sin(alpha)
   float rcd, zsd;    // (r_e/c) cos(delta), (z/c) sin(delta)  [s]
   float ea[5];       // a = ea0 cos2x + ea1 sin2x + ea2 cos x + ea3 sin x + ea4, x = alpha - theta
@@ -101,7 +108,7 @@ struct SkyConst32 {
 };
 // FP64 counterpart.
 struct SkyConst64 {
-  double nx, nyp, ca, sa, rcd, zsd;
+  double nx, nyp, nz, ca, sa, rcd, zsd;
   double ea[5];
   double eb[4];
 };

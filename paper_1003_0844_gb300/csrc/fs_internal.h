@@ -73,6 +73,13 @@ struct fs_seg {
   // FP64 (cos, sin) of the orbital and sidereal angles on t_k = k dt, built by
   // the first fine-search call
   void *etab64 = nullptr;
+  // caller's position table (fs_prepare_segment_eph), else NULL:
+  //   eph[2m] = (r_m, 0), eph[2m + 1] = (v_m, 0), m < n (light-seconds, SSB ecliptic frame)
+  fs::dbl4 *eph = nullptr;
+  // its FP32-path form on the grid t_m, m in [-margin, n + margin) (clamped linear extrapolation):
+  //   eph0[m] = (r_x.hi, r_x.lo, r_y.hi, r_y.lo), eph1[m] = (r_z.hi, r_z.lo, v_x, v_y), eph2[m] = v_z
+  float4 *eph0 = nullptr, *eph1 = nullptr;
+  float *eph2 = nullptr;
 };
 
 // ---- launchers implemented in the .cu files (all asynchronous on `st`) ----
@@ -90,6 +97,8 @@ cudaError_t fft64_twiddles(double2 *tw, int64_t n, cudaStream_t st);
 
 // Segment preparation (P0 tables, P1 upsampling, P2 spline).
 fs_status prepare_tables(fs_seg *seg, cudaStream_t st);
+// Copy a caller's position table (component-major r, v, 3 x n each) into seg->eph.
+fs_status import_eph(fs_seg *seg, const double *r, const double *v, cudaStream_t st);
 fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st);
 fs_status prepare_spline(fs_seg *seg, cudaStream_t st);
 

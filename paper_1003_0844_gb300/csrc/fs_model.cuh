@@ -44,6 +44,7 @@ __host__ __device__ inline void sky_constants(double alpha, double delta, double
   double ca = cos(alpha), sa = sin(alpha), cd = cos(delta), sd = sin(delta);
   k->nx = ca * cd;
   k->nyp = sa * cd * cos(eps) + sd * sin(eps);
+  k->nz = -sa * cd * sin(eps) + sd * cos(eps);
   k->ca = ca;
   k->sa = sa;
   k->rcd = g.re_c * cd;
@@ -75,18 +76,41 @@ __device__ inline void ab_eval64(const SkyConst64 &K, double cx, double sx, doub
   *b = K.eb[0] * c2 + K.eb[1] * s2 + K.eb[2] * cx + K.eb[3] * sx;
 }
 
-// Source time t with t + phi_m(t) = tb (Eq. eq:Bt) by Newton's method in FP64.
-__device__ inline double source_time64(double tb, const SkyConst64 &K, const SegGeom &g, Geo64 *geo) {
+// The same from a caller's position table eph[2m] = (r_m, 0), eph[2m + 1] =
+// (v_m, 0) on t_m = m dt: r(t) = r_m + (t - t_m) v_m from the nearest grid
+// point m clamped to [0, n); phi = n0 . r(t), phidot = n0 . v_m.  The sidereal
+// angle (for a, b) is the analytic one.
+__device__ inline Geo64 geometry64_eph(double t, const SkyConst64 &K, const SegGeom &g, const dbl4 *eph) {
+  double mf = rint(t / g.dt);
+  mf = fmin(fmax(mf, 0.0), (double)(g.n - 1));
+  const int64_t m = (int64_t)mf;
+  const double tau = t - mf * g.dt;
+  const dbl4 r = eph[2 * m], v = eph[2 * m + 1];
+  double sth, cth;
+  sincos(g.theta0 + kOmegaR * t, &sth, &cth);
+  Geo64 q;
+  q.phidot = K.nx * v.x + K.nyp * v.y + K.nz * v.z;
+  q.phi = K.nx * r.x + K.nyp * r.y + K.nz * r.z + tau * q.phidot;
+  q.cx = K.ca * cth + K.sa * sth;
+  q.sx = K.sa * cth - K.ca * sth;
+  return q;
+}
+
+// Source time t with t + phi_m(t) = tb (Eq. eq:Bt) by Newton's method in FP64;
+// eph: NULL for the analytic Earth, else the caller's table.
+__device__ inline double source_time64(double tb, const SkyConst64 &K, const SegGeom &g, Geo64 *geo,
+                                       const dbl4 *eph = nullptr) {
+  auto geom = [&](double tt) { return eph ? geometry64_eph(tt, K, g, eph) : geometry64(tt, K, g); };
   double t = tb;
-  Geo64 q = geometry64(t, K, g);
+  Geo64 q = geom(t);
   t = tb - q.phi;
 #pragma unroll 1
   for (int it = 0; it < 3; it++) {
-    q = geometry64(t, K, g);
+    q = geom(t);
     double gres = t + q.phi - tb;
     t -= gres / (1.0 + q.phidot);
   }
-  *geo = geometry64(t, K, g);
+  *geo = geom(t);
   return t;
 }
 

@@ -34,10 +34,57 @@ __global__ void k_tables32(SegGeom g, float4 *tab0, float4 *tab1) {
   tab1[i] = make_float4((float)cth, (float)sth, T.hi, T.lo);
 }
 
+// A caller's position table (Sec. V: the ephemerides), component-major r and v,
+// into (r, 0), (v, 0) pairs; entries that are not finite or beyond
+// kMaxDelayEph light-seconds latch ERRF_NONFINITE and are taken as zero.
+__global__ void k_eph_import(const double *r, const double *v, int64_t n, dbl4 *eph, uint32_t *flags) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double rx = r[m], ry = r[n + m], rz = r[2 * n + m];
+  double vx = v[m], vy = v[n + m], vz = v[2 * n + m];
+  const double r2 = rx * rx + ry * ry + rz * rz;
+  const bool ok = isfinite(rx) && isfinite(ry) && isfinite(rz) && isfinite(vx) && isfinite(vy) && isfinite(vz) &&
+                  r2 <= kMaxDelayEph * kMaxDelayEph && vx * vx + vy * vy + vz * vz <= 1.0;
+  if (!ok) {
+    atomicOr(flags, ERRF_NONFINITE);
+    rx = ry = rz = vx = vy = vz = 0.0;
+  }
+  eph[2 * m] = make_dbl4(rx, ry, rz, 0.0);
+  eph[2 * m + 1] = make_dbl4(vx, vy, vz, 0.0);
+}
+
+// FP32-path form of the table on the grid with margins: position at t_m by
+// linear extrapolation from the nearest table point (clamped), as double-floats.
+__global__ void k_eph_tables32(SegGeom g, const dbl4 *eph, float4 *e0, float4 *e1, float *e2) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.ngrid) return;
+  const int64_t m = i - g.margin;
+  const int64_t mc = m < 0 ? 0 : (m >= g.n ? g.n - 1 : m);
+  const double tau = (double)(m - mc) * g.dt;
+  const dbl4 r = eph[2 * mc], v = eph[2 * mc + 1];
+  const df32 X = df_from_double(r.x + tau * v.x), Y = df_from_double(r.y + tau * v.y),
+             Z = df_from_double(r.z + tau * v.z);
+  e0[i] = make_float4(X.hi, X.lo, Y.hi, Y.lo);
+  e1[i] = make_float4(Z.hi, Z.lo, (float)v.x, (float)v.y);
+  e2[i] = (float)v.z;
+}
+
+fs_status import_eph(fs_seg *seg, const double *r, const double *v, cudaStream_t st) {
+  const int64_t n = seg->g.n;
+  k_eph_import<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(r, v, n, seg->eph, seg->ctx->d_flags);
+  seg->ctx->launches++;
+  return cuda_status(cudaGetLastError());
+}
+
 fs_status prepare_tables(fs_seg *seg, cudaStream_t st) {
   const SegGeom &g = seg->g;
   k_tables32<<<(unsigned)((g.ngrid + 255) / 256), 256, 0, st>>>(g, seg->tab0, seg->tab1);
   seg->ctx->launches++;
+  if (seg->eph) {
+    k_eph_tables32<<<(unsigned)((g.ngrid + 255) / 256), 256, 0, st>>>(g, seg->eph, seg->eph0, seg->eph1,
+                                                                      seg->eph2);
+    seg->ctx->launches++;
+  }
   return cuda_status(cudaGetLastError());
 }
 

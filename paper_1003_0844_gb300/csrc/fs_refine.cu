@@ -5,7 +5,8 @@
 // hill climb from the coarse-search candidates that uses them.
 //
 // Per sample k (t_k = k dt) and point:
-//   phi_k = n0 . r_d(t_k) / c (Eq. pham) and its alpha, delta derivatives,
+//   phi_k = n0 . r_d(t_k) / c (Eq. pham) and its alpha, delta derivatives
+//   (analytic Earth, or the caller's position table at t_k),
 //   a_k, b_k and their derivatives (x = alpha - theta(t) and the delta
 //   dependence of the coefficients),
 //   Phi_k = f0 (t_k + phi_k) + fl phi_k + f1 (t_k^2/2 + t_k phi_k)   [cycles],
@@ -32,14 +33,14 @@ constexpr int kPtSamples = 32;   // samples per thread per block
 
 // Per-segment FP64 table on t_k = k dt: (cos, sin) of the orbital longitude
 // lambda_E(t_k) and of the local sidereal angle theta(t_k).
-__global__ void k_earth_table64(SegGeom g, double4 *tab) {
+__global__ void k_earth_table64(SegGeom g, dbl4 *tab) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= g.n) return;
   const double t = (double)k * g.dt;
   double sl, cl, sth, cth;
   sincos(g.lambda0 + kOmegaO * t, &sl, &cl);
   sincos(g.theta0 + kOmegaR * t, &sth, &cth);
-  tab[k] = make_double4(cl, sl, cth, sth);
+  tab[k] = make_dbl4(cl, sl, cth, sth);
 }
 
 // Per-point constants: the ecliptic-frame components of n0 (Eq. pha4) and of
@@ -51,6 +52,9 @@ struct PointConst {
   double nx, nyp, nx_a, nyp_a, nx_d, nyp_d, nx_aa, nyp_aa, nx_ad, nyp_ad, nx_dd, nyp_dd;
   double rcd, rcd_d, rcd_dd, zsd, zsd_d, zsd_dd;
   double ea[5], eb[4], ea_d[5], eb_d[4], ea_dd[5], eb_dd[4];
+  // n0 and its derivatives as full ecliptic-frame vectors (a caller's position table):
+  // [0] n0, [1] d/dalpha, [2] d/ddelta, [3] d2/dalpha2, [4] d2/dalpha ddelta, [5] d2/ddelta2
+  double n3[6][3];
 };
 
 __global__ void k_point_constants(const fs_point *pts, int npt, SegGeom g, fs_detector det, PointConst *out) {
@@ -84,6 +88,16 @@ __global__ void k_point_constants(const fs_point *pts, int npt, SegGeom g, fs_de
   c.zsd = g.z_c * sd;
   c.zsd_d = g.z_c * cd;
   c.zsd_dd = -g.z_c * sd;
+  {
+    // equatorial components of n and its derivatives, rotated to the ecliptic frame (Eq. pha4)
+    const double q[6][3] = {{ca * cd, sa * cd, sd},        {-sa * cd, ca * cd, 0.0}, {-ca * sd, -sa * sd, cd},
+                            {-ca * cd, -sa * cd, 0.0},     {sa * sd, -ca * sd, 0.0}, {-ca * cd, -sa * cd, -sd}};
+    for (int v = 0; v < 6; v++) {
+      c.n3[v][0] = q[v][0];
+      c.n3[v][1] = ce * q[v][1] + se * q[v][2];
+      c.n3[v][2] = -se * q[v][1] + ce * q[v][2];
+    }
+  }
   ab_coefficients(p.delta, det.lat, det.gamma, c.ea, c.eb);
   const double s2g = sin(2 * det.gamma), c2g = cos(2 * det.gamma);
   const double sl = sin(det.lat), cl = cos(det.lat), s2l = sin(2 * det.lat), c2l = cos(2 * det.lat);
@@ -125,8 +139,12 @@ struct PtLayout {
 };
 
 // Grid: x = point, y = block of kPtThreads x kPtSamples samples.
-template <bool HESS, bool MET>
-__global__ void __launch_bounds__(kPtThreads) k_points(SegGeom g, const double4 *__restrict__ etab,
+// EPH: phi and its sky derivatives from the caller's position table eph (r_k at
+// t_k = k dt: n0 . r_k and the derivatives of n0 dotted with r_k) instead of the
+// analytic orbit and rotation terms; the sidereal angle still comes from etab.
+template <bool HESS, bool MET, bool EPH>
+__global__ void __launch_bounds__(kPtThreads) k_points(SegGeom g, const dbl4 *__restrict__ etab,
+                                                       const dbl4 *__restrict__ eph,
                                                        const double *__restrict__ x, const PointConst *pcs,
                                                        double *partial) {
   using Lt = PtLayout<HESS, MET>;
@@ -144,14 +162,24 @@ __global__ void __launch_bounds__(kPtThreads) k_points(SegGeom g, const double4 
   const double two_pi = 6.283185307179586476925286766559;
   const double four_pi2 = 39.478417604357434475337963999505;
   for (int64_t k = k0 + threadIdx.x; k < k1; k += kPtThreads) {
-    const double4 e4 = etab[k];
+    const dbl4 e4 = etab[k];
     const double xk = x[k];
     const double t = (double)k * g.dt;
     const double cx = c.ca * e4.z + c.sa * e4.w;   // cos(alpha - theta)
     const double sx = c.sa * e4.z - c.ca * e4.w;   // sin(alpha - theta)
-    const double phi = kAUls * (c.nx * e4.x + c.nyp * e4.y) + c.rcd * cx + c.zsd;
-    const double phi_a = kAUls * (c.nx_a * e4.x + c.nyp_a * e4.y) - c.rcd * sx;
-    const double phi_d = kAUls * (c.nx_d * e4.x + c.nyp_d * e4.y) + c.rcd_d * cx + c.zsd_d;
+    dbl4 rk = make_dbl4(0.0, 0.0, 0.0, 0.0);
+    if constexpr (EPH) rk = eph[2 * k];
+    auto ndot = [&](int v) { return c.n3[v][0] * rk.x + c.n3[v][1] * rk.y + c.n3[v][2] * rk.z; };
+    double phi, phi_a, phi_d;
+    if constexpr (EPH) {
+      phi = ndot(0);
+      phi_a = ndot(1);
+      phi_d = ndot(2);
+    } else {
+      phi = kAUls * (c.nx * e4.x + c.nyp * e4.y) + c.rcd * cx + c.zsd;
+      phi_a = kAUls * (c.nx_a * e4.x + c.nyp_a * e4.y) - c.rcd * sx;
+      phi_d = kAUls * (c.nx_d * e4.x + c.nyp_d * e4.y) + c.rcd_d * cx + c.zsd_d;
+    }
     const double c2 = cx * cx - sx * sx, s2 = 2.0 * sx * cx;
     const double a = c.ea[0] * c2 + c.ea[1] * s2 + c.ea[2] * cx + c.ea[3] * sx + c.ea[4];
     const double b = c.eb[0] * c2 + c.eb[1] * s2 + c.eb[2] * cx + c.eb[3] * sx;
@@ -196,9 +224,16 @@ __global__ void __launch_bounds__(kPtThreads) k_points(SegGeom g, const double4 
         for (int j = i; j < 4; j++) acc[Lt::kM + 4 + sym_idx(i, j)] += dP[i] * dP[j];
     }
     if constexpr (HESS) {
-      const double phi_aa = kAUls * (c.nx_aa * e4.x + c.nyp_aa * e4.y) - c.rcd * cx;
-      const double phi_ad = kAUls * (c.nx_ad * e4.x + c.nyp_ad * e4.y) - c.rcd_d * sx;
-      const double phi_dd = kAUls * (c.nx_dd * e4.x + c.nyp_dd * e4.y) + c.rcd_dd * cx + c.zsd_dd;
+      double phi_aa, phi_ad, phi_dd;
+      if constexpr (EPH) {
+        phi_aa = ndot(3);
+        phi_ad = ndot(4);
+        phi_dd = ndot(5);
+      } else {
+        phi_aa = kAUls * (c.nx_aa * e4.x + c.nyp_aa * e4.y) - c.rcd * cx;
+        phi_ad = kAUls * (c.nx_ad * e4.x + c.nyp_ad * e4.y) - c.rcd_d * sx;
+        phi_dd = kAUls * (c.nx_dd * e4.x + c.nyp_dd * e4.y) + c.rcd_dd * cx + c.zsd_dd;
+      }
       const double a_aa = -4.0 * c.ea[0] * c2 - 4.0 * c.ea[1] * s2 - c.ea[2] * cx - c.ea[3] * sx;
       const double b_aa = -4.0 * c.eb[0] * c2 - 4.0 * c.eb[1] * s2 - c.eb[2] * cx - c.eb[3] * sx;
       const double a_ad = -2.0 * c.ea_d[0] * s2 + 2.0 * c.ea_d[1] * c2 - c.ea_d[2] * sx + c.ea_d[3] * cx;
@@ -446,12 +481,12 @@ __global__ void k_climb_out(int npt, const ClimbState *st, double *F) {
 // ------------------------------------------------------------------ host
 static fs_status earth_table(fs_seg *seg, cudaStream_t st) {
   if (seg->etab64) return FS_OK;
-  if (cudaMalloc(&seg->etab64, sizeof(double4) * seg->g.n) != cudaSuccess) {
+  if (cudaMalloc(&seg->etab64, sizeof(dbl4) * seg->g.n) != cudaSuccess) {
     cudaGetLastError();
     seg->etab64 = nullptr;
     return FS_ERR_NOMEM;
   }
-  k_earth_table64<<<(unsigned)((seg->g.n + 255) / 256), 256, 0, st>>>(seg->g, (double4 *)seg->etab64);
+  k_earth_table64<<<(unsigned)((seg->g.n + 255) / 256), 256, 0, st>>>(seg->g, (dbl4 *)seg->etab64);
   seg->ctx->launches += 1;
   return cuda_status(cudaGetLastError());
 }
@@ -502,8 +537,12 @@ static fs_status refine_ws(fs_ctx *ctx, const fs_seg *seg, int npt, bool climb, 
 template <bool HESS, bool MET>
 static void launch_points(fs_seg *seg, const RefWs &w, int npt, double *F, double *grad, double *hess,
                           double *metric, double *amp, cudaStream_t st) {
-  k_points<HESS, MET><<<dim3(npt, w.nblk), kPtThreads, 0, st>>>(seg->g, (const double4 *)seg->etab64, seg->x64,
-                                                                 w.pc, w.partial);
+  const dim3 grid(npt, w.nblk);
+  const dbl4 *et = (const dbl4 *)seg->etab64;
+  if (seg->eph)
+    k_points<HESS, MET, true><<<grid, kPtThreads, 0, st>>>(seg->g, et, seg->eph, seg->x64, w.pc, w.partial);
+  else
+    k_points<HESS, MET, false><<<grid, kPtThreads, 0, st>>>(seg->g, et, nullptr, seg->x64, w.pc, w.partial);
   k_points_final<HESS, MET><<<(unsigned)((npt + 127) / 128), 128, 0, st>>>(w.partial, w.nblk, npt, seg->g, F, grad,
                                                                             hess, metric, amp);
 }

@@ -25,6 +25,7 @@ __global__ void k_skyconst(const double *alpha, const double *delta, int nsky, S
     SkyConst32 c;
     c.nx = df_from_double(k.nx);  // the tables carry the factor AU/c
     c.nyp = df_from_double(k.nyp);
+    c.nz = df_from_double(k.nz);
     c.ca = (float)k.ca;
     c.sa = (float)k.sa;
     c.rcd = (float)k.rcd;
@@ -56,6 +57,8 @@ struct DemodArgs {
   df32 fl;
   const SkyConst32 *sky;
   const float4 *tab0, *tab1;  // indexed by m + margin
+  const float4 *eph0, *eph1;  // caller's position table (EPH), indexed by m + margin
+  const float *eph2;
   const float4 *coef;         // spline intervals [2n]
   const float *x32;           // data, nearest-neighbour path
   float2 *ya, *yb, *qq;       // [nsky][stride]
@@ -64,7 +67,9 @@ struct DemodArgs {
   double *tsrc;               // optional [n] (first sky only)
 };
 
-template <int INTERP>
+// EPH: the delay from the caller's position table (eph0..2: r_m as double-floats
+// and v_m on the grid) in place of the analytic orbit and rotation terms.
+template <int INTERP, bool EPH>
 __global__ void __launch_bounds__(256) k_demod32(DemodArgs A) {
   const int s = blockIdx.y;
   const SkyConst32 K = A.sky[s];
@@ -75,28 +80,50 @@ __global__ void __launch_bounds__(256) k_demod32(DemodArgs A) {
     if (j < A.g.n) {
       const int64_t M = A.g.margin;
       // 1) delay at the output time t_b = j dt, plain FP32 (only seeds the solve)
-      const float4 T0 = A.tab0[j + M], T1 = A.tab1[j + M];
-      const float phi0 = fmaf(K.nx.hi, T0.x, K.nyp.hi * T0.z) + fmaf(K.rcd, K.ca * T1.x + K.sa * T1.y, K.zsd);
+      float phi0;
+      if constexpr (EPH) {
+        const float4 E0 = A.eph0[j + M], E1 = A.eph1[j + M];
+        phi0 = fmaf(K.nx.hi, E0.x, fmaf(K.nyp.hi, E0.z, K.nz.hi * E1.x));
+      } else {
+        const float4 T0 = A.tab0[j + M], T1 = A.tab1[j + M];
+        phi0 = fmaf(K.nx.hi, T0.x, K.nyp.hi * T0.z) + fmaf(K.rcd, K.ca * T1.x + K.sa * T1.y, K.zsd);
+      }
       // 2) first source time t1 = m1 dt + tau1 with t1 - t_b = -phi0 (up to rounding)
       const float kf = rintf(-phi0 * A.inv_dt);
       const int k1 = (int)kf;
       const df32 kd = two_prod(kf, A.dt2.hi);  // k1 dt as an exact pair (plus kf * dt.lo)
       const float kdlo = fmaf(kf, A.dt2.lo, kd.lo);
       const float tau1 = (-phi0 - kd.hi) - kdlo;
+      // |phi0| <= 600 s keeps m1 inside the margins; the clamp guards the table reads
       const int64_t m1 = j + k1;
-      const float4 U0 = A.tab0[m1 + M], U1 = A.tab1[m1 + M];
-      // 3) delay at t1: orbit term as double-float at the grid point, rotated by Omega_o tau1
-      df32 P = df_add(df_mul(K.nx, df32{U0.x, U0.y}), df_mul(K.nyp, df32{U0.z, U0.w}));
-      const float eo = (float)kOmegaO * tau1;
-      const float Qo = fmaf(-K.nx.hi, U0.z, K.nyp.hi * U0.x);  // d(orbit)/d(lambda)
-      const float orb = fmaf(eo, Qo, -0.5f * eo * eo * P.hi);
+      const int64_t mi = min(max(m1 + M, (int64_t)0), A.g.ngrid - 1);
+      const float4 U1 = A.tab1[mi];
+      df32 P;
+      float orb, rot, phidot;
       const float er = (float)kOmegaR * tau1;
       const float ce = 1.f - 0.5f * er * er, se = er - er * er * er * (1.f / 6.f);
       const float cth = fmaf(U1.x, ce, -U1.y * se), sth = fmaf(U1.y, ce, U1.x * se);
       float cx = fmaf(K.ca, cth, K.sa * sth);   // cos(alpha - theta(t1))
       float sx = fmaf(K.sa, cth, -K.ca * sth);  // sin(alpha - theta(t1))
-      const float rot = fmaf(K.rcd, cx, K.zsd);
-      const float phidot = fmaf((float)kOmegaO, Qo, K.rcd * (float)kOmegaR * sx);
+      if constexpr (EPH) {
+        // 3) delay at t1: n0 . r_m1 as double-float plus tau1 n0 . v_m1
+        const float4 V0 = A.eph0[mi], V1 = A.eph1[mi];
+        const float vz = A.eph2[mi];
+        P = df_add(df_add(df_mul(K.nx, df32{V0.x, V0.y}), df_mul(K.nyp, df32{V0.z, V0.w})),
+                   df_mul(K.nz, df32{V1.x, V1.y}));
+        phidot = fmaf(K.nx.hi, V1.z, fmaf(K.nyp.hi, V1.w, K.nz.hi * vz));
+        orb = tau1 * phidot;
+        rot = 0.f;
+      } else {
+        // 3) delay at t1: orbit term as double-float at the grid point, rotated by Omega_o tau1
+        const float4 U0 = A.tab0[mi];
+        P = df_add(df_mul(K.nx, df32{U0.x, U0.y}), df_mul(K.nyp, df32{U0.z, U0.w}));
+        const float eo = (float)kOmegaO * tau1;
+        const float Qo = fmaf(-K.nx.hi, U0.z, K.nyp.hi * U0.x);  // d(orbit)/d(lambda)
+        orb = fmaf(eo, Qo, -0.5f * eo * eo * P.hi);
+        rot = fmaf(K.rcd, cx, K.zsd);
+        phidot = fmaf((float)kOmegaO, Qo, K.rcd * (float)kOmegaR * sx);
+      }
       // 4) Newton step on g(t) = t + phi_m(t) - t_b at t1
       const df32 Ah = two_sum(kd.hi, P.hi);
       const float gres = ((Ah.hi + tau1) + (Ah.lo + kdlo)) + ((P.lo + orb) + rot);
@@ -338,6 +365,9 @@ static DemodArgs demod_args(const fs_seg *seg, const Ws32 &w, int64_t npad) {
   A.sky = w.skyc;
   A.tab0 = seg->tab0;
   A.tab1 = seg->tab1;
+  A.eph0 = seg->eph0;
+  A.eph1 = seg->eph1;
+  A.eph2 = seg->eph2;
   A.coef = (const float4 *)seg->coef;
   A.x32 = seg->x32;
   A.ya = w.ya;
@@ -352,8 +382,14 @@ static DemodArgs demod_args(const fs_seg *seg, const Ws32 &w, int64_t npad) {
 
 static cudaError_t launch_demod(const DemodArgs &A, int nsky, int nblk, int interp, cudaStream_t st) {
   dim3 grid(nblk, nsky);
-  if (interp == FS_INTERP_NEAREST) k_demod32<FS_INTERP_NEAREST><<<grid, 256, 0, st>>>(A);
-  else k_demod32<FS_INTERP_SPLINE2X><<<grid, 256, 0, st>>>(A);
+  const bool eph = A.eph0 != nullptr;
+  if (interp == FS_INTERP_NEAREST) {
+    if (eph) k_demod32<FS_INTERP_NEAREST, true><<<grid, 256, 0, st>>>(A);
+    else k_demod32<FS_INTERP_NEAREST, false><<<grid, 256, 0, st>>>(A);
+  } else {
+    if (eph) k_demod32<FS_INTERP_SPLINE2X, true><<<grid, 256, 0, st>>>(A);
+    else k_demod32<FS_INTERP_SPLINE2X, false><<<grid, 256, 0, st>>>(A);
+  }
   return cudaGetLastError();
 }
 

@@ -1,5 +1,5 @@
-// Plain FP64 form of the search: every step in double, the analytic model
-// evaluated directly at each source time, the spline in double, and the
+// Plain FP64 form of the search: every step in double, the analytic model (or
+// the caller's position table) evaluated directly at each source time, the spline in double, and the
 // zero-padded transform by the FP64 radix-2 Stockham FFT.  It is the
 // all-FP64 comparison for the FP32 path on the same GPU.
 #include "fs_internal.h"
@@ -9,16 +9,18 @@ namespace fs {
 
 constexpr unsigned kFull64 = 0xffffffffu;
 
+// eph: NULL (analytic Earth) or the caller's position table of the segment.
 __global__ void __launch_bounds__(256) k_demod64(SegGeom g, const SkyConst64 *sky, const dcoef4 *coef,
                                                  const double *x64, int interp, double2 *ya, double2 *yb,
-                                                 double *qq, int64_t stride, double *partial, double *tsrc) {
+                                                 double *qq, int64_t stride, double *partial, double *tsrc,
+                                                 const dbl4 *eph) {
   const int s = blockIdx.y;
   const SkyConst64 K = sky[s];
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double a2 = 0.0, b2 = 0.0;
   if (j < g.n) {
     Geo64 geo;
-    const double t = source_time64((double)j * g.dt, K, g, &geo);
+    const double t = source_time64((double)j * g.dt, K, g, &geo, eph);
     double xr = 0.0;
     if (interp == FS_INTERP_SPLINE2X) {
       if (t >= 0.0 && t <= (double)(g.n - 1) * g.dt) {
@@ -205,7 +207,8 @@ fs_status search64(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
   for (int sk = 0; sk < nsky; sk++) {
     if (sky_constants64(alpha + sk, delta + sk, 1, seg->g, ctx->det, w.skyc, st) != cudaSuccess) return FS_ERR_CUDA;
     k_demod64<<<dim3(w.nblk, 1), 256, 0, st>>>(seg->g, w.skyc, (const dcoef4 *)seg->coef, seg->x64,
-                                                seg->d.interp, w.ya, w.yb, w.qq, 0, w.partial, nullptr);
+                                                seg->d.interp, w.ya, w.yb, w.qq, 0, w.partial, nullptr,
+                                                seg->eph);
     k_finalize64<<<1, 256, 0, st>>>(w.partial, w.nblk, n, seg->g.dt, seg->g.S0, w.norm, w.ab2);
     ctx->launches += 5;  // sky constants, demodulation, finalize, modulation, F epilogue
     k_modulate64<<<dim3((unsigned)((nfft + 255) / 256), nspin), 256, 0, st>>>(w.ya, w.yb, w.qq, f1, nspin, n,
@@ -235,7 +238,8 @@ fs_status demod64_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, do
   if (sky_constants64(dd, dd + 1, 1, seg->g, ctx->det, w.skyc, st) != cudaSuccess) return FS_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return FS_ERR_CUDA;
   k_demod64<<<dim3(w.nblk, 1), 256, 0, st>>>(seg->g, w.skyc, (const dcoef4 *)seg->coef, seg->x64,
-                                              seg->d.interp, w.ya, w.yb, w.qq, 0, w.partial, tsrc);
+                                              seg->d.interp, w.ya, w.yb, w.qq, 0, w.partial, tsrc,
+                                              seg->eph);
   k_finalize64<<<1, 256, 0, st>>>(w.partial, w.nblk, n, seg->g.dt, seg->g.S0, nullptr, (double2 *)ab2);
   k_copy_pairs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.ya, ya, n);
   k_copy_pairs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w.yb, yb, n);

@@ -23,7 +23,7 @@ STATUS = {0: "FS_OK", 1: "FS_ERR_ARG", 2: "FS_ERR_SHAPE", 3: "FS_ERR_CAPACITY", 
           5: "FS_ERR_CUDA", 6: "FS_ERR_TIMEOUT", 7: "FS_ERR_UNSUPPORTED", 8: "FS_ERR_NOMEM", 9: "FS_ERR_SCRATCH"}
 PREC = {"f32": 0, "f64": 1}
 INTERP = {"spline": 0, "nearest": 1}
-EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_seg_destroy", "fs_seg_load", "fs_search",
+EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_prepare_segment_eph", "fs_seg_destroy", "fs_seg_load", "fs_search",
            "fs_sync_status", "fs_strerror", "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling",
            "fs_get_stats", "fs_search_noalloc", "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune",
            "fs_fstat_points", "fs_refine", "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm_cell",
@@ -80,6 +80,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.fs_destroy.argtypes = [vp]
     lib.fs_destroy.restype = None
     lib.fs_prepare_segment.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(_SegDesc), vp, vp]
+    lib.fs_prepare_segment_eph.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(_SegDesc), vp, vp, vp, vp]
     lib.fs_seg_destroy.argtypes = [vp]
     lib.fs_seg_destroy.restype = None
     lib.fs_seg_load.argtypes = [vp, vp, vp]
@@ -110,7 +111,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.fs_lattice.argtypes = [i32, ctypes.POINTER(f64), f64, f64, i32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
     lib.fs_lattice_nodes.argtypes = [ctypes.POINTER(f64), ctypes.POINTER(_Detector), f64, f64, f64, f64, f64, vp,
                                      i64, ctypes.POINTER(i64)]
-    for name in ("fs_create", "fs_prepare_segment", "fs_seg_load", "fs_search", "fs_search_noalloc", "fs_sync_status",
+    for name in ("fs_create", "fs_prepare_segment", "fs_prepare_segment_eph", "fs_seg_load", "fs_search", "fs_search_noalloc", "fs_sync_status",
                  "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling", "fs_get_stats",
                  "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune", "fs_fstat_points", "fs_refine",
                  "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm", "fs_threshold", "fs_cell_count",
@@ -220,11 +221,15 @@ def _tuning_dict(t) -> dict:
 
 
 class Segment:
-    """One prepared data segment (fs_prepare_segment): tables, x2 upsampling, spline."""
+    """One prepared data segment (fs_prepare_segment): tables, x2 upsampling, spline.
+
+    eph: None for the analytic Earth, else (r, v), device float64 tensors of shape
+    (3, n): the detector's SSB position r_d(t_m)/c [light-seconds] and velocity
+    v_d(t_m)/c at t_m = m dt, ecliptic axes (fs_prepare_segment_eph)."""
 
     def __init__(self, ctx: Context, x: torch.Tensor, dt: float, nfft: int, fl: float, S0: float,
                  precision: str = "f32", interp: str = "spline", t0: float = 0.0, interbin: bool = False,
-                 stream=None):
+                 eph=None, stream=None):
         _need_cuda(x, "x")
         if x.dtype not in (torch.float32, torch.float64):
             raise ValueError("x must be float32 or float64")
@@ -238,8 +243,18 @@ class Segment:
         d = _SegDesc(self.n, self.nfft, self.dt, self.fl, self.S0, PREC[precision], INTERP[interp],
                      0 if x.dtype == torch.float32 else 1, 1 if interbin else 0, self.t0)
         h = ctypes.c_void_p()
-        _check(ctx.lib.fs_prepare_segment(ctx.handle, ctypes.byref(h), ctypes.byref(d), _ptr(x), _stream(stream)),
-               "fs_prepare_segment")
+        if eph is None:
+            _check(ctx.lib.fs_prepare_segment(ctx.handle, ctypes.byref(h), ctypes.byref(d), _ptr(x),
+                                              _stream(stream)), "fs_prepare_segment")
+        else:
+            r, v = eph
+            for t, nm in ((r, "r"), (v, "v")):
+                _need_cuda(t, nm, torch.float64)
+                if tuple(t.shape) != (3, self.n) or not t.is_contiguous():
+                    raise ValueError("%s must be a contiguous (3, %d) tensor" % (nm, self.n))
+            _check(ctx.lib.fs_prepare_segment_eph(ctx.handle, ctypes.byref(h), ctypes.byref(d), _ptr(x), _ptr(r),
+                                                  _ptr(v), _stream(stream)), "fs_prepare_segment_eph")
+        self.eph = eph is not None
         self.handle = h
         ctx._segments.add(self)
 

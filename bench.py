@@ -57,6 +57,7 @@ def _args():
     p.add_argument("--quick", action="store_true", help="skip the CPU baseline and FP64 comparison")
     p.add_argument("--nsky", type=int, default=None, help="override the sky count (profiling runs, batch sky subset)")
     p.add_argument("--tune", action="store_true", help="run the launch tuner for each transform length first")
+    p.add_argument("--n1", type=int, default=0, help="first-pass length N1 of the transform split (0: default)")
     p.add_argument("--cands", type=int, default=1024, help="fine-search workload: candidates refined per step")
     return p.parse_args()
 
@@ -556,6 +557,9 @@ def main():
         fs.search(ctx, seg, alpha, delta, f1, wl.F_thr, F_out=F_out, cand=cand, n_cand=ncand, cand_cap=cap)
 
     tuning = None
+    if args.n1:
+        ctx.set_tuning(wl.nfft, n1=args.n1)
+        tuning = ctx.get_tuning(wl.nfft)
     if args.tune:
         tuning = ctx.autotune(seg, alpha[:min(nsky, 64)].contiguous(), delta[:min(nsky, 64)].contiguous(), f1)
 

@@ -181,7 +181,9 @@ struct Pass2Args {
   int sky_base;        // global index of the group's first sky
   float *F;            // NULL or F_out + (global template of the group's first template) * nbins
   int64_t nbins;       // F row length of one template (all its sub-transforms)
-  float2 *X;           // XOUT items: complex bins [batch][2][nfft] in natural order
+  float2 *X;           // XOUT items: complex bins [batch][2][nfft] in natural order;
+                       // interbinning items: edge rows, eb_stride per template (pass2_item_ib)
+  int64_t eb_stride;
   float thr;
   fs_candidate *cand;
   int64_t cap;
@@ -378,6 +380,113 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
   }
 }
 
+// Interbinning pass-2 work item (Eq. intbin, Sec. VI.B) for P <= 16: F on the
+// half-bin grid j = 2k, 2k + 1 of the band k < Nfft/2 for the R rows k1 of tile
+// rt.  Even j from X(k); odd j from (X(k+1) - X(k)) / sqrt 2, where X(k+1) sits in
+// row k1 + 1 of the same k2 (k = k1 + N1 k2).  The tile's last row pairs with the
+// next tile's first row (the last tile's with row 0 at k2 + 1), so every item
+// stores its first and last rows in A.X (per template, eb_stride float2:
+// [tiles2][first a, first b, last a, last b][N2/2], then X(Nfft/2) of a and b)
+// and k_interbin_edges forms those odd bins after the launch.  X(Nfft/2) =
+// sum_n2 Z[0][n2] (-1)^n2 comes from row 0 before its transform.
+template <int P, int Q, int WARPS>
+__device__ __forceinline__ void pass2_item_ib(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
+                                              const float2 *twM) {
+  static_assert(P <= 16, "interbinning items need at least two rows per warp group");
+  constexpr int T = P, G = 16 / P, R = WARPS * G, S = Q / P, D = Q / 2, DP = D * P, FP = 2 * R + 1;
+  using X = Xch2<P, Q>;
+  constexpr int XW = X::SIZE;
+  static_assert(DP >= 32 && (DP & (DP - 1)) == 0, "a warp's F items share one row");
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = lane % T, sig = (lane / T) & 1, gr = lane / (2 * T);
+  const int row = w * G + gr;
+  const int k1 = rt * R + row;
+  const int sky = fdiv(tm, A.nspin_fd), spin = tm - sky * A.nspin;
+  constexpr int L2 = P * Q;
+  const int64_t N1 = A.N1, nfft = A.nfft;
+  const int tiles2 = (int)(N1 / R);
+  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * nfft + (int64_t)k1 * L2;
+  float2 v[Q];
+  sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = __ldcg(z + Q * a + t + P * s); }); });
+  float2 *eb = A.X + (int64_t)tm * A.eb_stride;
+  if (rt == 0 && w == 0) {  // row k1 = 0 (lanes with gr = 0): X(Nfft/2); n2 = Q a + t + P s has the parity of t
+    float2 sum = make_float2(0.f, 0.f);
+    sfor<0, Q>([&](auto i) { sum = cadd(sum, v[i]); });
+    if (t & 1) sum = make_float2(-sum.x, -sum.y);
+    for (int o = T / 2; o > 0; o >>= 1) {
+      sum.x += __shfl_xor_sync(kFull, sum.x, o);
+      sum.y += __shfl_xor_sync(kFull, sum.y, o);
+    }
+    if (gr == 0 && t == 0) eb[(int64_t)tiles2 * 4 * DP + sig] = sum;
+  }
+  float2 *xw = work + (w * 2 * G + (sig + 2 * gr)) * XW;
+  sfor<0, S>([&](auto s) {
+    const int b = t + P * s;
+    dft_inplace<P>(v + s * P);
+    sfor<1, P>([&](auto c) { v[s * P + c] = cmul(v[s * P + c], twM[c * Q + b]); });
+    sfor<0, P>([&](auto c) { xw[X::at(c, b)] = v[s * P + c]; });
+  });
+  __syncwarp();
+  sfor<0, Q>([&](auto bb) { v[bb] = xw[X::at(t, bb)]; });
+  __syncthreads();  // every warp is done with the exchange area (reused for the rows and the F tile)
+  dft_inplace<Q, Q, D>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)
+  float2 *Xs = work;                         // [R][2][DP]
+  float *Fs = (float *)(work + 2 * R * DP);  // [DP][FP]: even and odd F of the tile's rows
+  sfor<0, D>([&](auto d) { Xs[(row * 2 + sig) * DP + t + P * d] = v[d]; });
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * DP; i += blockDim.x) {
+    eb[(int64_t)rt * 4 * DP + i] = Xs[i];
+    eb[(int64_t)rt * 4 * DP + 2 * DP + i] = Xs[(R - 1) * 2 * DP + i];
+  }
+  const float2 nrm = A.norm[sky];
+  const unsigned lt_mask = (1u << lane) - 1u;
+  auto emit = [&](bool hit, float Fv, uint32_t bin) {  // warp-uniform call: ballot compaction
+    const unsigned m = __ballot_sync(kFull, hit);
+    if (!m) return;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(A.ncand, (unsigned long long)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (hit) {
+      const unsigned long long idx = base + __popc(m & lt_mask);
+      if ((long long)idx < A.cap) {
+        fs_candidate c;
+        c.sky = (uint32_t)(A.sky_base + sky);
+        c.spin = (uint32_t)spin;
+        c.bin = bin;
+        c.F = Fv;
+        A.cand[idx] = c;
+      } else {
+        atomicOr(A.flags, ERRF_CAPACITY);
+      }
+    }
+  };
+  static_assert((R * DP) % 32 == 0, "whole warps per F loop");
+  for (int idx = threadIdx.x; idx < R * DP; idx += blockDim.x) {
+    const int r = idx / DP, k2 = idx - r * DP;  // r is the same across a warp
+    const float2 a0 = Xs[(r * 2) * DP + k2], b0 = Xs[(r * 2 + 1) * DP + k2];
+    const float Fe = fmaf(a0.x, a0.x, a0.y * a0.y) * nrm.x + fmaf(b0.x, b0.x, b0.y * b0.y) * nrm.y;
+    Fs[k2 * FP + 2 * r] = Fe;
+    const uint32_t j = 2u * (uint32_t)(rt * R + r + N1 * k2);
+    emit(Fe > A.thr, Fe, j);
+    if (r < R - 1) {
+      const float2 a1 = Xs[(r * 2 + 2) * DP + k2], b1 = Xs[(r * 2 + 3) * DP + k2];
+      const float dax = a1.x - a0.x, day = a1.y - a0.y, dbx = b1.x - b0.x, dby = b1.y - b0.y;
+      const float Fo = 0.5f * (fmaf(dax, dax, day * day) * nrm.x + fmaf(dbx, dbx, dby * dby) * nrm.y);
+      Fs[k2 * FP + 2 * r + 1] = Fo;
+      emit(Fo > A.thr, Fo, j + 1u);
+    }
+  }
+  if (A.F == nullptr) return;
+  __syncthreads();
+  // bins j = 2 rt R + q + 2 N1 k2, q < 2R: runs of 2R floats; the last odd one is the edge kernel's
+  float *Fout = A.F + (int64_t)tm * A.nbins + 2 * rt * R;
+  for (int idx = threadIdx.x; idx < 2 * R * DP; idx += blockDim.x) {
+    const int k2 = idx / (2 * R), q = idx - k2 * (2 * R);
+    if (q != 2 * R - 1) __stcs(Fout + q + 2 * N1 * k2, Fs[k2 * FP + q]);
+  }
+}
+
 template <int P, int Q, int WARPS, bool FULLBINS, bool ALIAS_F = false>
 constexpr size_t pass2_work_floats2() {
   constexpr int G = P <= 16 ? 16 / P : 1;
@@ -446,7 +555,8 @@ __device__ inline void wait_at_least(const unsigned *p, unsigned target, uint32_
   }
 }
 
-template <int P1, int Q1, int AM, int P2, int Q2, int NT, int MINB, int VS>
+// IB: pass-2 items are interbinning items (pass2_item_ib).
+template <int P1, int Q1, int AM, int P2, int Q2, int NT, int MINB, int VS, bool IB = false>
 __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2, QueueArgs Qa) {
   constexpr int CW = NT / (2 * P1);
   constexpr int L1 = P1 * Q1, L2 = P2 * Q2;
@@ -523,6 +633,7 @@ __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2,
       // the items take N1, N2 at run time: compiled in, they measured 5.5% slower here
       const int zs = d.tm - fdiv(d.tm, Qa.slots_fd) * Qa.slots;
       if (d.is1) pass1_item<P1, Q1, CW, AM, VS, 0>(A1, d.tm, zs, d.j, work, twL);
+      else if constexpr (IB) pass2_item_ib<P2, Q2, NT / 32>(A2, d.tm, zs, d.j - T1, work, twM);
       else pass2_item<P2, Q2, NT / 32, false, true, VS, false, 0>(A2, d.tm, zs, d.j - T1, work, twM);
     }
     if (threadIdx.x == 0) {
@@ -585,11 +696,11 @@ constexpr size_t persist_smem() {
 template <int P1, int Q1, int P2, int Q2, int NT>
 constexpr int persist_minb() { return persist_smem<P1, Q1, P2, Q2, NT>() <= 74 * 1024 ? kPersistMinBlocks : 2; }
 
-template <int P1, int Q1, int AM, int P2, int Q2, int NT, int VS>
+template <int P1, int Q1, int AM, int P2, int Q2, int NT, int VS, bool IB = false>
 static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
   constexpr int MINB = persist_minb<P1, Q1, P2, Q2, NT>();
   const size_t sm = persist_smem<P1, Q1, P2, Q2, NT>();
-  auto kern = k_passes<P1, Q1, AM, P2, Q2, NT, MINB, VS>;
+  auto kern = k_passes<P1, Q1, AM, P2, Q2, NT, MINB, VS, IB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, occ = 0;
@@ -607,11 +718,11 @@ static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, con
 
 // VS: sub-transforms per template (2^VS) compiled in; only the 2^20 split is
 // built with VS = 1 (the 2^21 transform).
-template <int P1, int Q1, int P2, int Q2, int NT, int VS = 0>
+template <int P1, int Q1, int P2, int Q2, int NT, int VS = 0, bool IB = false>
 static cudaError_t launch_passes_am(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
   if (a1.vshift != VS) return cudaErrorInvalidValue;
-  if (a1.n1max <= P1 * Q1 / 2) return launch_passes_t<P1, Q1, P1 / 2, P2, Q2, NT, VS>(a1, a2, qa, st);
-  return launch_passes_t<P1, Q1, P1, P2, Q2, NT, VS>(a1, a2, qa, st);
+  if (a1.n1max <= P1 * Q1 / 2) return launch_passes_t<P1, Q1, P1 / 2, P2, Q2, NT, VS, IB>(a1, a2, qa, st);
+  return launch_passes_t<P1, Q1, P1, P2, Q2, NT, VS, IB>(a1, a2, qa, st);
 }
 
 // Work-item geometry of the persistent kernel for NT threads per CTA.
@@ -632,6 +743,19 @@ cudaError_t dispatch_pass2(int N2, bool full, const Pass2Args &a, int nb, cudaSt
 cudaError_t dispatch_pass2x(int N2, const Pass2Args &a, int nb, cudaStream_t st);
 // Interbinning epilogue (Eq. intbin) over nb templates of a batch from a.X.
 cudaError_t launch_interbin(const Pass2Args &a, int nb, cudaStream_t st);
+// Persistent launch with interbinning items for the default split N1 x N2 of
+// 2^12 .. 2^19 (N2 <= 512; also 256 x 512), and the edge bins after
+// it (k_interbin_edges);
+// cudaErrorInvalidValue for another split (passes_ib_instantiated is false).
+cudaError_t dispatch_passes_ib(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
+                               cudaStream_t st);
+bool passes_ib_instantiated(int N1, int N2);
+// Per-template stride (float2) of the interbinning items' edge rows.
+inline int64_t ib_edge_stride(int N1, int N2, int NT) {
+  const int P2 = N2 <= 128 ? 8 : 16;
+  const int R = (NT / 32) * (16 / P2);
+  return (int64_t)(N1 / R) * 4 * (N2 / 2) + 2;
+}
 // Persistent launch for an N1 x N2 split; cudaErrorInvalidValue for a split
 // this build does not instantiate (split_instantiated is false).
 cudaError_t dispatch_passes(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,

@@ -239,3 +239,37 @@ def test_interbinning_matches_oracle(fs, name, n, nfft, precision):
         with pytest.raises(fs.FstatError) as e:
             fs.search_batch(ctx, [seg], _dev(alpha), _dev(delta), _dev(f1), wl.F_thr)
         assert e.value.status == 7
+
+
+@pytest.mark.parametrize("name,nfft,n1,qround,nsky,nspin", [
+    ("tiny", 1 << 12, 0, 0, 3, 2),        # 64 x 64: two rows per warp, 16-row tiles
+    ("small", 1 << 15, 0, 1, 2, 3),       # 256 x 128, one template per queue round
+    ("small", 1 << 16, 512, 0, 1, 2),     # 512 x 128: no interbinning items, per-batch launches
+    ("grid_2d", 1 << 17, 512, 0, 1, 2),   # 512 x 256 (the default 2^17 interbinning split is 256 x 512)
+])
+def test_interbinning_persistent_splits(fs, name, nfft, n1, qround, nsky, nspin):
+    """The interbinning items of the persistent queue (tile-interior odd bins) and the
+    edge kernel (odd bins between tiles, the wrap to row 0 and X(Nfft/2)) on every
+    bin against the oracle, for splits and queue shapes the default test does not reach."""
+    from oracle import fstat as ofs
+    wl, det, x, alpha, delta, f1 = make_case(name, nfft=nfft, nsky=nsky, nspin=nspin)
+    seg_o = ors.Segment(x, wl.dt)
+    ref = np.stack([ofs.fstat_interbinned(seg_o, a, d, s1, wl.fl, det, wl.S0, nfft)
+                    for a, d in zip(alpha, delta) for s1 in f1])
+    ctx = fs.Context(det)
+    if n1 or qround:
+        ctx.set_tuning(nfft, n1=n1, queue_round=qround)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, nfft, wl.fl, wl.S0, interbin=True)
+    thr = float(np.quantile(ref, 0.999))   # enough crossings to exercise the compaction on both grids
+    res = fs.search(ctx, seg, _dev(alpha), _dev(delta), _dev(f1), thr)
+    assert ctx.sync_status() == 0
+    F = res.F.double().cpu().numpy()
+    assert max_rel_dF(F, ref) <= F32_TOL
+    assert max_rel_dF(F[:, 1::2], ref[:, 1::2]) <= F32_TOL
+    missing, bad = check_candidates(*res.candidates(), ref, thr, len(f1))
+    assert not missing and not bad
+    # candidates only (no F written) give the same crossings
+    res2 = fs.search(ctx, seg, _dev(alpha), _dev(delta), _dev(f1), thr, write_F=False)
+    c1 = sorted(zip(*[a.tolist() for a in res.candidates()[:3]]))
+    c2 = sorted(zip(*[a.tolist() for a in res2.candidates()[:3]]))
+    assert c1 == c2

@@ -81,9 +81,20 @@ def fstat_from_transforms(Xa, Xb, dm: Demodulated, n: int, dt: float, S0: float)
 
 
 def fstat(seg: resample.Segment, alpha, delta, f1, fl, det, S0, nfft, bins=None, nbins=None,
-          interp="spline"):
-    """F on the requested bins (direct sums) or on bins [0, nbins) (FFT)."""
+          interp="spline", bin_offset=0.0):
+    """F on the requested bins (direct sums) or on bins [0, nbins) (FFT).
+
+    bin_offset: F at the frequencies (k + bin_offset) / (Nfft dt) instead of the
+    Fourier frequencies: X(k + d) = sum_j y_j exp(-2 pi i j (k + d) / Nfft) is the
+    DFT at bin k of y_j exp(-2 pi i d j / Nfft) (Eq. eq:DFT off the Fourier grid;
+    used to search lattice nodes that fall between Fourier frequencies, Sec. IV)."""
     dm = demodulate(seg, alpha, delta, f1, fl, det, interp=interp)
+    if bin_offset:
+        j = np.arange(seg.n, dtype=np.float64)
+        c = bin_offset * j / nfft
+        rot = np.exp(-2j * math.pi * (c - np.floor(c)))
+        dm.ya = dm.ya * rot
+        dm.yb = dm.yb * rot
     if bins is not None:
         Xa = dft_direct(dm.ya, nfft, bins)
         Xb = dft_direct(dm.yb, nfft, bins)

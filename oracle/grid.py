@@ -24,6 +24,16 @@ the l with the largest det S = mu nu^(n-1); rotate l onto e0 (O2) and, for the
 second constraint, rotate about e0 (O3) so that a second lattice vector f has
 no sky components; map back with M^T.  All in row-vector form: a lattice vector
 r of A_n* becomes r O1 S O2^T O3^T M^T.
+
+Search of the lattice with the FFT (Sec. IV, Sec. VII): with a0 the Fourier
+spacing dp0 = 2 pi / (Nfft dt) and a1 free of sky components, the nodes
+k0 a0 + k1 a1 + k2 b2 + k3 b3 group into lines along a0 that one zero-padded
+transform evaluates at once: per sky node (k2, k3) and spindown node k1, the line
+omega0 = c0 + k0 dp0 with c0 = k1 a1_0 + k2 b2_0 + k3 b3_0 falls on the bins k of
+the transform shifted by the fraction d = frac(c0/dp0 - fl Nfft dt) of a bin.  The
+sky position of (alpha1, alpha2) = omega0 (n0_y, n0_x) (Eq. albe) is taken at one
+reference frequency for the whole line (reading: the band's upper edge,
+fl + 1/(2 dt)), both ecliptic hemispheres.
 """
 from __future__ import annotations
 
@@ -323,3 +333,59 @@ def constrained_lattice(G: np.ndarray, C0: float, dp0: float, n_candidates: int 
     details = dict(l=l, mu=mu, nu=nu, e0=e0, Mx=Mx, theta_min=theta_min, f=f, R=R, O1=O1, O2=O2, O3=O3, S=S,
                    U=U, gen_images=gen_all)
     return gen, theta_min / detS, details
+
+
+def lattice_templates(basis, det, fl: float, nfft: int, dt: float, f1_min: float, f1_max: float,
+                      box=(-1.0, 1.0, -1.0, 1.0)):
+    """Templates of the FFT search of a 4-dimensional lattice with both constraints
+    (basis rows a0 = (dp0, 0, 0, 0), a1 = (a1_0, a1_1, 0, 0), b2, b3 in
+    (omega0, omega1, alpha1, alpha2) units, dp0 = 2 pi / (Nfft dt)): a list, one
+    entry per sky node and hemisphere, of (alpha, delta, [(f1, d, k1), ...]) with the
+    spindown nodes in [f1_min, f1_max] Hz/s (k1 increasing) and the bin offsets d in
+    [0, 1).  box = (nx_lo, nx_hi, ny_lo, ny_hi) limits the ecliptic components of the
+    sky nodes (the whole sky by default).  Sky nodes run over k2, then k3 (both
+    increasing), north before south."""
+    B = np.array(basis, dtype=np.float64).reshape(4, 4)
+    tp = 2.0 * math.pi
+    dp0 = B[0, 0]
+    scale = np.abs(B).max(axis=0)
+    if abs(dp0 - tp / (nfft * dt)) > 1e-9 * dp0 or np.any(np.abs(B[0, 1:]) > 1e-9 * scale[1:]) or \
+            np.any(np.abs(B[1, 2:]) > 1e-9 * scale[2:]):
+        raise ValueError("basis is not a constrained lattice on this transform's Fourier spacing")
+    B[0, 1:] = 0.0          # exact zeros of the constraints (rounding of the construction)
+    B[1, 2:] = 0.0
+    w_ref = tp * (fl + 0.5 / dt)
+    w1lo, w1hi = tp * f1_min, tp * f1_max
+    S = B[2:4, 2:4]
+    Sinv = np.linalg.inv(S)
+    k2r = int(math.ceil(w_ref * np.linalg.norm(Sinv[:, 0]))) + 1
+    k3r = int(math.ceil(w_ref * np.linalg.norm(Sinv[:, 1]))) + 1
+    ce, se = math.cos(det.eps), math.sin(det.eps)
+    out = []
+    for k2 in range(-k2r, k2r + 1):
+        for k3 in range(-k3r, k3r + 1):
+            a1 = k2 * B[2, 2] + k3 * B[3, 2]
+            a2 = k2 * B[2, 3] + k3 * B[3, 3]
+            ny, nx = a1 / w_ref, a2 / w_ref        # ecliptic n0_y, n0_x (Eq. albe)
+            r2 = nx * nx + ny * ny
+            if r2 > 1.0 or not (box[0] <= nx <= box[1] and box[2] <= ny <= box[3]):
+                continue
+            c1 = k2 * B[2, 1] + k3 * B[3, 1]
+            lo, hi = sorted(((w1lo - c1) / B[1, 1], (w1hi - c1) / B[1, 1]))
+            rows = []
+            for k1 in range(int(math.ceil(lo)), int(math.floor(hi)) + 1):
+                om1 = k1 * B[1, 1] + c1
+                if om1 < w1lo or om1 > w1hi:
+                    continue
+                c0 = k1 * B[1, 0] + k2 * B[2, 0] + k3 * B[3, 0]
+                x = c0 / dp0 - fl * nfft * dt
+                rows.append((om1 / tp, x - math.floor(x), k1))
+            if not rows:
+                continue
+            nz_abs = math.sqrt(max(0.0, 1.0 - r2))
+            for nz in ((nz_abs, -nz_abs) if nz_abs > 0.0 else (0.0,)):
+                ex, ey, ez = nx, ce * ny - se * nz, se * ny + ce * nz   # n_eq = Rot(eps)^T n0
+                alpha = math.atan2(ey, ex) % tp
+                delta = math.asin(max(-1.0, min(1.0, ez)))
+                out.append((alpha, delta, rows))
+    return out

@@ -367,6 +367,37 @@ FS_API fs_status fs_lattice(int32_t dim, const double *G_host, double C0, double
 FS_API fs_status fs_lattice_nodes(const double *basis_host, const fs_detector *det, double fl, double f0_min,
                                   double f0_max, double f1_min, double f1_max, fs_point *pts_host, int64_t cap,
                                   int64_t *count);
+/* Templates of the FFT search of that lattice (Sec. IV: a0 on the Fourier
+ * spacing makes every line of nodes along a0 one zero-padded transform; Sec.
+ * VII evaluates F over the whole band for each (omega1, alpha1, alpha2)).
+ * basis_host: fs_lattice with both constraints and dp0 = 2 pi / (nfft dt).
+ * Per sky node (alpha1, alpha2) and hemisphere one sky position (Eq. albe
+ * read at the band's upper edge, omega0 = 2 pi (fl + 1/(2 dt))), inside the
+ * ecliptic-component box box_host = (n_x lo, n_x hi, n_y lo, n_y hi) (NULL:
+ * the whole sky); per sky a row of the spindown nodes in [f1_min, f1_max]
+ * Hz/s and, for each, the fraction d in [0, 1) of a bin by which its line
+ * falls off the Fourier grid: its nodes are f0 = (k + d) / (nfft dt) above fl.
+ * Rows are padded to the longest, *nspin, by repeating their last node.
+ * alpha_host, delta_host: sky_cap doubles; f1_host, offset_host: sky_cap x
+ * spin_cap doubles, row-major with row length *nspin.  With sky_cap = spin_cap
+ * = 0 the call only returns *nsky and *nspin; FS_ERR_CAPACITY (with both
+ * counts) when they exceed the capacities; FS_ERR_ARG for a basis not of that
+ * form.  Host only. */
+FS_API fs_status fs_lattice_templates(const double *basis_host, const fs_detector *det, double fl, int64_t nfft,
+                                      double dt, double f1_min, double f1_max, const double *box_host,
+                                      double *alpha_host, double *delta_host, double *f1_host, double *offset_host,
+                                      int64_t sky_cap, int32_t spin_cap, int64_t *nsky, int32_t *nspin);
+/* Coarse search of lattice templates: as fs_search, but template (s, m) has its
+ * own spindown f1_dev[s * nspin + m] and evaluates F at the frequencies
+ * (k + offset_dev[s * nspin + m]) / (nfft dt) above fl (the data times
+ * exp(-2 pi i d j / nfft) before the transform, Eq. eq:DFT at a shifted
+ * frequency); a candidate's bin k means that frequency.  Device arrays of
+ * nsky * nspin doubles, offsets in [0, 1).  FP32 segments without
+ * interbinning, nbins = nfft/2, nfft <= 2^20 (else FS_ERR_UNSUPPORTED). */
+FS_API fs_status fs_search_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const double *delta_dev,
+                                   int32_t nsky, const double *f1_dev, const double *offset_dev, int32_t nspin,
+                                   float F_thr, float *F_out_dev, int64_t nbins, fs_candidate *cand_dev,
+                                   int64_t cand_cap, int64_t *n_cand_dev, void *stream);
 
 /* Synchronise `stream` and return (and clear) the first device-side error
  * latched since the last call, or FS_OK. */

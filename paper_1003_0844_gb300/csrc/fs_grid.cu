@@ -666,4 +666,95 @@ fs_status fs_lattice_nodes(const double *basis, const fs_detector *det, double f
   return cnt > cap ? FS_ERR_CAPACITY : FS_OK;
 }
 
+fs_status fs_lattice_templates(const double *basis, const fs_detector *det, double fl, int64_t nfft, double dt,
+                               double f1_min, double f1_max, const double *box, double *alpha, double *delta,
+                               double *f1, double *offset, int64_t sky_cap, int32_t spin_cap, int64_t *nsky,
+                               int32_t *nspin) {
+  if (!basis || !det || !nsky || !nspin || sky_cap < 0 || spin_cap < 0) return FS_ERR_ARG;
+  if (sky_cap > 0 && (!alpha || !delta || !f1 || !offset)) return FS_ERR_ARG;
+  if (nfft < 2 || !(dt > 0.0) || !(f1_max >= f1_min) || !(fl > 0.0)) return FS_ERR_ARG;
+  const double tp = 2.0 * M_PI;
+  const double *B0 = basis, *B1 = basis + 4, *B2 = basis + 8, *B3 = basis + 12;
+  // a0 must be the transform's Fourier spacing and a1 free of sky components
+  // (zeros up to the rounding of the construction)
+  const double dp0 = B0[0];
+  if (!(fabs(dp0 - tp / ((double)nfft * dt)) <= 1e-9 * dp0)) return FS_ERR_ARG;
+  double scale[4] = {0, 0, 0, 0};
+  for (int r = 0; r < 4; r++)
+    for (int c = 0; c < 4; c++) scale[c] = fmax(scale[c], fabs(basis[4 * r + c]));
+  for (int c = 1; c < 4; c++)
+    if (fabs(B0[c]) > 1e-9 * scale[c]) return FS_ERR_ARG;
+  for (int c = 2; c < 4; c++)
+    if (fabs(B1[c]) > 1e-9 * scale[c]) return FS_ERR_ARG;
+  if (B1[1] == 0.0) return FS_ERR_ARG;
+  const double bx[4] = {box ? box[0] : -1.0, box ? box[1] : 1.0, box ? box[2] : -1.0, box ? box[3] : 1.0};
+  const double w_ref = tp * (fl + 0.5 / dt);  // sky positions at the band's upper edge (Eq. albe)
+  const double w1lo = tp * f1_min, w1hi = tp * f1_max;
+  const double s00 = B2[2], s01 = B2[3], s10 = B3[2], s11 = B3[3];
+  const double dS = s00 * s11 - s01 * s10;
+  if (dS == 0.0) return FS_ERR_ARG;
+  // k^T = alpha^T S^-1 with S^-1 = [[s11, -s01], [-s10, s00]] / dS: |k_i| <= w_ref |column i|
+  const int64_t k2r = (int64_t)ceil(w_ref * sqrt(s11 * s11 + s10 * s10) / fabs(dS)) + 1;
+  const int64_t k3r = (int64_t)ceil(w_ref * sqrt(s01 * s01 + s00 * s00) / fabs(dS)) + 1;
+  if ((double)(2 * k2r + 1) * (double)(2 * k3r + 1) > 4e8) return FS_ERR_SHAPE;
+  const double ce = cos(det->eps), se = sin(det->eps);
+  const double fl_bins = fl * (double)nfft * dt;
+  std::vector<std::pair<double, double>> row;  // (f1, bin offset) of one line family
+  int64_t ns = 0;
+  int32_t nmax = 0;
+  for (int pass = 0; pass < 2; pass++) {  // pass 0 sizes (skies, longest row), pass 1 writes
+    ns = 0;
+    for (int64_t k2 = -k2r; k2 <= k2r; k2++)
+      for (int64_t k3 = -k3r; k3 <= k3r; k3++) {
+        const double a1 = k2 * B2[2] + k3 * B3[2], a2 = k2 * B2[3] + k3 * B3[3];
+        const double ny = a1 / w_ref, nx = a2 / w_ref;  // ecliptic n0_y, n0_x
+        const double r2 = nx * nx + ny * ny;
+        if (r2 > 1.0 || !(nx >= bx[0] && nx <= bx[1] && ny >= bx[2] && ny <= bx[3])) continue;
+        const double c1 = k2 * B2[1] + k3 * B3[1];
+        double lo = (w1lo - c1) / B1[1], hi = (w1hi - c1) / B1[1];
+        if (lo > hi) std::swap(lo, hi);
+        row.clear();
+        for (int64_t k1 = (int64_t)ceil(lo); (double)k1 <= hi; k1++) {
+          const double om1 = k1 * B1[1] + c1;
+          if (om1 < w1lo || om1 > w1hi) continue;
+          // the line omega0 = c0 + k0 dp0 sits on bins k shifted by the fraction xb - floor(xb)
+          const double c0 = k1 * B1[0] + k2 * B2[0] + k3 * B3[0];
+          const double xb = c0 / dp0 - fl_bins;
+          double d = xb - floor(xb);
+          if (d >= 1.0) d = 0.0;
+          row.push_back({om1 / tp, d});
+        }
+        if (row.empty()) continue;
+        const double nz_abs = sqrt(fmax(0.0, 1.0 - r2));
+        const int nh = nz_abs > 0.0 ? 2 : 1;
+        if (pass == 0) {
+          nmax = std::max(nmax, (int32_t)row.size());
+        } else {
+          for (int h = 0; h < nh; h++) {
+            const int64_t sk = ns + h;
+            const double nz = h ? -nz_abs : nz_abs;
+            const double ex = nx, ey = ce * ny - se * nz, ez = se * ny + ce * nz;  // n_eq = Rot(eps)^T n0
+            double a = atan2(ey, ex);
+            if (a < 0) a += tp;
+            alpha[sk] = a;
+            delta[sk] = asin(fmax(-1.0, fmin(1.0, ez)));
+            for (int32_t q = 0; q < nmax; q++) {  // shorter rows repeat their last node
+              const auto &e = row[std::min<size_t>((size_t)q, row.size() - 1)];
+              f1[sk * nmax + q] = e.first;
+              offset[sk * nmax + q] = e.second;
+            }
+          }
+        }
+        ns += nh;
+      }
+    if (pass == 0) {
+      *nsky = ns;
+      *nspin = nmax;
+      if (sky_cap == 0 && spin_cap == 0) return FS_OK;  // size query
+      if (ns > sky_cap || nmax > spin_cap) return FS_ERR_CAPACITY;
+    }
+  }
+  return FS_OK;
+}
+
 }  // extern "C"

@@ -56,6 +56,9 @@ struct Pass1Args {
   int vshift;
   float inv_nfft_total;  // 1 / Nfft
   float2 *Z;  // [batch][2][N1][N2]
+  // lattice templates (LAT items): f1 and the bin offset d per template of the group
+  // (index sky * nspin + spin); the chirp gains exp(-2 pi i d j / Nfft)
+  const double *bin_offset;
 };
 
 // CW columns per CTA; a warp holds CW columns x 2 signals x TPW sub-DFT threads.
@@ -72,7 +75,8 @@ __device__ __forceinline__ float2 chirp_cycles(float f) {
 // tile, writing Z slot zs.  Needs P * 2 * CW threads; xch holds L * 2 * CW
 // float2, twL the table W_L^q (q < L).  The caller synchronises before and after.
 // N2T: N2 at compile time (0: A.N2 at run time); the sub-transform length is then P Q N2T.
-template <int P, int Q, int CW, int AM, int VS = 0, int N2T = 0>
+// LAT: lattice templates (own f1 and bin offset per template, Pass1Args::bin_offset).
+template <int P, int Q, int CW, int AM, int VS = 0, int N2T = 0, bool LAT = false>
 __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, int tile, float2 *xch,
                                            const float2 *twL) {
   constexpr int L = P * Q;
@@ -87,7 +91,8 @@ __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, i
   const int n2 = tile * CW + col;
   const float2 *y = (sig ? A.yb : A.ya) + sky * A.sky_stride;
   const float2 *qq = A.qq + sky * A.sky_stride;
-  const df32 f1 = df_from_double(A.f1[spin]);
+  const df32 f1 = df_from_double(A.f1[LAT ? tr : spin]);
+  const float boff = LAT ? (float)A.bin_offset[tr] : 0.f;
   const int n1max = A.n1max;
   const int64_t N2 = N2T ? (int64_t)N2T : (int64_t)A.N2;
 
@@ -115,6 +120,10 @@ __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, i
         float f = df_mul_frac(f1, df32{qv[ap].x, qv[ap].y});
         if (VS > 0 && par) {  // sub-transform shift: exact fraction (j < 2^24)
           f += (float)(par * (my * N2 + n2)) * A.inv_nfft_total;
+          f -= rintf(f);
+        }
+        if constexpr (LAT) {  // bin offset d: d j / Nfft < 1 cycle, error ~ 1e-7 cycles
+          f = fmaf(boff * (float)(my * N2 + n2), A.inv_nfft_total, f);
           f -= rintf(f);
         }
         cm = chirp_cycles(f);
@@ -555,8 +564,9 @@ __device__ inline void wait_at_least(const unsigned *p, unsigned target, uint32_
   }
 }
 
-// IB: pass-2 items are interbinning items (pass2_item_ib).
-template <int P1, int Q1, int AM, int P2, int Q2, int NT, int MINB, int VS, bool IB = false>
+// IB: pass-2 items are interbinning items (pass2_item_ib); LAT: pass-1 items of
+// lattice templates.
+template <int P1, int Q1, int AM, int P2, int Q2, int NT, int MINB, int VS, bool IB = false, bool LAT = false>
 __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2, QueueArgs Qa) {
   constexpr int CW = NT / (2 * P1);
   constexpr int L1 = P1 * Q1, L2 = P2 * Q2;
@@ -632,7 +642,7 @@ __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2,
       }
       // the items take N1, N2 at run time: compiled in, they measured 5.5% slower here
       const int zs = d.tm - fdiv(d.tm, Qa.slots_fd) * Qa.slots;
-      if (d.is1) pass1_item<P1, Q1, CW, AM, VS, 0>(A1, d.tm, zs, d.j, work, twL);
+      if (d.is1) pass1_item<P1, Q1, CW, AM, VS, 0, LAT>(A1, d.tm, zs, d.j, work, twL);
       else if constexpr (IB) pass2_item_ib<P2, Q2, NT / 32>(A2, d.tm, zs, d.j - T1, work, twM);
       else pass2_item<P2, Q2, NT / 32, false, true, VS, false, 0>(A2, d.tm, zs, d.j - T1, work, twM);
     }
@@ -696,11 +706,11 @@ constexpr size_t persist_smem() {
 template <int P1, int Q1, int P2, int Q2, int NT>
 constexpr int persist_minb() { return persist_smem<P1, Q1, P2, Q2, NT>() <= 74 * 1024 ? kPersistMinBlocks : 2; }
 
-template <int P1, int Q1, int AM, int P2, int Q2, int NT, int VS, bool IB = false>
+template <int P1, int Q1, int AM, int P2, int Q2, int NT, int VS, bool IB = false, bool LAT = false>
 static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
   constexpr int MINB = persist_minb<P1, Q1, P2, Q2, NT>();
   const size_t sm = persist_smem<P1, Q1, P2, Q2, NT>();
-  auto kern = k_passes<P1, Q1, AM, P2, Q2, NT, MINB, VS, IB>;
+  auto kern = k_passes<P1, Q1, AM, P2, Q2, NT, MINB, VS, IB, LAT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, occ = 0;
@@ -718,11 +728,11 @@ static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, con
 
 // VS: sub-transforms per template (2^VS) compiled in; only the 2^20 split is
 // built with VS = 1 (the 2^21 transform).
-template <int P1, int Q1, int P2, int Q2, int NT, int VS = 0, bool IB = false>
+template <int P1, int Q1, int P2, int Q2, int NT, int VS = 0, bool IB = false, bool LAT = false>
 static cudaError_t launch_passes_am(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
   if (a1.vshift != VS) return cudaErrorInvalidValue;
-  if (a1.n1max <= P1 * Q1 / 2) return launch_passes_t<P1, Q1, P1 / 2, P2, Q2, NT, VS, IB>(a1, a2, qa, st);
-  return launch_passes_t<P1, Q1, P1, P2, Q2, NT, VS, IB>(a1, a2, qa, st);
+  if (a1.n1max <= P1 * Q1 / 2) return launch_passes_t<P1, Q1, P1 / 2, P2, Q2, NT, VS, IB, LAT>(a1, a2, qa, st);
+  return launch_passes_t<P1, Q1, P1, P2, Q2, NT, VS, IB, LAT>(a1, a2, qa, st);
 }
 
 // Work-item geometry of the persistent kernel for NT threads per CTA.
@@ -750,6 +760,11 @@ cudaError_t launch_interbin(const Pass2Args &a, int nb, cudaStream_t st);
 cudaError_t dispatch_passes_ib(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
                                cudaStream_t st);
 bool passes_ib_instantiated(int N1, int N2);
+// Persistent launch of lattice templates (LAT items) for the default split of
+// 2^12 .. 2^20; cudaErrorInvalidValue for another split.
+cudaError_t dispatch_passes_lat(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
+                                cudaStream_t st);
+bool passes_lat_instantiated(int N1, int N2);
 // Per-template stride (float2) of the interbinning items' edge rows.
 inline int64_t ib_edge_stride(int N1, int N2, int NT) {
   const int P2 = N2 <= 128 ? 8 : 16;
@@ -811,8 +826,10 @@ fs_status config32(const fs_ctx *ctx, const fs_seg *seg, int nsky, int64_t nbins
 fs_status workspace32(fs_ctx *ctx, int slot, const fs_seg *seg, const Cfg32 &c, int nsky, int nspin,
                       bool may_alloc, cudaStream_t st, Ws32 *w);
 // Enqueue one search on `st` with a laid-out workspace; allocates nothing.
+// lat_offset: NULL, or lattice templates (f1 and lat_offset per template, nsky x nspin).
 fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, const double *alpha,
                        const double *delta, int nsky, const double *f1, int nspin, float thr, float *F,
-                       int64_t nbins, fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st);
+                       int64_t nbins, fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st,
+                       const double *lat_offset = nullptr);
 
 }  // namespace fs

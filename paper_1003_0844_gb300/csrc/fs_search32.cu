@@ -436,7 +436,9 @@ static void pass_args(const fs_seg *seg, const Cfg32 &c, const Ws32 &w, const do
 
 fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, const double *alpha,
                        const double *delta, int nsky, const double *f1, int nspin, float thr, float *F,
-                       int64_t nbins, fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st) {
+                       int64_t nbins, fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st,
+                       const double *lat_offset) {
+  if (lat_offset && !c.persistent) return FS_ERR_UNSUPPORTED;
   const int64_t n = seg->g.n;
   if (cudaMemsetAsync(ncand, 0, sizeof(int64_t), st) != cudaSuccess) return FS_ERR_CUDA;
   DemodArgs DA = demod_args(seg, w, c.npad);
@@ -463,6 +465,10 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
     ctx->launches += 2;
     const int ntm = (gs * nspin) << c.vshift;  // virtual templates of the group
     p2.sky_base = g0;
+    if (lat_offset) {  // the group's rows of per-template spindowns and bin offsets
+      p1.f1 = f1 + (int64_t)g0 * nspin;
+      p1.bin_offset = lat_offset + (int64_t)g0 * nspin;
+    }
     p2.F = F ? F + (int64_t)g0 * nspin * nbins : nullptr;
     if (c.persistent) {
       QueueArgs qa{};
@@ -484,6 +490,8 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
           p2.eb_stride = ib_edge_stride(c.sh.N1, c.sh.N2, kPersistThreads);
           if (dispatch_passes_ib(c.sh.N1, c.sh.N2, p1, p2, qa, st) != cudaSuccess) return FS_ERR_CUDA;
           ctx->launches += 1;  // the edge bins
+        } else if (lat_offset) {
+          if (dispatch_passes_lat(c.sh.N1, c.sh.N2, p1, p2, qa, st) != cudaSuccess) return FS_ERR_CUDA;
         } else if (dispatch_passes(c.sh.N1, c.sh.N2, p1, p2, qa, st) != cudaSuccess) {
           return FS_ERR_CUDA;
         }
@@ -513,6 +521,20 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
     }
   }
   return FS_OK;
+}
+
+fs_status search32_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
+                           const double *f1, const double *offset, int nspin, float thr, float *F, int64_t nbins,
+                           fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st) {
+  Cfg32 c;
+  fs_status s = config32(ctx, seg, nsky, nbins, &c);
+  if (s != FS_OK) return s;
+  if (c.interbin || c.vshift || c.full || !c.persistent || !passes_lat_instantiated(c.sh.N1, c.sh.N2))
+    return FS_ERR_UNSUPPORTED;
+  Ws32 w;
+  s = workspace32(ctx, 0, seg, c, nsky, nspin, true, st, &w);
+  if (s != FS_OK) return s;
+  return search32_run(ctx, seg, c, w, alpha, delta, nsky, f1, nspin, thr, F, nbins, cand, cap, ncand, st, offset);
 }
 
 fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,

@@ -28,7 +28,7 @@ EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_prepare_segment_
            "fs_get_stats", "fs_search_noalloc", "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune",
            "fs_fstat_points", "fs_refine", "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm_cell",
            "fs_false_alarm", "fs_threshold", "fs_cell_count", "fs_linear_model_fisher", "fs_lattice",
-           "fs_lattice_nodes"]
+           "fs_lattice_nodes", "fs_lattice_templates", "fs_search_lattice"]
 PROF_KINDS = ("prepare", "demodulate", "pass1", "pass2", "other")
 
 
@@ -111,11 +111,15 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.fs_lattice.argtypes = [i32, ctypes.POINTER(f64), f64, f64, i32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
     lib.fs_lattice_nodes.argtypes = [ctypes.POINTER(f64), ctypes.POINTER(_Detector), f64, f64, f64, f64, f64, vp,
                                      i64, ctypes.POINTER(i64)]
+    lib.fs_lattice_templates.argtypes = [ctypes.POINTER(f64), ctypes.POINTER(_Detector), f64, i64, f64, f64, f64,
+                                         vp, vp, vp, vp, vp, i64, i32, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    lib.fs_search_lattice.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, f32, vp, i64, vp, i64, vp, vp]
     for name in ("fs_create", "fs_prepare_segment", "fs_prepare_segment_eph", "fs_seg_load", "fs_search", "fs_search_noalloc", "fs_sync_status",
                  "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling", "fs_get_stats",
                  "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune", "fs_fstat_points", "fs_refine",
                  "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm", "fs_threshold", "fs_cell_count",
-                 "fs_linear_model_fisher", "fs_lattice", "fs_lattice_nodes"):
+                 "fs_linear_model_fisher", "fs_lattice", "fs_lattice_nodes", "fs_lattice_templates",
+                 "fs_search_lattice"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -499,6 +503,49 @@ def lattice_nodes(basis, det, fl: float, f0_range, f1_range, cap: int = 1 << 20)
                               ctypes.byref(cnt))
     _check(st, "fs_lattice_nodes")
     return pts[:cnt.value].copy()
+
+
+def lattice_templates(basis, det, fl: float, nfft: int, dt: float, f1_range, box=None):
+    """Templates of the FFT search of the lattice (fs_lattice_templates): numpy arrays
+    alpha [nsky], delta [nsky], f1 [nsky, nspin], bin offset [nsky, nspin]."""
+    import numpy as np
+    lib = load_library()
+    b = np.ascontiguousarray(np.asarray(basis, dtype=np.float64))
+    d = _Detector(det.lat, det.lon, det.gamma, det.eps, det.lambda_e0, det.theta_g0)
+    bx = None if box is None else np.ascontiguousarray(np.asarray(box, dtype=np.float64))
+    ns, nm = ctypes.c_int64(), ctypes.c_int32()
+    args = (_dptr(b), ctypes.byref(d), float(fl), int(nfft), float(dt), float(f1_range[0]), float(f1_range[1]),
+            bx.ctypes.data_as(ctypes.c_void_p) if bx is not None else None)
+    _check(lib.fs_lattice_templates(*args, None, None, None, None, 0, 0, ctypes.byref(ns), ctypes.byref(nm)),
+           "fs_lattice_templates")
+    a, de = np.empty(ns.value), np.empty(ns.value)
+    f1, off = np.empty((ns.value, nm.value)), np.empty((ns.value, nm.value))
+    vpp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    _check(lib.fs_lattice_templates(*args, vpp(a), vpp(de), vpp(f1), vpp(off), ns.value, nm.value, ctypes.byref(ns),
+                                    ctypes.byref(nm)), "fs_lattice_templates")
+    return a, de, f1, off
+
+
+def search_lattice(ctx: Context, seg: Segment, alpha: torch.Tensor, delta: torch.Tensor, f1: torch.Tensor,
+                   offset: torch.Tensor, F_thr: float, write_F: bool = True, cand_cap: int = 1 << 16,
+                   stream=None) -> SearchResult:
+    """fs_search_lattice: sky s and row m have spindown f1[s, m] and F at the bins
+    k + offset[s, m] (device float64 [nsky, nspin] each); returns device tensors."""
+    for t, nm in ((alpha, "alpha"), (delta, "delta"), (f1, "f1"), (offset, "offset")):
+        _need_cuda(t, nm, torch.float64)
+    nsky = alpha.numel()
+    if delta.numel() != nsky or f1.dim() != 2 or f1.shape[0] != nsky or tuple(offset.shape) != tuple(f1.shape):
+        raise ValueError("alpha, delta [nsky] and f1, offset [nsky, nspin] expected")
+    nspin = f1.shape[1]
+    nb = seg.nfft // 2
+    F_out = torch.empty((nsky * nspin, nb), dtype=torch.float32, device="cuda") if write_F else None
+    cand = torch.empty((max(cand_cap, 1), 4), dtype=torch.int32, device="cuda")
+    n_cand = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = ctx.lib.fs_search_lattice(ctx.handle, seg.handle, _ptr(alpha), _ptr(delta), nsky, _ptr(f1), _ptr(offset),
+                                   nspin, float(F_thr), _ptr(F_out) if F_out is not None else None, nb, _ptr(cand),
+                                   int(cand.shape[0]) if cand_cap > 0 else 0, _ptr(n_cand), _stream(stream))
+    _check(st, "fs_search_lattice")
+    return SearchResult(F_out, cand, n_cand)
 
 
 def demodulate(ctx: Context, seg: Segment, alpha: float, delta: float, stream=None):

@@ -398,17 +398,22 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
 // [tiles2][first a, first b, last a, last b][N2/2], then X(Nfft/2) of a and b)
 // and k_interbin_edges forms those odd bins after the launch.  X(Nfft/2) =
 // sum_n2 Z[0][n2] (-1)^n2 comes from row 0 before its transform.
+// For P = 32 (1024-point rows) a warp holds one signal of one row, as in
+// pass2_item_wide: warps 2r, 2r + 1 hold signals a, b of row r.
 template <int P, int Q, int WARPS>
 __device__ __forceinline__ void pass2_item_ib(const Pass2Args &A, int tm, int zs, int rt, float2 *work,
                                               const float2 *twM) {
-  static_assert(P <= 16, "interbinning items need at least two rows per warp group");
-  constexpr int T = P, G = 16 / P, R = WARPS * G, S = Q / P, D = Q / 2, DP = D * P, FP = 2 * R + 1;
+  constexpr bool WIDE = (P == 32);
+  constexpr int T = P, G = WIDE ? 1 : 16 / P, R = WIDE ? WARPS / 2 : WARPS * G, S = Q / P, D = Q / 2, DP = D * P,
+                FP = 2 * R + 1;
   using X = Xch2<P, Q>;
   constexpr int XW = X::SIZE;
   static_assert(DP >= 32 && (DP & (DP - 1)) == 0, "a warp's F items share one row");
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int t = lane % T, sig = (lane / T) & 1, gr = lane / (2 * T);
-  const int row = w * G + gr;
+  const int t = WIDE ? lane : lane % T;
+  const int sig = WIDE ? (w & 1) : (lane / T) & 1;
+  const int gr = WIDE ? 0 : lane / (2 * T);
+  const int row = WIDE ? (w >> 1) : w * G + gr;
   const int k1 = rt * R + row;
   const int sky = fdiv(tm, A.nspin_fd), spin = tm - sky * A.nspin;
   constexpr int L2 = P * Q;
@@ -418,7 +423,7 @@ __device__ __forceinline__ void pass2_item_ib(const Pass2Args &A, int tm, int zs
   float2 v[Q];
   sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = __ldcg(z + Q * a + t + P * s); }); });
   float2 *eb = A.X + (int64_t)tm * A.eb_stride;
-  if (rt == 0 && w == 0) {  // row k1 = 0 (lanes with gr = 0): X(Nfft/2); n2 = Q a + t + P s has the parity of t
+  if (rt == 0 && (WIDE ? w < 2 : w == 0)) {  // row k1 = 0 (gr = 0): X(Nfft/2); n2 = Q a + t + P s has t's parity
     float2 sum = make_float2(0.f, 0.f);
     sfor<0, Q>([&](auto i) { sum = cadd(sum, v[i]); });
     if (t & 1) sum = make_float2(-sum.x, -sum.y);
@@ -428,7 +433,7 @@ __device__ __forceinline__ void pass2_item_ib(const Pass2Args &A, int tm, int zs
     }
     if (gr == 0 && t == 0) eb[(int64_t)tiles2 * 4 * DP + sig] = sum;
   }
-  float2 *xw = work + (w * 2 * G + (sig + 2 * gr)) * XW;
+  float2 *xw = WIDE ? work + w * XW : work + (w * 2 * G + (sig + 2 * gr)) * XW;
   sfor<0, S>([&](auto s) {
     const int b = t + P * s;
     dft_inplace<P>(v + s * P);
@@ -754,8 +759,7 @@ cudaError_t dispatch_pass2x(int N2, const Pass2Args &a, int nb, cudaStream_t st)
 // Interbinning epilogue (Eq. intbin) over nb templates of a batch from a.X.
 cudaError_t launch_interbin(const Pass2Args &a, int nb, cudaStream_t st);
 // Persistent launch with interbinning items for the default split N1 x N2 of
-// 2^12 .. 2^19 (N2 <= 512; also 256 x 512), and the edge bins after
-// it (k_interbin_edges);
+// 2^12 .. 2^20 (also 256 x 512), and the edge bins after it (k_interbin_edges);
 // cudaErrorInvalidValue for another split (passes_ib_instantiated is false).
 cudaError_t dispatch_passes_ib(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
                                cudaStream_t st);
@@ -767,8 +771,8 @@ cudaError_t dispatch_passes_lat(int N1, int N2, const Pass1Args &a1, const Pass2
 bool passes_lat_instantiated(int N1, int N2);
 // Per-template stride (float2) of the interbinning items' edge rows.
 inline int64_t ib_edge_stride(int N1, int N2, int NT) {
-  const int P2 = N2 <= 128 ? 8 : 16;
-  const int R = (NT / 32) * (16 / P2);
+  const int P2 = N2 <= 128 ? 8 : (N2 <= 512 ? 16 : 32);
+  const int R = P2 == 32 ? (NT / 32) / 2 : (NT / 32) * (16 / P2);
   return (int64_t)(N1 / R) * 4 * (N2 / 2) + 2;
 }
 // Persistent launch for an N1 x N2 split; cudaErrorInvalidValue for a split

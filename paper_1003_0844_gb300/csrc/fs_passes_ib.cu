@@ -1,5 +1,5 @@
 // Persistent transform launches with interbinning items (Eq. intbin, Sec. VI.B)
-// for the default split of each transform length 2^12 .. 2^19 (and the other
+// for the default split of each transform length 2^12 .. 2^20 (and the other
 // near-square split of 2^17), followed by the odd bins of the tile edges.
 #include "fs_pass32.cuh"
 
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) k_interbin_edges(Pass2Args A, int ntm, in
 template <int P1, int Q1, int P2, int Q2>
 static cudaError_t launch_ib(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
   constexpr int NT = kPersistThreads;
-  constexpr int R = (NT / 32) * (16 / P2), DP = P2 * Q2 / 2;
+  constexpr int R = P2 == 32 ? (NT / 32) / 2 : (NT / 32) * (16 / P2), DP = P2 * Q2 / 2;
   // the item's rows (float2 [R][2][DP]) and F tile (float [DP][2R + 1]) fit the work area
   static_assert(2 * R * DP + (DP * (2 * R + 1) + 1) / 2 <=
                     persist_smem<P1, Q1, P2, Q2, NT>() / sizeof(float2) - P1 * Q1 - P2 * Q2,
@@ -94,6 +94,7 @@ cudaError_t dispatch_passes_ib(int N1, int N2, const Pass1Args &a1, const Pass2A
     case 256 * 4096 + 512: return launch_ib<16, 16, 16, 32>(a1, a2, qa, st);
     case 512 * 4096 + 512: return launch_ib<16, 32, 16, 32>(a1, a2, qa, st);
     case 1024 * 4096 + 512: return launch_ib<32, 32, 16, 32>(a1, a2, qa, st);
+    case 1024 * 4096 + 1024: return launch_ib<32, 32, 32, 32>(a1, a2, qa, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -109,6 +110,7 @@ bool passes_ib_instantiated(int N1, int N2) {
     case 256 * 4096 + 512:
     case 512 * 4096 + 512:
     case 1024 * 4096 + 512:
+    case 1024 * 4096 + 1024:
       return true;
   }
   return false;

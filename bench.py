@@ -200,37 +200,93 @@ def cpu_oracle_rate(x, wl, det, alpha, delta, f1, ntempl):
     return done / dt, dt, done
 
 
+def _grid_config(wl, nsky, nspin, world):
+    """config of a single-segment workload (both arms)."""
+    return {"workload": wl.name, "n": wl.n, "nfft": wl.nfft, "nsky": nsky, "nspin": nspin,
+            "templates_per_gpu": nsky * nspin, "nbins": wl.nbins, "F_thr": wl.F_thr, "F_written": True,
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky shards x%d" % world}
+
+
 def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on the host cores, each step a
+    bounded sample of the workload (grid workloads: segment preparation plus a few
+    templates; batches: preparation plus one template of each segment kind; the fine
+    search: one exact-F pass with gradient and Hessian, 1/21 of a candidate's work)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import response as orsp
-    wl = W.WORKLOADS[args.workload]
-    det = W.detector_for(wl)
-    x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float32)
-    alpha, delta = W.sky_grid(wl.nsky)
-    f1 = W.spin_grid(wl.nspin, *wl.f1_range)
-    per_step = 4  # templates per step: each step is a bounded sample of the workload
+    from oracle import earth as oe, refine as orf, response as orsp
+    metric, unit = METRICS.get(args.workload, METRIC), "templates/s"
+    if args.workload in W.BATCHES:
+        b = W.BATCHES[args.workload]
+        det = W.detector_for(b)
+        kinds = {}
+        for wl, t0 in zip(b.segments(), b.epochs()):
+            kinds.setdefault((wl.days, wl.nfft), (wl, float(t0)))
+        a_all, d_all = W.sky_grid(b.nsky)
+        f1 = W.spin_grid(b.nspin, *b.f1_range)
+        data = []
+        for wl, t0 in kinds.values():
+            dk = oe.detector_at_epoch(det, t0)
+            x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, dk, wl.sigma)).astype(np.float32)
+            data.append((x, wl, dk))
+
+        def sample():
+            return sum(cpu_oracle_rate(x, wl, dk, a_all[:1], d_all[:1], f1[:1], 1)[2] for x, wl, dk in data)
+        nsub = args.nsky or 64
+        config = {"workload": args.workload, "segments": len(b.segments()),
+                  "segment_kinds": [list(p) for p in b.parts], "dt": b.dt, "nsky": nsub, "nsky_lattice": b.nsky,
+                  "nspin": b.nspin, "templates_per_gpu": len(b.segments()) * nsub * b.nspin, "F_thr": b.F_thr,
+                  "F_written": False, "l2": "flushed between timed steps (256 MiB write)",
+                  "parallelism": "sky shards x%d" % args.gpus, "graph": "one CUDA graph per batch, two branches"}
+        what = "one template of each of the %d segment kinds with its preparation" % len(data)
+        per_unit = 1.0
+    elif args.workload == "refine_2d":
+        wl = W.WORKLOADS["grid_2d"]
+        det = W.detector_for(wl)
+        x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float64)
+        inj = W.injections(wl)[0]
+        th = np.array([inj.f0, inj.f1, inj.alpha, inj.delta])
+
+        def sample():
+            orf.fstat_point(x, wl.dt, th, wl.fl, det, wl.S0, grad=True, hess=True)
+            return 1
+        metric, unit = METRICS["refine_2d"], "candidates/s"
+        config = {"workload": "refine_2d", "n": wl.n, "candidates": args.cands, "newton_steps": 20,
+                  "coarse": "grid_2d search (256 sky x 16 spindowns), strongest %d crossings" % args.cands,
+                  "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky shards x%d" % args.gpus}
+        what = "one exact-F pass with gradient and Hessian (a candidate's climb takes 21)"
+        per_unit = 1.0 / 21.0
+    else:
+        wl = W.WORKLOADS[args.workload]
+        det = W.detector_for(wl)
+        x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float32)
+        alpha, delta = W.sky_grid(wl.nsky)
+        f1 = W.spin_grid(wl.nspin, *wl.f1_range)
+        per_step = max(2, int(16 * 86164 / wl.n))
+
+        def sample():
+            return cpu_oracle_rate(x, wl, det, alpha, delta, f1, per_step)[2]
+        config = _grid_config(wl, wl.nsky, wl.nspin, args.gpus)
+        what = "segment preparation + %d templates (FFT mode)" % per_step
+        per_unit = 1.0
     for _ in range(args.warmup):
-        cpu_oracle_rate(x, wl, det, alpha, delta, f1, per_step)
-    rates, secs = [], 0.0
+        sample()
     t0 = time.perf_counter()
     total = 0
     for _ in range(args.steps):
-        r, dt, n = cpu_oracle_rate(x, wl, det, alpha, delta, f1, per_step)
-        total += n
+        total += sample()
     wall = time.perf_counter() - t0
-    value = total / wall
+    value = total * per_unit / wall
+    config["sample_per_step"] = what
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "templates/s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": wl.n, "nfft": wl.nfft, "templates": wl.nsky * wl.nspin,
-                   "sample_templates_per_step": per_step},
-        "cpu_baseline": {"value": value, "unit": "templates/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d templates per step (oracle segment preparation + FFT-mode F), %d steps"
-                                   % (per_step, args.steps)},
-        "e2e": {"value": value, "unit": "templates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                         "sample": "%s per step, %d steps" % (what, args.steps)},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -634,9 +690,7 @@ def main():
         "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (FP64/double-float phases)", "data": "synthetic",
-        "config": {"workload": args.workload, "n": wl.n, "nfft": wl.nfft, "nsky": nsky, "nspin": nspin,
-                   "templates_per_gpu": ntempl, "nbins": nbins, "F_thr": wl.F_thr, "F_written": True,
-                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky shards x%d" % world},
+        "config": _grid_config(wl, nsky, nspin, world),
         "roofline": roof,
         "hbm_alg_gbs": hbm_alg, "hbm_peak_gbs": hbm_gbs, "hbm_peak_kind": hbm_kind,
         "kernel_ms_share": shares,

@@ -8,6 +8,7 @@ import pytest
 import torch
 
 from oracle import earth as oe
+from oracle import fstat as ofs
 from oracle import resample as ors
 from oracle import response as orsp
 from paper_1003_0844_gb300 import workloads as W
@@ -160,6 +161,43 @@ def test_batch_matches_oracle_and_single_searches(fs):
     F0, _ = _search_F(fs, ctx, s0, alpha, delta, f1, b.F_thr)
     ref = oracle_F(x, wl, oe.detector_at_epoch(det, t0[2]), alpha, delta, f1)
     assert max_rel_dF(F0, ref) > 10 * F32_TOL
+
+
+def test_batch_full_configuration_sampled(fs):
+    """The benchmark's batch (64 segments of 1/2/3/6 days, 2^16-2^20, 64 skies x 64
+    spindowns, one graph): for one template of each segment kind, the crossings the
+    batch reports equal the oracle's F above threshold (FFT mode, that template)."""
+    b = W.BATCHES["uneven_64"]
+    det = W.detector_for(b)
+    segs, t0 = b.segments(), b.epochs()
+    a_all, d_all = W.sky_grid(b.nsky)
+    alpha, delta = a_all[:64], d_all[:64]
+    f1 = W.spin_grid(b.nspin, *b.f1_range)
+    ctx = fs.Context(det)
+    xs, handles = [], []
+    for i, wl in enumerate(segs):
+        de = oe.detector_at_epoch(det, t0[i])
+        x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, de, wl.sigma)).astype(np.float32)
+        xs.append(x)
+        handles.append(fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0, t0=t0[i]))
+    res = fs.search_batch(ctx, handles, _dev(alpha), _dev(delta), _dev(f1), b.F_thr, cand_cap=1 << 16)
+    assert ctx.sync_status() == 0
+    g = np.random.default_rng(3)
+    seen = set()
+    for i, wl in enumerate(segs):
+        if (wl.days, wl.nfft) in seen:
+            continue
+        seen.add((wl.days, wl.nfft))
+        s, m = int(g.integers(0, len(alpha))), int(g.integers(0, len(f1)))
+        so = ors.Segment(xs[i].astype(np.float64), wl.dt)
+        ref = ofs.fstat(so, alpha[s], delta[s], f1[m], wl.fl, oe.detector_at_epoch(det, t0[i]), wl.S0, wl.nfft)
+        sky, spin, bins, Fc = res.candidates(i)
+        mine = (sky == s) & (spin == m)
+        z = np.zeros(int(mine.sum()), dtype=np.int64)
+        missing, bad = check_candidates(z, z, bins[mine], Fc[mine], ref[None, :], b.F_thr, 1)
+        assert not missing and not bad, (i, s, m, missing, bad)
+    assert len(seen) == 4
+    ctx.close()
 
 
 def test_batch_graph_replay_and_reload(fs):

@@ -262,3 +262,43 @@ def test_argument_errors(fs):
     with pytest.raises(fs.FstatError) as e:
         fs.search(ctx, seg, _dev(alpha), _dev(delta), _dev(f1), 10.0, nbins=wl.nfft // 4)
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("name", ["grid_2d", "grid_2d_ib", "wide_6d"])
+def test_full_configuration_sampled(fs, name):
+    """The benchmark's launch configuration (all 256 skies x 16 spindowns in one sky
+    group, the persistent queue sized as the bench sizes it): sampled template rows
+    against the oracle (FFT mode) and their candidates, and for all 4096 templates the
+    count of crossings equals the number of F values above threshold."""
+    wl = W.WORKLOADS[name]
+    det = W.detector_for(wl)
+    x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float32)
+    alpha, delta = W.sky_grid(wl.nsky)
+    f1 = W.spin_grid(wl.nspin, *wl.f1_range)
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0, interbin=wl.interbin)
+    res = fs.search(ctx, seg, _dev(alpha), _dev(delta), _dev(f1), wl.F_thr, cand_cap=1 << 20)
+    assert ctx.sync_status() == 0
+    F = res.F
+    assert F.shape == (wl.nsky * wl.nspin, wl.nbins)
+    assert bool(torch.isfinite(F).all()) and float(F.min()) >= 0.0
+    n = int(res.n_cand.item())
+    assert n == int((F > wl.F_thr).sum().item())
+    sky, spin, bins, Fc = res.candidates()
+    g = np.random.default_rng(5)
+    picks = sorted({0, wl.nsky * wl.nspin - 1, *g.integers(0, wl.nsky * wl.nspin, 4).tolist()})
+    so = ors.Segment(x.astype(np.float64), wl.dt)
+    for t in picks:
+        s, m = divmod(t, wl.nspin)
+        if wl.interbin:
+            ref = ofs.fstat_interbinned(so, alpha[s], delta[s], f1[m], wl.fl, det, wl.S0, wl.nfft)
+        else:
+            ref = ofs.fstat(so, alpha[s], delta[s], f1[m], wl.fl, det, wl.S0, wl.nfft)
+        row = F[t].double().cpu().numpy()
+        assert max_rel_dF(row, ref) <= F32_TOL, (t, max_rel_dF(row, ref))
+        mine = (sky == s) & (spin == m)
+        missing, bad = check_candidates(np.zeros(mine.sum(), dtype=np.int64), np.zeros(mine.sum(), dtype=np.int64),
+                                        bins[mine], Fc[mine], ref[None, :], wl.F_thr, 1)
+        assert not missing and not bad, (t, missing, bad)
+    seg.close()
+    ctx.close()

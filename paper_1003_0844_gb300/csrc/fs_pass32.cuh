@@ -733,9 +733,13 @@ static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, con
 
 // VS: sub-transforms per template (2^VS) compiled in; only the 2^20 split is
 // built with VS = 1 (the 2^21 transform).
-template <int P1, int Q1, int P2, int Q2, int NT, int VS = 0, bool IB = false, bool LAT = false>
+// AM4: also build the variant for data in the first quarter of the rows (n1max <= L/4).
+template <int P1, int Q1, int P2, int Q2, int NT, int VS = 0, bool IB = false, bool LAT = false, bool AM4 = false>
 static cudaError_t launch_passes_am(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
   if (a1.vshift != VS) return cudaErrorInvalidValue;
+  if constexpr (AM4) {
+    if (a1.n1max <= P1 * Q1 / 4) return launch_passes_t<P1, Q1, P1 / 4, P2, Q2, NT, VS, IB, LAT>(a1, a2, qa, st);
+  }
   if (a1.n1max <= P1 * Q1 / 2) return launch_passes_t<P1, Q1, P1 / 2, P2, Q2, NT, VS, IB, LAT>(a1, a2, qa, st);
   return launch_passes_t<P1, Q1, P1, P2, Q2, NT, VS, IB, LAT>(a1, a2, qa, st);
 }

@@ -73,27 +73,28 @@ constexpr int cx_bitrev(int i, int bits) {
 
 // In-place DFT of v[0..N) (N = 2..32), natural order in and out: radix-2
 // decimation in frequency, then a compile-time bit-reversal (register renaming).
-// NZ: the inputs v[NZ..N) are known to be zero (NZ = N, N/2 or N/4).  Within
-// every group of a stage the nonzero entries stay at offsets below NZ, so a
-// stage whose span is at least NZ reduces to copies and twiddle products (and
-// leaves the zero pairs alone).  NOUT: only outputs X[0..NOUT) are needed
-// (NOUT = N or N/2); with NOUT = N/2 the last stage skips the differences (they
-// land on odd bit-reversed positions).
+// NZ: the inputs v[NZ..N) are known to be zero.  After each stage the nonzero
+// entries of every group (2 span entries) stay at offsets below
+// min(NZ, 2 span), so a pair whose both entries lie beyond that is left alone,
+// and a pair whose second entry does reduces to a copy and a twiddle product.
+// NOUT: only outputs X[0..NOUT) are needed (NOUT = N or N/2); with NOUT = N/2
+// the last stage skips the differences (they land on odd bit-reversed positions).
 template <int N, int NZ = N, int NOUT = N>
 __device__ __forceinline__ void dft_inplace(float2 *v) {
-  static_assert(NZ == N || 2 * NZ == N || 4 * NZ == N, "pruning supports a zero upper half or three quarters");
+  static_assert(NZ >= 1 && NZ <= N, "NZ leading inputs may be nonzero");
   static_assert(NOUT == N || 2 * NOUT == N, "output pruning keeps the lower half only");
   constexpr int LG = cx_log2(N);
   sfor<0, LG>([&](auto st) {
     constexpr int span = N >> (st + 1);
+    constexpr int nz = NZ < 2 * span ? NZ : 2 * span;  // nonzero prefix of each group
     sfor<0, N / (2 * span)>([&](auto g) {
       sfor<0, span>([&](auto k) {
         constexpr int i0 = g * 2 * span + k;
-        if constexpr (NZ < N && span >= NZ) {
-          if constexpr (k < NZ) {
-            const float2 a = v[i0];
-            v[i0 + span] = twmul<2 * span, k>(a);
-          }
+        if constexpr (k >= nz) {
+          // both entries are zero
+        } else if constexpr (k + span >= nz) {
+          const float2 a = v[i0];
+          v[i0 + span] = twmul<2 * span, k>(a);
         } else if constexpr (st == LG - 1 && NOUT < N) {
           v[i0] = cadd(v[i0], v[i0 + span]);
         } else {

@@ -82,6 +82,7 @@ __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, i
   constexpr int L = P * Q;
   constexpr int S = Q / P;
   constexpr int CS = 2 * CW;     // (column, signal) pairs
+  static_assert(AM >= 2 && AM <= P && AM % 2 == 0, "rows with data come in chirp pairs");
   constexpr int TPW = 32 / CS;   // sub-DFT threads per warp
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int cs = lane % CS, col = cs % CW, sig = cs / CW;
@@ -733,12 +734,14 @@ static cudaError_t launch_passes_t(const Pass1Args &a1, const Pass2Args &a2, con
 
 // VS: sub-transforms per template (2^VS) compiled in; only the 2^20 split is
 // built with VS = 1 (the 2^21 transform).
-// AM4: also build the variant for data in the first quarter of the rows (n1max <= L/4).
-template <int P1, int Q1, int P2, int Q2, int NT, int VS = 0, bool IB = false, bool LAT = false, bool AM4 = false>
+// AMQ > 0: also build the variant for data in the rows n1 < AMQ Q1 (AMQ even, < P1/2),
+// whose first-pass DFTs skip the pairs known to be zero.
+template <int P1, int Q1, int P2, int Q2, int NT, int VS = 0, bool IB = false, bool LAT = false, int AMQ = 0>
 static cudaError_t launch_passes_am(const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa, cudaStream_t st) {
   if (a1.vshift != VS) return cudaErrorInvalidValue;
-  if constexpr (AM4) {
-    if (a1.n1max <= P1 * Q1 / 4) return launch_passes_t<P1, Q1, P1 / 4, P2, Q2, NT, VS, IB, LAT>(a1, a2, qa, st);
+  if constexpr (AMQ > 0) {
+    static_assert(AMQ % 2 == 0 && 2 * AMQ < P1, "a pruned variant below the half");
+    if (a1.n1max <= AMQ * Q1) return launch_passes_t<P1, Q1, AMQ, P2, Q2, NT, VS, IB, LAT>(a1, a2, qa, st);
   }
   if (a1.n1max <= P1 * Q1 / 2) return launch_passes_t<P1, Q1, P1 / 2, P2, Q2, NT, VS, IB, LAT>(a1, a2, qa, st);
   return launch_passes_t<P1, Q1, P1, P2, Q2, NT, VS, IB, LAT>(a1, a2, qa, st);

@@ -12,7 +12,7 @@ cudaError_t dispatch_passes_large(int N1, int N2, const Pass1Args &a1, const Pas
     case 1024 * 4096 + 1024:
       if (a1.vshift == 1) return launch_passes_am<32, 32, 32, 32, NT, 1>(a1, a2, qa, st);
       // data in a quarter of the rows (6 days at 2 s padded to 2^20) prunes two stages
-      return launch_passes_am<32, 32, 32, 32, NT, 0, false, false, true>(a1, a2, qa, st);
+      return launch_passes_am<32, 32, 32, 32, NT, 0, false, false, 8>(a1, a2, qa, st);
   }
   return cudaErrorInvalidValue;
 }

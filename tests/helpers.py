@@ -1,6 +1,7 @@
 """Shared test helpers: seeded cases built from the workload generators and
 the oracle's injection model, and the F / candidate comparison rules."""
 import math
+import os
 
 import numpy as np
 
@@ -65,3 +66,17 @@ def check_candidates(sky, spin, bins, Fc, Fref, thr, nspin, rel=1e-4):
     missing = must - got
     bad = [(t, b) for (t, b) in got if Fref[t, b] < thr * (1 - rel)]
     return missing, bad
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    """Values of a fixture under tests/golden/ ("key = value  # comment" lines)."""
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            k, v = (x.strip() for x in line.split("=", 1))
+            out[k] = float(v)
+    return out

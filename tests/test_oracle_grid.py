@@ -8,6 +8,7 @@ import pytest
 
 from oracle import grid as og
 from paper_1003_0844_gb300 import workloads as W
+from tests.helpers import golden
 
 
 def _brute_covering_radius(gen, n=60000, seed=3):
@@ -25,14 +26,18 @@ def _brute_covering_radius(gen, n=60000, seed=3):
     return best.max()
 
 
-@pytest.mark.parametrize("dim,theta", [(2, 2 * math.pi / (3 * math.sqrt(3))), (4, 1.7655)])
-def test_printed_a_star_generators(dim, theta):
-    """Eqs. A2gen and gen: covering radius R, thickness 1.2092 (hexagonal) and 1.7655 (A4*)."""
+@pytest.mark.parametrize("dim,key", [(2, "theta_A2star"), (4, "theta_A4star")])
+def test_printed_a_star_generators(dim, key):
+    """Eqs. A2gen and gen: covering radius R and the printed thicknesses
+    (tests/golden/sec4_lattice_thickness.txt), hexagonal = 2 pi / (3 sqrt 3)."""
+    theta = golden("sec4_lattice_thickness.txt")[key]
     R = 0.5
     M0 = og.a_star_generator(dim, R)
     Rv, holes = og.covering_radius(M0)
     assert abs(Rv - R) < 1e-12
     assert og.thickness(M0, Rv) == pytest.approx(theta, abs=1e-4)
+    if dim == 2:
+        assert theta == pytest.approx(2 * math.pi / (3 * math.sqrt(3)), abs=1e-4)
     rb = _brute_covering_radius(M0)
     assert 0.97 * R < rb <= R * (1 + 1e-9)
 
@@ -42,12 +47,13 @@ def test_two_dimensional_example():
     length of l and mu are reproduced; nu is fixed by the covering radius staying R
     (Eq. condition), which for this l gives the thinnest lattice with a0 as a basis
     vector: the isosceles Delaunay triangle on a0 with circumradius R."""
-    G = np.array([[1 / 12, 1 / 12], [1 / 12, 4 / 45]])
-    gen, th, d = og.constrained_lattice(G, 0.75, math.pi)
-    R, L = 0.5, math.pi / (2 * math.sqrt(3))
+    g = golden("sec4c_example_2d.txt")
+    G = np.array([[g["G_11"], g["G_12"]], [g["G_12"], g["G_22"]]])
+    gen, th, d = og.constrained_lattice(G, g["C0"], g["a0_1"])
+    R, L = 0.5, g["norm_Minv_a0"]
     assert np.linalg.norm(d["e0"]) == pytest.approx(L, rel=1e-12)
-    assert np.linalg.norm(d["l"]) == pytest.approx(1.5, rel=1e-12)      # |sqrt(3)/4 (3, sqrt(3))|
-    assert d["mu"] == pytest.approx(math.pi / (3 * math.sqrt(3)), rel=1e-12)
+    assert np.linalg.norm(d["l"]) == pytest.approx(math.hypot(g["l_1"], g["l_2"]), rel=1e-12)
+    assert d["mu"] == pytest.approx(g["mu"], rel=1e-12)
     assert th == pytest.approx(math.pi * R * R / (L * (R + math.sqrt(R * R - L * L / 4))), rel=1e-9)
     assert np.allclose(gen[0], [math.pi, 0.0], atol=1e-12)
     x = gen @ np.linalg.inv(d["Mx"].T)                  # the lattice in x = M^-1 tau
@@ -59,15 +65,16 @@ def test_printed_nu_of_the_example_is_not_a_tight_covering():
     """The example's printed nu = sqrt(108 - pi^2)/9 (thickness 18/sqrt(108 - pi^2) ~ 1.8171
     assuming radius R) leaves the covering radius at ~0.908 R for the same l and mu,
     so it does not meet Eq. condition: the reading used solves that condition."""
+    g = golden("sec4c_example_2d.txt")
     R = 0.5
     M0 = og.a_star_generator(2, R)
-    l = math.sqrt(3) / 4 * np.array([3.0, math.sqrt(3)])
+    l = np.array([g["l_1"], g["l_2"]])
     O1 = og._frame(l / np.linalg.norm(l))
-    mu, nu = math.pi / (3 * math.sqrt(3)), math.sqrt(108 - math.pi ** 2) / 9
+    mu, nu = g["mu"], g["nu_printed"]
     M = M0 @ O1 @ np.diag([mu, 1.0]) @ O1.T @ O1 @ np.diag([1.0, nu]) @ O1.T
     r = og.covering_radius(M)[0]
     assert r / R == pytest.approx(0.908, abs=1e-3)
-    assert og.thickness(M0, R) / (mu * nu) == pytest.approx(18 / math.sqrt(108 - math.pi ** 2), rel=1e-12)
+    assert og.thickness(M0, R) / (mu * nu) == pytest.approx(g["theta_printed"], abs=1e-4)
 
 
 def test_linear_model_fisher_closed_forms():

@@ -9,6 +9,7 @@ import pytest
 
 from oracle import earth, fstat, resample, response
 from paper_1003_0844_gb300 import workloads as W
+from tests.helpers import golden
 
 DET = W.Detector(lambda_e0=1.234, theta_g0=0.3)
 
@@ -223,9 +224,10 @@ def _worst_loss(pad):
 
 
 def test_zero_padding_losses_printed_in_paper():
-    # Sec. VI.B: worst loss 36.3% without padding, 9.97% with N zeros appended
-    assert abs(_worst_loss(1) - 0.363) < 1e-3
-    assert abs(_worst_loss(2) - 0.0997) < 1e-3
+    # Sec. VI.B (tests/golden/sec6b_losses.txt): worst loss without padding and with N zeros
+    g = golden("sec6b_losses.txt")
+    assert abs(_worst_loss(1) - g["loss_no_padding"]) < 1e-3
+    assert abs(_worst_loss(2) - g["loss_padding_2"]) < 1e-3
 
 
 # --------------------------------------------------------------------------- F-statistic (Sec. III)
@@ -399,8 +401,9 @@ def test_interbinning_worst_loss_is_13_percent():
         best = max(np.max(np.abs(X[95:106])), np.max(np.abs(H[95:106])))
         worst_ib = max(worst_ib, 1.0 - best / N)
         worst_plain = max(worst_plain, 1.0 - np.max(np.abs(X[95:106])) / N)
-    assert abs(worst_plain - 0.363) < 2e-3
-    assert abs(worst_ib - 0.13) < 6e-3, worst_ib
+    g = golden("sec6b_losses.txt")
+    assert abs(worst_plain - g["loss_no_padding"]) < 2e-3
+    assert abs(worst_ib - g["loss_interbinning"]) < 6e-3, worst_ib
 
 
 def test_interbinned_F_even_entries_are_the_plain_bins():

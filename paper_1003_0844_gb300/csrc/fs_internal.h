@@ -62,6 +62,7 @@ struct fs_seg {
   //   tab0[m] = (C.hi, C.lo, S.hi, S.lo) with C, S = (AU/c) (cos, sin) lambda_E(t_m)
   //   tab1[m] = (cos theta_m, sin theta_m, t_m.hi, t_m.lo)
   float4 *tab0 = nullptr, *tab1 = nullptr;
+  bool tables_ready = false;  // built by the first load (they do not depend on the data)
   double *x64 = nullptr;    // input as double [n]
   float *x32 = nullptr;     // input as float [n] (nearest-neighbour path)
   double *x2 = nullptr;     // Fourier x2 upsampled [2n]

@@ -10,10 +10,9 @@
 //      samples).  Both length-N transforms use Bluestein's chirp-z identity
 //      on power-of-two FP64 FFTs, so any N is accepted;
 //  P2  natural cubic spline through x2 at unit spacing: second derivatives
-//      from the [1 4 1] tridiagonal system by the Thomas recurrences, run in
-//      parallel chunks whose start and end are warmed up over 40 points
-//      (errors of the truncated recurrences shrink by (2 - sqrt 3)^40 ~ 1e-23),
-//      then per-interval polynomial coefficients.
+//      from the [1 4 1] tridiagonal system by the Thomas recurrences, exact at
+//      the ends and as 21-tap filters (their pole (2 - sqrt 3)^21 ~ 1e-12)
+//      one point per thread inside, then per-interval polynomial coefficients.
 #include <stdio.h>
 #include <algorithm>
 #include "fs_internal.h"
@@ -77,6 +76,7 @@ fs_status import_eph(fs_seg *seg, const double *r, const double *v, cudaStream_t
 }
 
 fs_status prepare_tables(fs_seg *seg, cudaStream_t st) {
+  if (seg->tables_ready) return FS_OK;  // they depend on the geometry only, not on the data
   const SegGeom &g = seg->g;
   k_tables32<<<(unsigned)((g.ngrid + 255) / 256), 256, 0, st>>>(g, seg->tab0, seg->tab1);
   seg->ctx->launches++;
@@ -85,7 +85,9 @@ fs_status prepare_tables(fs_seg *seg, cudaStream_t st) {
                                                                       seg->eph2);
     seg->ctx->launches++;
   }
-  return cuda_status(cudaGetLastError());
+  const fs_status r = cuda_status(cudaGetLastError());
+  seg->tables_ready = (r == FS_OK);
+  return r;
 }
 
 // ------------------------------------------------------------------ P1 upsampling
@@ -244,10 +246,12 @@ fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st) {
 // c'_i reaches its limit c = 2 - sqrt(3) in double within ~20 steps.  Away
 // from the ends both recurrences are first-order filters with pole -c, so
 //   d'_i = c sum_{k=0}^{K} (-c)^k r_{i-k},   M_i = sum_{k=0}^{K} (-c)^k d'_{i+k}
-// with K = 40 (the dropped tail weighs c^41 ~ 4e-24); these run one point per
-// thread.  The first and last kSplEnd points follow the exact recurrences
-// serially, so the result equals the sequential Thomas solution to rounding.
-constexpr int kSplK = 40;
+// with K = 20; these run one point per thread.  The first and last kSplEnd
+// points follow the exact recurrences serially.  The dropped tail weighs
+// c^21 ~ 1e-12 of the data's scale: the result equals the sequential Thomas
+// solution to that level, far below the FP32 coefficients' rounding and the
+// FP64 path's 1e-8 tolerance on F.
+constexpr int kSplK = 20;
 constexpr int kSplEnd = 64;
 
 __device__ inline double spline_climit() {

@@ -403,6 +403,14 @@ FS_API fs_status fs_search_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha
  * latched since the last call, or FS_OK. */
 FS_API fs_status fs_sync_status(fs_ctx *ctx, void *stream);
 
+/* Self-test of the bounded waits of the persistent transform queue (no
+ * counterpart in the paper: it exercises the failure path without a GPU
+ * fault).  Launches one block whose first thread waits, with the queue's own
+ * wait routine and bound, for a device counter that nothing increments; the
+ * wait runs out after its iteration limit (seconds), latches FS_ERR_TIMEOUT
+ * for fs_sync_status and the block returns.  The context stays usable. */
+FS_API fs_status fs_selftest_wait(fs_ctx *ctx, void *stream);
+
 /* Launch accounting and optional per-kernel timing.
  * launches: kernels launched by this context since the last reset.
  * With profiling on, every launch of the kinds below is bracketed by CUDA

@@ -251,6 +251,13 @@ fs_status fs_search(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const dou
                   cand_dev, cand_cap, n_cand_dev, st);
 }
 
+fs_status fs_selftest_wait(fs_ctx *ctx, void *stream) {
+  if (!ctx) return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  ctx->launches++;
+  return cuda_status(selftest_wait(ctx->d_flags, as_stream(stream)));
+}
+
 fs_status fs_search_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const double *delta_dev,
                             int32_t nsky, const double *f1_dev, const double *offset_dev, int32_t nspin, float F_thr,
                             float *F_out_dev, int64_t nbins, fs_candidate *cand_dev, int64_t cand_cap,

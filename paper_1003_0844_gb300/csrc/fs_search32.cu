@@ -13,6 +13,19 @@
 
 namespace fs {
 
+// ------------------------------------------------------------------ self-test of the bounded waits
+__device__ unsigned g_never_incremented = 0;  // nothing writes it
+
+__global__ void k_selftest_wait(uint32_t *flags) {
+  if (threadIdx.x == 0) wait_at_least(&g_never_incremented, 1u, flags);
+  __syncthreads();
+}
+
+cudaError_t selftest_wait(uint32_t *flags, cudaStream_t st) {
+  k_selftest_wait<<<1, 32, 0, st>>>(flags);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ per-sky constants
 __global__ void k_skyconst(const double *alpha, const double *delta, int nsky, SegGeom g, double eps,
                            double lat, double gamma, SkyConst32 *out32, SkyConst64 *out64) {

@@ -302,3 +302,26 @@ def test_full_configuration_sampled(fs, name):
         assert not missing and not bad, (t, missing, bad)
     seg.close()
     ctx.close()
+
+
+def test_bounded_wait_runs_out_and_the_context_recovers(fs):
+    """A wait of the persistent queue on a counter that nothing increments runs out
+    after its iteration bound, latches FS_ERR_TIMEOUT for the host and returns; the
+    same context then searches normally."""
+    import time
+    wl, det, x, alpha, delta, f1 = make_case("tiny")
+    ctx = fs.Context(det)
+    t0 = time.perf_counter()
+    ctx.selftest_wait()
+    assert ctx.sync_status() == 6          # FS_ERR_TIMEOUT
+    elapsed = time.perf_counter() - t0
+    assert elapsed < 120.0
+    print("bounded wait ran out after %.1f s" % elapsed)
+    assert ctx.sync_status() == 0          # cleared by the read
+    seg = fs.Segment(ctx, _dev(x.astype(np.float32), torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0)
+    res = fs.search(ctx, seg, _dev(alpha), _dev(delta), _dev(f1), wl.F_thr)
+    assert ctx.sync_status() == 0
+    ref = oracle_F(x.astype(np.float32).astype(np.float64), wl, det, alpha, delta, f1)
+    assert max_rel_dF(res.F.double().cpu().numpy(), ref) < F32_TOL
+    seg.close()
+    ctx.close()

@@ -87,8 +87,8 @@ enum { FS_X_F32 = 0, FS_X_F64 = 1 };
  * (interbinning, Eq. intbin, Sec. VI.B) for both Fa and Fb -- the frequency grid
  * of a transform padded to 2 nfft at the cost of one of length nfft.  Searches
  * of such a segment take nbins = nfft (the F row length) and report candidate
- * bins j on that grid; FP32 segments need nfft <= 2^20; fs_search_batch and
- * fs_search_noalloc do not take them (FS_ERR_UNSUPPORTED). */
+ * bins j on that grid (also in fs_search_batch); FP32 segments need
+ * nfft <= 2^20; fs_search_noalloc does not take them (FS_ERR_UNSUPPORTED). */
 enum { FS_OPT_INTERBIN = 1 };
 
 /* One data segment: x_k = x(k dt), k < n, t = 0 at the first sample.
@@ -216,7 +216,8 @@ FS_API fs_status fs_search_noalloc(fs_ctx *ctx, fs_seg *seg,
 /* First, coherent stage of a hierarchical search (Sec. I): the same template
  * grid searched in each of nseg segments, candidates only.  Every segment
  * must be prepared with FS_PREC_F32 on this context; lengths and transform
- * sizes may differ.  Bins are nfft/2 per segment (bins up to Nyquist).
+ * sizes may differ.  Bins are nfft/2 per segment (bins up to Nyquist), or the
+ * nfft half-bin frequencies of an interbinning segment (FS_OPT_INTERBIN).
  * cand_dev: [nseg][cand_cap] candidates, segment s at cand_dev + s cand_cap;
  * n_cand_dev: [nseg] device int64 counts, overwritten (semantics of
  * fs_search per segment).  The segments run longest transform first on two

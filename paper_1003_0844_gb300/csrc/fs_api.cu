@@ -295,7 +295,6 @@ fs_status fs_search_batch(fs_ctx *ctx, fs_seg *const *segs, int32_t nseg, const 
   if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
   for (int i = 0; i < nseg; i++) {
     if (!segs[i] || segs[i]->ctx != ctx || segs[i]->d.precision != FS_PREC_F32) return FS_ERR_ARG;
-    if (segs[i]->d.options & FS_OPT_INTERBIN) return FS_ERR_UNSUPPORTED;
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
   return search32_batch(ctx, segs, nseg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, cand_dev, cand_cap,

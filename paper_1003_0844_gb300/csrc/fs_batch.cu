@@ -83,9 +83,14 @@ fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const doubl
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return FS_ERR_ARG;
 
+  // the F row length of each segment: the band's bins, or the half-bin grid of an
+  // interbinning segment (candidate bins are indices on that row)
+  auto seg_nbins = [](const fs_seg *sg) {
+    return (sg->d.options & FS_OPT_INTERBIN) ? sg->g.nfft : sg->g.nfft / 2;
+  };
   std::vector<Cfg32> cfg(nseg);
   for (int i = 0; i < nseg; i++) {
-    fs_status s = config32(ctx, segs[i], nsky, segs[i]->g.nfft / 2, &cfg[i]);
+    fs_status s = config32(ctx, segs[i], nsky, seg_nbins(segs[i]), &cfg[i]);
     if (s != FS_OK) return s;
   }
   // longest transforms first, each onto the branch with less work so far
@@ -128,7 +133,7 @@ fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const doubl
     Ws32 w;
     r = workspace32(ctx, 1 + branch[i], segs[i], cfg[i], nsky, nspin, false, sb, &w);
     if (r == FS_OK)
-      r = search32_run(ctx, segs[i], cfg[i], w, alpha, delta, nsky, f1, nspin, thr, nullptr, segs[i]->g.nfft / 2,
+      r = search32_run(ctx, segs[i], cfg[i], w, alpha, delta, nsky, f1, nspin, thr, nullptr, seg_nbins(segs[i]),
                        cand ? cand + (int64_t)i * cap : nullptr, cap, ncand + i, sb);
   }
   if (r == FS_OK && (cudaEventRecord(ctx->join[1], s1) != cudaSuccess || cudaStreamWaitEvent(s0, ctx->join[1], 0) != cudaSuccess))

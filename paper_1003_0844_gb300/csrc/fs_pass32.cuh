@@ -43,7 +43,7 @@ __device__ __forceinline__ int fdiv(int n, const FastDiv &f) {
 struct Pass1Args {
   const float2 *ya, *yb, *qq;
   int64_t sky_stride;
-  const double *f1;
+  const float2 *f1df;  // spindowns as double-floats (hi, lo), converted once per search
   int nspin, tmpl0;
   FastDiv nspin_fd;  // division by nspin
   int N2, n1max;
@@ -56,7 +56,7 @@ struct Pass1Args {
   int vshift;
   float inv_nfft_total;  // 1 / Nfft
   float2 *Z;  // [batch][2][N1][N2]
-  // lattice templates (LAT items): f1 and the bin offset d per template of the group
+  // lattice templates (LAT items): f1df and the bin offset d per template of the group
   // (index sky * nspin + spin); the chirp gains exp(-2 pi i d j / Nfft)
   const double *bin_offset;
 };
@@ -92,7 +92,8 @@ __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, i
   const int n2 = tile * CW + col;
   const float2 *y = (sig ? A.yb : A.ya) + sky * A.sky_stride;
   const float2 *qq = A.qq + sky * A.sky_stride;
-  const df32 f1 = df_from_double(A.f1[LAT ? tr : spin]);
+  const float2 f1v = A.f1df[LAT ? tr : spin];
+  const df32 f1{f1v.x, f1v.y};
   const float boff = LAT ? (float)A.bin_offset[tr] : 0.f;
   const int n1max = A.n1max;
   const int64_t N2 = N2T ? (int64_t)N2T : (int64_t)A.N2;
@@ -825,7 +826,8 @@ struct Ws32 {
   SkyConst32 *skyc;
   float2 *ya, *yb, *qq, *norm;
   double2 *ab2;
-  double *partial;
+  float2 *partial; // per-block sums of a^2, b^2 of the demodulation
+  float2 *f1df;    // spindowns (per template for lattice searches) as double-floats
   float2 *Z;
   float2 *X;       // interbinning: complex bins of a batch [B][2][nsub]
   unsigned *counters;

@@ -13,6 +13,21 @@
 
 namespace fs {
 
+// Spindowns as double-floats, once per search (the FP64 conversion in every
+// transform item would occupy the slow FP64 pipe).
+__global__ void k_f1_df32(const double *f1, int64_t n, float2 *out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const df32 d = df_from_double(f1[i]);
+    out[i] = make_float2(d.hi, d.lo);
+  }
+}
+
+static cudaError_t f1_to_df32(const double *f1, int64_t n, float2 *out, cudaStream_t st) {
+  k_f1_df32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f1, n, out);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ self-test of the bounded waits
 __device__ unsigned g_never_incremented = 0;  // nothing writes it
 
@@ -76,7 +91,7 @@ struct DemodArgs {
   const float *x32;           // data, nearest-neighbour path
   float2 *ya, *yb, *qq;       // [nsky][stride]
   int64_t stride, npad;
-  double *partial;            // [nsky][gridDim.x][2]
+  float2 *partial;            // [nsky][gridDim.x]: block sums of a^2, b^2
   double *tsrc;               // optional [n] (first sky only)
 };
 
@@ -185,33 +200,34 @@ __global__ void __launch_bounds__(256) k_demod32(DemodArgs A) {
     A.yb[s * A.stride + j] = ob;
     A.qq[s * A.stride + j] = oq;
   }
-  // deterministic block sums of a^2, b^2: FP32 within a warp (32 terms), FP64 beyond
+  // deterministic block sums of a^2, b^2 by pairwise trees in FP32 (relative error
+  // below 8 roundings of the 256 positive terms); the blocks are summed in FP64 by
+  // k_demod_finalize.  (FP64 here would cost half the kernel: its pipe runs at 1/64
+  // of the FP32 rate on this GPU.)
   for (int o = 16; o > 0; o >>= 1) {
     a2 += __shfl_down_sync(kFull, a2, o);
     b2 += __shfl_down_sync(kFull, b2, o);
   }
-  const double da = a2, db = b2;
-  __shared__ double wa[8], wb[8];
-  if ((threadIdx.x & 31) == 0) { wa[threadIdx.x >> 5] = da; wb[threadIdx.x >> 5] = db; }
+  __shared__ float wa[8], wb[8];
+  if ((threadIdx.x & 31) == 0) { wa[threadIdx.x >> 5] = a2; wb[threadIdx.x >> 5] = b2; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double sa = 0.0, sb = 0.0;
-    for (int w = 0; w < 8; w++) { sa += wa[w]; sb += wb[w]; }
-    double *p = A.partial + ((int64_t)s * gridDim.x + blockIdx.x) * 2;
-    p[0] = sa;
-    p[1] = sb;
+    const float sa = ((wa[0] + wa[1]) + (wa[2] + wa[3])) + ((wa[4] + wa[5]) + (wa[6] + wa[7]));
+    const float sb = ((wb[0] + wb[1]) + (wb[2] + wb[3])) + ((wb[4] + wb[5]) + (wb[6] + wb[7]));
+    A.partial[(int64_t)s * gridDim.x + blockIdx.x] = make_float2(sa, sb);
   }
 }
 
 // <a^2>, <b^2> over the n output samples and the per-sky F normalisation
 // (cF / <a^2>, cF / <b^2>) with cF = 2 dt^2 / (S0 To) = 2 dt / (S0 n).
-__global__ void k_demod_finalize(const double *partial, int nb, int64_t n, double dt, double S0, float2 *norm,
+__global__ void k_demod_finalize(const float2 *partial, int nb, int64_t n, double dt, double S0, float2 *norm,
                                  double2 *ab2) {
   const int s = blockIdx.x;
   double sa = 0.0, sb = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    sa += partial[((int64_t)s * nb + i) * 2];
-    sb += partial[((int64_t)s * nb + i) * 2 + 1];
+    const float2 v = partial[(int64_t)s * nb + i];
+    sa += v.x;
+    sb += v.y;
   }
   __shared__ double ra[256], rb[256];
   ra[threadIdx.x] = sa;
@@ -346,7 +362,8 @@ fs_status workspace32(fs_ctx *ctx, int slot, const fs_seg *seg, const Cfg32 &c, 
   size_t o_qq = off; off = align256(off + sizeof(float2) * stride * G);
   size_t o_nm = off; off = align256(off + sizeof(float2) * G);
   size_t o_ab = off; off = align256(off + sizeof(double2) * G);
-  size_t o_pa = off; off = align256(off + sizeof(double) * 2 * (size_t)nblk * G);
+  size_t o_pa = off; off = align256(off + sizeof(float2) * (size_t)nblk * G);
+  size_t o_f1 = off; off = align256(off + sizeof(float2) * (size_t)nsky * nspin);
   size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)c.nsub * c.B);
   const size_t xn = !c.interbin ? 0
                     : c.persistent ? vt * (size_t)ib_edge_stride(c.sh.N1, c.sh.N2, kPersistThreads)
@@ -366,7 +383,8 @@ fs_status workspace32(fs_ctx *ctx, int slot, const fs_seg *seg, const Cfg32 &c, 
   w->qq = (float2 *)(base + o_qq);
   w->norm = (float2 *)(base + o_nm);
   w->ab2 = (double2 *)(base + o_ab);
-  w->partial = (double *)(base + o_pa);
+  w->partial = (float2 *)(base + o_pa);
+  w->f1df = (float2 *)(base + o_f1);
   w->Z = (float2 *)(base + o_z);
   w->X = c.interbin ? (float2 *)(base + o_x) : nullptr;
   w->counters = (unsigned *)(base + o_ct);
@@ -422,7 +440,8 @@ static void pass_args(const fs_seg *seg, const Cfg32 &c, const Ws32 &w, const do
   p1->yb = w.yb;
   p1->qq = w.qq;
   p1->sky_stride = w.stride;
-  p1->f1 = f1;
+  (void)f1;
+  p1->f1df = w.f1df;
   p1->nspin = nspin;
   p1->nspin_fd = make_fastdiv((uint32_t)nspin);
   p1->N2 = c.sh.N2;
@@ -464,6 +483,8 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
   Pass2Args p2;
   pass_args(seg, c, w, f1, nspin, thr, cand, cap, ncand, ctx->d_flags, &p1, &p2);
   p2.nbins = nbins;
+  if (f1_to_df32(f1, lat_offset ? (int64_t)nsky * nspin : nspin, w.f1df, st) != cudaSuccess) return FS_ERR_CUDA;
+  ctx->launches += 1;
   for (int g0 = 0; g0 < nsky; g0 += c.G) {
     const int gs = (nsky - g0) < c.G ? (nsky - g0) : c.G;
     DA.sky = w.skyc + g0;
@@ -479,7 +500,7 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
     const int ntm = (gs * nspin) << c.vshift;  // virtual templates of the group
     p2.sky_base = g0;
     if (lat_offset) {  // the group's rows of per-template spindowns and bin offsets
-      p1.f1 = f1 + (int64_t)g0 * nspin;
+      p1.f1df = w.f1df + (int64_t)g0 * nspin;
       p1.bin_offset = lat_offset + (int64_t)g0 * nspin;
     }
     p2.F = F ? F + (int64_t)g0 * nspin * nbins : nullptr;
@@ -646,7 +667,8 @@ fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
   const size_t o_qq = off; off = align256(off + sizeof(float2) * stride);
   const size_t o_nm = off; off = align256(off + sizeof(float2));
   const size_t o_ab = off; off = align256(off + sizeof(double2));
-  const size_t o_pa = off; off = align256(off + sizeof(double) * 2 * (size_t)nblk);
+  const size_t o_pa = off; off = align256(off + sizeof(float2) * (size_t)nblk);
+  const size_t o_f1 = off; off = align256(off + sizeof(float2) * (size_t)nspin);
   const size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)seg->g.nfft * slots);
   const size_t o_ct = off; off = align256(off + sizeof(unsigned) * (1 + 2 * (size_t)nspin));
   if (off > (size_t)FS_NOALLOC_SCRATCH_BYTES) return FS_ERR_SCRATCH;
@@ -660,12 +682,15 @@ fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
   w.qq = (float2 *)(base + o_qq);
   w.norm = (float2 *)(base + o_nm);
   w.ab2 = (double2 *)(base + o_ab);
-  w.partial = (double *)(base + o_pa);
+  w.partial = (float2 *)(base + o_pa);
+  w.f1df = (float2 *)(base + o_f1);
   w.Z = (float2 *)(base + o_z);
   w.counters = (unsigned *)(base + o_ct);
   w.stride = stride;
   w.nblk_a1 = nblk;
   if (cudaMemsetAsync(ncand, 0, sizeof(int64_t), st) != cudaSuccess) return FS_ERR_CUDA;
+  if (f1_to_df32(f1, nspin, w.f1df, st) != cudaSuccess) return FS_ERR_CUDA;
+  ctx->launches += 1;
   DemodArgs DA = demod_args(seg, w, npad);
   for (int g0 = 0; g0 < nsky; g0++) {
     if (sky_constants32(alpha + g0, delta + g0, 1, seg->g, ctx->det, w.skyc, st) != cudaSuccess) return FS_ERR_CUDA;

@@ -432,7 +432,7 @@ static cudaError_t launch_demod(const DemodArgs &A, int nsky, int nblk, int inte
   return cudaGetLastError();
 }
 
-static void pass_args(const fs_seg *seg, const Cfg32 &c, const Ws32 &w, const double *f1, int nspin, float thr,
+static void pass_args(const fs_seg *seg, const Cfg32 &c, const Ws32 &w, int nspin, float thr,
                       fs_candidate *cand, int64_t cap, int64_t *ncand, uint32_t *flags, Pass1Args *p1,
                       Pass2Args *p2) {
   *p1 = Pass1Args{};
@@ -440,8 +440,7 @@ static void pass_args(const fs_seg *seg, const Cfg32 &c, const Ws32 &w, const do
   p1->yb = w.yb;
   p1->qq = w.qq;
   p1->sky_stride = w.stride;
-  (void)f1;
-  p1->f1df = w.f1df;
+  p1->f1df = w.f1df;  // filled by f1_to_df32 before the launches
   p1->nspin = nspin;
   p1->nspin_fd = make_fastdiv((uint32_t)nspin);
   p1->N2 = c.sh.N2;
@@ -481,7 +480,7 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
   }
   Pass1Args p1;
   Pass2Args p2;
-  pass_args(seg, c, w, f1, nspin, thr, cand, cap, ncand, ctx->d_flags, &p1, &p2);
+  pass_args(seg, c, w, nspin, thr, cand, cap, ncand, ctx->d_flags, &p1, &p2);
   p2.nbins = nbins;
   if (f1_to_df32(f1, lat_offset ? (int64_t)nsky * nspin : nspin, w.f1df, st) != cudaSuccess) return FS_ERR_CUDA;
   ctx->launches += 1;
@@ -704,7 +703,7 @@ fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
     c.npad = npad;
     Pass1Args p1;
     Pass2Args p2;
-    pass_args(seg, c, w, f1, nspin, thr, cand, cap, ncand, ctx->d_flags, &p1, &p2);
+    pass_args(seg, c, w, nspin, thr, cand, cap, ncand, ctx->d_flags, &p1, &p2);
     p2.sky_base = g0;
     p2.F = F ? F + (int64_t)g0 * nspin * nbins : nullptr;
     p2.nbins = nbins;

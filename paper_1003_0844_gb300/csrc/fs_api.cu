@@ -96,6 +96,7 @@ static void seg_release(fs_seg *s) {
   cudaFree(s->coef);
   cudaFree(s->blu_bhat);
   cudaFree(s->blu_tw);
+  cudaFree(s->blu_chirp);
   cudaFree(s->etab64);
   cudaFree(s->eph);
   cudaFree(s->eph0);

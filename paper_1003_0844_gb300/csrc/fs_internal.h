@@ -71,6 +71,7 @@ struct fs_seg {
   // FFT of the chirp b and the FFT twiddles; built by the first load
   int64_t blu_m = 0;
   double2 *blu_bhat = nullptr, *blu_tw = nullptr;
+  double2 *blu_chirp = nullptr;  // [2N]: chirp exp(-i pi m^2/N), then the half-sample shift
   // FP64 (cos, sin) of the orbital and sidereal angles on t_k = k dt, built by
   // the first fine-search call
   void *etab64 = nullptr;

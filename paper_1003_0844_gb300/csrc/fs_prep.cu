@@ -119,16 +119,33 @@ __global__ void k_bluestein_b(double2 *b, int64_t N, int64_t M) {
   b[i] = v;
 }
 
+// Per-segment tables of the upsampler (they depend on N only): the chirp
+// exp(-i pi m^2/N) and the half-sample shift exp(i pi k'/N) (k' the signed
+// frequency of bin k; zero at the Nyquist bin of even N), m, k < N.
+__global__ void k_bluestein_tables(double2 *chirp, double2 *shift, int64_t N) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  chirp[k] = bluestein_chirp(k, N, -1);
+  if ((N % 2 == 0) && k == N / 2) {
+    shift[k] = make_double2(0.0, 0.0);
+  } else {
+    const int64_t kp = (2 * k < N) ? k : k - N;  // signed frequency
+    double sn, cs;
+    sincospi((double)kp / (double)N, &sn, &cs);
+    shift[k] = make_double2(cs, sn);
+  }
+}
+
 // a[n] = in[n] * exp(-i pi n^2/N) for n < N (in real or complex, optionally conjugated), 0 beyond.
 __global__ void k_bluestein_a(double2 *a, const double *in_real, const double2 *in_cplx, int conj_in,
-                              int64_t N, int64_t M) {
+                              const double2 *chirp, int64_t N, int64_t M) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= M) return;
   double2 v = make_double2(0.0, 0.0);
   if (i < N) {
     double2 u = in_cplx ? in_cplx[i] : make_double2(in_real[i], 0.0);
     if (conj_in) u.y = -u.y;
-    v = cmul(u, bluestein_chirp(i, N, -1));
+    v = cmul(u, chirp[i]);
   }
   a[i] = v;
 }
@@ -138,25 +155,22 @@ __global__ void k_pointwise_mul(double2 *a, const double2 *b, int64_t M) {
   if (i < M) a[i] = cmul(a[i], b[i]);
 }
 
-// out[k] = exp(-i pi k^2/N) conv[k] / M   (k < N)
-__global__ void k_bluestein_out(double2 *out, const double2 *conv, int64_t N, int64_t M) {
+// out[k] = exp(-i pi k^2/N) conv[k] / M   (k < N; M a power of two: exact scaling)
+__global__ void k_bluestein_out(double2 *out, const double2 *conv, const double2 *chirp, int64_t N, int64_t M) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= N) return;
+  const double inv = 1.0 / (double)M;
   double2 v = conv[k];
-  v.x /= (double)M;
-  v.y /= (double)M;
-  out[k] = cmul(v, bluestein_chirp(k, N, -1));
+  v.x *= inv;
+  v.y *= inv;
+  out[k] = cmul(v, chirp[k]);
 }
 
-// Z_k = X_k exp(i pi k'/N), Nyquist bin of even N zeroed.
-__global__ void k_halfshift(double2 *Z, const double2 *X, int64_t N) {
+// Z_k = X_k exp(i pi k'/N), Nyquist bin of even N zeroed (the shift table).
+__global__ void k_halfshift(double2 *Z, const double2 *X, const double2 *shift, int64_t N) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= N) return;
-  if ((N % 2 == 0) && k == N / 2) { Z[k] = make_double2(0.0, 0.0); return; }
-  int64_t kp = (2 * k < N) ? k : k - N;  // signed frequency
-  double s, c;
-  sincospi((double)kp / (double)N, &s, &c);
-  Z[k] = cmul(X[k], make_double2(c, s));
+  Z[k] = cmul(X[k], shift[k]);
 }
 
 // x2[2m] = x[m]; x2[2m+1] = Re(IDFT_N(Z))[m] = Re(conj(DFT_N(conj Z)))[m] / N
@@ -171,15 +185,15 @@ static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t -
 
 // DFT of length N of `in` (real or complex, optionally conjugated) into out, by Bluestein.
 static cudaError_t bluestein_dft(double2 *out, const double *in_real, const double2 *in_cplx, int conj_in,
-                                 int64_t N, int64_t M, const double2 *Bhat, double2 *a, double2 *tmp,
-                                 const double2 *tw, cudaStream_t st, int64_t *launches) {
-  k_bluestein_a<<<nblk(M), 256, 0, st>>>(a, in_real, in_cplx, conj_in, N, M);
+                                 int64_t N, int64_t M, const double2 *Bhat, const double2 *chirp, double2 *a,
+                                 double2 *tmp, const double2 *tw, cudaStream_t st, int64_t *launches) {
+  k_bluestein_a<<<nblk(M), 256, 0, st>>>(a, in_real, in_cplx, conj_in, chirp, N, M);
   cudaError_t e = fft64(a, tmp, tw, M, 1, -1, st, launches);
   if (e != cudaSuccess) return e;
   k_pointwise_mul<<<nblk(M), 256, 0, st>>>(a, Bhat, M);
   e = fft64(a, tmp, tw, M, 1, +1, st, launches);
   if (e != cudaSuccess) return e;
-  k_bluestein_out<<<nblk(N), 256, 0, st>>>(out, a, N, M);
+  k_bluestein_out<<<nblk(N), 256, 0, st>>>(out, a, chirp, N, M);
   *launches += 3;
   return cudaGetLastError();
 }
@@ -189,18 +203,22 @@ fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st) {
   int64_t M = 1;
   while (M < 2 * N - 1) M <<= 1;
   int64_t *L = &seg->ctx->launches;
-  // plan (once per segment): chirp spectrum Bhat = FFT_M(b) and the FFT twiddles
+  // plan (once per segment): chirp spectrum Bhat = FFT_M(b), the FFT twiddles, and the
+  // chirp and half-shift tables of length N
   if (seg->blu_m != M) {
     cudaFree(seg->blu_bhat);
     cudaFree(seg->blu_tw);
-    seg->blu_bhat = seg->blu_tw = nullptr;
+    cudaFree(seg->blu_chirp);
+    seg->blu_bhat = seg->blu_tw = seg->blu_chirp = nullptr;
     seg->blu_m = 0;
     if (cudaMalloc(&seg->blu_bhat, sizeof(double2) * M) != cudaSuccess ||
-        cudaMalloc(&seg->blu_tw, sizeof(double2) * (M / 2)) != cudaSuccess) {
+        cudaMalloc(&seg->blu_tw, sizeof(double2) * (M / 2)) != cudaSuccess ||
+        cudaMalloc(&seg->blu_chirp, sizeof(double2) * 2 * N) != cudaSuccess) {
       cudaGetLastError();
       return FS_ERR_NOMEM;
     }
   }
+  double2 *chirp = seg->blu_chirp, *shift = seg->blu_chirp + N;
   // scratch: a, tmp, X (M each)
   size_t need = sizeof(double2) * 3 * (size_t)M;
   fs_status s = ensure_buffer(&seg->ctx->scratch, &seg->ctx->scratch_bytes, need, st);
@@ -213,7 +231,8 @@ fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st) {
     e = fft64_twiddles(tw, M, st);
     if (e != cudaSuccess) return FS_ERR_CUDA;
     k_bluestein_b<<<nblk(M), 256, 0, st>>>(Bhat, N, M);
-    *L += 2;
+    k_bluestein_tables<<<nblk(N), 256, 0, st>>>(chirp, shift, N);
+    *L += 3;
     e = fft64(Bhat, tmp, tw, M, 1, -1, st, L);
     if (e != cudaSuccess) return FS_ERR_CUDA;
     seg->blu_m = M;
@@ -225,13 +244,13 @@ fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st) {
     k_load_x<double><<<nblk(N), 256, 0, st>>>((const double *)x_dev, seg->x64, seg->x32, N, seg->ctx->d_flags);
   *L += 1;
   // X = DFT_N(x)
-  e = bluestein_dft(X, seg->x64, nullptr, 0, N, M, Bhat, a, tmp, tw, st, L);
+  e = bluestein_dft(X, seg->x64, nullptr, 0, N, M, Bhat, chirp, a, tmp, tw, st, L);
   if (e != cudaSuccess) return FS_ERR_CUDA;
   // Z = half-sample shift; odd samples = Re IDFT_N(Z) = Re conj(DFT_N(conj Z)) / N
-  k_halfshift<<<nblk(N), 256, 0, st>>>(X, X, N);
+  k_halfshift<<<nblk(N), 256, 0, st>>>(X, X, shift, N);
   *L += 1;
   // the result overwrites X: the transform reads its whole input before writing
-  e = bluestein_dft(X, nullptr, X, 1, N, M, Bhat, a, tmp, tw, st, L);
+  e = bluestein_dft(X, nullptr, X, 1, N, M, Bhat, chirp, a, tmp, tw, st, L);
   if (e != cudaSuccess) return FS_ERR_CUDA;
   k_interleave<<<nblk(N), 256, 0, st>>>(seg->x2, seg->x64, X, N);
   *L += 1;

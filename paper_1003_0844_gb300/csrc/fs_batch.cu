@@ -222,7 +222,8 @@ fs_status autotune32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double
   if (cudaMalloc(&dcount, sizeof(int64_t)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)
     r = FS_ERR_CUDA;
-  const int64_t nbins = seg->g.nfft / 2;
+  // the segment's own F row: the band's bins, or the half-bin grid with interbinning
+  const int64_t nbins = (seg->d.options & FS_OPT_INTERBIN) ? seg->g.nfft : seg->g.nfft / 2;
   fs_tuning best{};
   float best_ms = FLT_MAX;
   for (size_t c = 0; c < cands.size() && r == FS_OK; c++) {

@@ -246,6 +246,23 @@ def test_autotune_picks_a_valid_split(fs):
     assert not missing and not bad
 
 
+def test_autotune_interbinning_segment(fs):
+    """The tuner times an interbinning segment on its own half-bin row and keeps a
+    split whose search still matches the oracle."""
+    from oracle import fstat as ofs_
+    wl, det, x, alpha, delta, f1 = make_case("small", nfft=1 << 15, nsky=2, nspin=2)
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0, interbin=True)
+    t = ctx.autotune(seg, _dev(alpha), _dev(delta), _dev(f1), reps=1)
+    assert t["n1"] in (64, 128, 256, 512) and t["ms_per_template"] > 0
+    res = fs.search(ctx, seg, _dev(alpha), _dev(delta), _dev(f1), wl.F_thr)
+    assert ctx.sync_status() == 0
+    so = ors.Segment(x, wl.dt)
+    ref = np.stack([ofs_.fstat_interbinned(so, a, d, s1, wl.fl, det, wl.S0, wl.nfft)
+                    for a, d in zip(alpha, delta) for s1 in f1])
+    assert max_rel_dF(res.F.double().cpu().numpy(), ref) <= F32_TOL
+
+
 # ------------------------------------------------------------------ interbinning
 
 @pytest.mark.parametrize("name,n,nfft,precision", [("small", None, 1 << 14, "f32"), ("small", None, 1 << 14, "f64"),

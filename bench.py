@@ -39,6 +39,18 @@ METRICS = {
     "grid_2d_ib": "F-stat templates/s (N=86,164, 2^17 FFT + interbinning) on 1 GB300; max rel dF vs FP64",
     "refine_2d": "fine-search candidates/s (20 Newton steps on the exact F, N=86,164) on 1 GB300",
 }
+
+
+def metric_name(workload: str) -> str:
+    """The metric string of a named workload (test-size workloads get a descriptive one)."""
+    if workload in METRICS:
+        return METRICS[workload]
+    if workload in W.BATCHES:
+        return "F-stat templates/s (%s batch of segments) on 1 GB300" % workload
+    wl = W.WORKLOADS[workload]
+    return "F-stat templates/s (N=%d, 2^%d FFT, %s) on 1 GB300" % (wl.n, wl.nfft.bit_length() - 1, workload)
+
+
 FP64_PEAK_TFLOPS = 1.25          # nominal FP64 rate of a GB300 (no measured figure)
 REFINE_FLOP_PER_SAMPLE = 685.0   # FP64 flops per sample and point of the Hessian pass, from ncu's
                                  # DFMA/DMUL/DADD counts (profiles/k_points_refine_2d.md)
@@ -216,7 +228,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import earth as oe, refine as orf, response as orsp
-    metric, unit = METRICS.get(args.workload, METRIC), "templates/s"
+    metric, unit = metric_name(args.workload), "templates/s"
     if args.workload in W.BATCHES:
         b = W.BATCHES[args.workload]
         det = W.detector_for(b)
@@ -233,7 +245,7 @@ def run_reference(args):
 
         def sample():
             return sum(cpu_oracle_rate(x, wl, dk, a_all[:1], d_all[:1], f1[:1], 1)[2] for x, wl, dk in data)
-        nsub = args.nsky or 64
+        nsub = min(args.nsky or 64, b.nsky)
         config = {"workload": args.workload, "segments": len(b.segments()),
                   "segment_kinds": [list(p) for p in b.parts], "dt": b.dt, "nsky": nsub, "nsky_lattice": b.nsky,
                   "nspin": b.nspin, "templates_per_gpu": len(b.segments()) * nsub * b.nspin, "F_thr": b.F_thr,
@@ -316,7 +328,7 @@ def main_batch(args):
         x32 = x64.float().contiguous()
         xs.append(x32)
         segs.append(fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0, t0=float(t0)))
-    nsky_sub = args.nsky or 64   # sky subset of the batch's lattice (templates/s is per template)
+    nsky_sub = min(args.nsky or 64, b.nsky)   # sky subset of the batch's lattice (templates/s is per template)
     a_all, d_all = W.sky_grid(b.nsky)
     mine = shard.sky_shard(nsky_sub, rank, world)
     alpha = torch.as_tensor(np.ascontiguousarray(a_all[mine]), device="cuda")
@@ -371,7 +383,7 @@ def main_batch(args):
     achieved = flops / (ms_per_step / 1e3) / 1e12
     hbm_gbs, hbm_kind = _peaks()
     line = {
-        "metric": METRICS[args.workload], "value": value, "unit": "templates/s", "n_gpus": world,
+        "metric": metric_name(args.workload), "value": value, "unit": "templates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64/double-float phases)", "data": "synthetic",
         "config": {"workload": args.workload, "segments": nseg,
@@ -682,17 +694,32 @@ def main():
     hbm_gbs, hbm_kind = _peaks()
     # whole-path HBM view: algorithmic bytes = F written (4 B per bin) per template
     hbm_alg = ntempl * nbins * 4 / (ms_per_step / 1e3) / 1e9
+    dram = bound = None
+    if roof is not None and roof.get("traffic"):
+        # achieved DRAM rate of the transform kernel (ncu bytes per launch over the event-timed
+        # launch), and the model bound that binds: HBM on the design's bytes per template
+        # (measured traffic) or the FP32 ALU on the algorithmic flops
+        dram_gbs = roof["traffic"] / (roof["per_launch_ms"] / 1e3) / 1e9
+        dram = {"kernel": roof["kernel"], "achieved_gbs": dram_gbs, "peak_gbs": hbm_gbs, "frac": dram_gbs / hbm_gbs,
+                "peak_kind": hbm_kind, "source": "ncu dram bytes per launch / event-timed launch duration"}
+        per_tpl = roof["traffic"] / roof["templates_per_launch"]
+        hbm_tps = hbm_gbs * 1e9 / per_tpl
+        alu_tps = FP32_PEAK_TFLOPS * 1e12 / flops_tmpl[dom]
+        bound = {"hbm_templates_per_s": hbm_tps, "alu_templates_per_s": alu_tps,
+                 "binding": "hbm" if hbm_tps < alu_tps else "alu", "frac": value / min(hbm_tps, alu_tps),
+                 "note": "HBM bound on the measured bytes per template, ALU bound on 5 Nfft log2 Nfft x 2 flops"}
     shares = {names[k]: round(v[0] / max(sum(x[0] for x in kinds.values()), 1e-9), 4)
               for k, v in kinds.items() if v[1]}
 
     line = {
-        "metric": METRICS.get(args.workload, METRIC), "value": value, "unit": "templates/s", "n_gpus": world,
+        "metric": metric_name(args.workload), "value": value, "unit": "templates/s", "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (FP64/double-float phases)", "data": "synthetic",
         "config": _grid_config(wl, nsky, nspin, world),
         "roofline": roof,
         "hbm_alg_gbs": hbm_alg, "hbm_peak_gbs": hbm_gbs, "hbm_peak_kind": hbm_kind,
+        "dram": dram, "model_bound": bound,
         "kernel_ms_share": shares,
         "gpu_launches": int(stats["launches"]),
         "clocks": ck,

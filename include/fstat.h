@@ -394,7 +394,8 @@ FS_API fs_status fs_lattice_templates(const double *basis_host, const fs_detecto
  * exp(-2 pi i d j / nfft) before the transform, Eq. eq:DFT at a shifted
  * frequency); a candidate's bin k means that frequency.  Device arrays of
  * nsky * nspin doubles, offsets in [0, 1).  FP32 segments without
- * interbinning, nbins = nfft/2, nfft <= 2^20 (else FS_ERR_UNSUPPORTED). */
+ * interbinning, nbins = nfft/2, nfft <= 2^21 (2^21 as two 2^20 sub-transforms on
+ * the default 1024 x 1024 split; else FS_ERR_UNSUPPORTED). */
 FS_API fs_status fs_search_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const double *delta_dev,
                                    int32_t nsky, const double *f1_dev, const double *offset_dev, int32_t nspin,
                                    float F_thr, float *F_out_dev, int64_t nbins, fs_candidate *cand_dev,

@@ -562,8 +562,10 @@ fs_status search32_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
   Cfg32 c;
   fs_status s = config32(ctx, seg, nsky, nbins, &c);
   if (s != FS_OK) return s;
-  if (c.interbin || c.vshift || c.full || !c.persistent || !passes_lat_instantiated(c.sh.N1, c.sh.N2))
+  if (c.interbin || c.full || !c.persistent || !passes_lat_instantiated(c.sh.N1, c.sh.N2))
     return FS_ERR_UNSUPPORTED;
+  // 2^21: sub-transforms on the 1024 x 1024 split only
+  if (c.vshift && (c.vshift != 1 || c.sh.N1 != 1024 || c.sh.N2 != 1024)) return FS_ERR_UNSUPPORTED;
   Ws32 w;
   s = workspace32(ctx, 0, seg, c, nsky, nspin, true, st, &w);
   if (s != FS_OK) return s;

@@ -2,7 +2,9 @@
 bin of every template (per-sky spindown rows, bins shifted by the lines' offsets)
 against the oracle, the plain product grid reproduced bit for bit with zero offsets,
 and an injection inside the searched patch recovered within the lattice's mismatch,
-at a node whose exact F confirms the reported frequency."""
+at a node whose exact F confirms the reported frequency; the same on the 2^21
+transform (two 2^20 sub-transforms per template)."""
+import dataclasses
 import math
 
 import numpy as np
@@ -104,4 +106,45 @@ def test_lattice_search_finds_an_injection_in_the_patch(fs):
     node = np.array([[(k + off[s, m]) / (wl.nfft * wl.dt), f1[s, m], a[s], d[s]]])
     F_node = float(fs.fstat_points(ctx, seg, _dev(node), grad=False)[0].cpu()[0])
     assert F_node == pytest.approx(F.max(), rel=0.03)
+    ctx.close()
+
+
+@pytest.mark.parametrize("n,dt", [(300000, 2.0), (1033968, 0.5)])
+def test_lattice_search_2p21_matches_oracle(fs, n, dt):
+    """nfft = 2^21, both data lengths (at most half of a 2^20 sub-transform, and nearly
+    all of it): the first nodes of the lattice lines of a small patch against the
+    oracle on every bin; zero offsets and a shared spindown row give the plain 2^21
+    search bit for bit."""
+    nfft = 1 << 21
+    wl = dataclasses.replace(W.WORKLOADS["wide_6d"], dt=dt)
+    det = W.detector_for(wl)
+    G = og.linear_model_fisher(n, dt, det)
+    B, _, _ = og.constrained_lattice(G, 0.75, 2 * math.pi / (nfft * dt))
+    a, d, f1, off = fs.lattice_templates(B, det, wl.fl, nfft, dt, F1R, (0.30, 0.32, -0.10, -0.08))
+    assert a.size >= 1 and f1.shape[1] >= 3
+    a, d = a[:2].copy(), d[:2].copy()
+    f1, off = f1[:2, :3].copy(), off[:2, :3].copy()
+    injs = [W.Injection(f0=0.1 + 0.37 / (n * dt), f1=float(f1[0, 1]), alpha=float(a[0]), delta=float(d[0]),
+                        psi=0.4, cos_iota=0.5, phi0=0.2, snr=20.0)]
+    x = (W.noise(wl)[:n] + orsp.inject(n, dt, injs, wl.fl, det, wl.sigma)).astype(np.float32)
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), dt, nfft, wl.fl, wl.S0)
+    res = fs.search_lattice(ctx, seg, _dev(a), _dev(d), _dev(f1), _dev(off), wl.F_thr)
+    assert ctx.sync_status() == 0
+    F = res.F.double().cpu().numpy()
+    assert F.shape == (f1.size, nfft // 2)
+    so = ors.Segment(x.astype(np.float64), dt)
+    ns, nm = f1.shape
+    ref = np.stack([ofs.fstat(so, a[s], d[s], f1[s, m], wl.fl, det, wl.S0, nfft, bin_offset=off[s, m])
+                    for s in range(ns) for m in range(nm)])
+    assert max_rel_dF(F, ref) <= F32_TOL
+    assert ref.max() > 100
+    missing, bad = check_candidates(*res.candidates(), ref, wl.F_thr, nm)
+    assert not missing and not bad
+    f1s = f1[0]
+    r0 = fs.search_lattice(ctx, seg, _dev(a), _dev(d), _dev(np.tile(f1s, (ns, 1))), _dev(np.zeros((ns, nm))),
+                           wl.F_thr)
+    r1 = fs.search(ctx, seg, _dev(a), _dev(d), _dev(f1s), wl.F_thr)
+    assert torch.equal(r0.F, r1.F)
+    seg.close()
     ctx.close()

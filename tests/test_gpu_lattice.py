@@ -126,7 +126,8 @@ def test_lattice_search_2p21_matches_oracle(fs, n, dt):
     f1, off = f1[:2, :3].copy(), off[:2, :3].copy()
     injs = [W.Injection(f0=0.1 + 0.37 / (n * dt), f1=float(f1[0, 1]), alpha=float(a[0]), delta=float(d[0]),
                         psi=0.4, cos_iota=0.5, phi0=0.2, snr=20.0)]
-    x = (W.noise(wl)[:n] + orsp.inject(n, dt, injs, wl.fl, det, wl.sigma)).astype(np.float32)
+    x = (np.random.default_rng(5).standard_normal(n) * wl.sigma
+         + orsp.inject(n, dt, injs, wl.fl, det, wl.sigma)).astype(np.float32)
     ctx = fs.Context(det)
     seg = fs.Segment(ctx, _dev(x, torch.float32), dt, nfft, wl.fl, wl.S0)
     res = fs.search_lattice(ctx, seg, _dev(a), _dev(d), _dev(f1), _dev(off), wl.F_thr)

@@ -38,7 +38,14 @@ METRICS = {
     "uneven_64": "F-stat templates/s (64 segments of 1/2/3/6 days, 2^16-2^20 FFT) on 1 GB300",
     "grid_2d_ib": "F-stat templates/s (N=86,164, 2^17 FFT + interbinning) on 1 GB300; max rel dF vs FP64",
     "refine_2d": "fine-search candidates/s (20 Newton steps on the exact F, N=86,164) on 1 GB300",
+    "lattice_2d": "F-stat templates/s (N=86,164, 2^18 FFT, constrained A4* lattice of a sky patch) on 1 GB300",
 }
+
+# the constrained-lattice workload: the 2-day data of grid_2d, the A4* lattice of
+# minimal match 0.75 built by the library (Sec. IV) over this patch of ecliptic
+# (n_x, n_y) near the ecliptic pole, spindowns in the grid's range
+LATTICE_BOX = (0.30, 0.45, -0.10, 0.05)
+LATTICE_MATCH = 0.75
 
 
 def metric_name(workload: str) -> str:
@@ -219,6 +226,15 @@ def _grid_config(wl, nsky, nspin, world):
             "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky shards x%d" % world}
 
 
+def _lattice_config(wl, nsky, nspin, world):
+    """config of the constrained-lattice workload (both arms)."""
+    return {"workload": "lattice_2d", "n": wl.n, "nfft": wl.nfft, "nsky": nsky, "nspin": nspin,
+            "templates_per_gpu": nsky * nspin // world, "nbins": wl.nbins, "F_thr": wl.F_thr, "F_written": True,
+            "lattice": "constrained A4*, minimal match %.2f, sky patch n_x in [%.2f, %.2f], n_y in [%.2f, %.2f]"
+                       % ((LATTICE_MATCH,) + LATTICE_BOX),
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky rows dealt over %d ranks" % world}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands, on the host cores, each step a
     bounded sample of the workload (grid workloads: segment preparation plus a few
@@ -252,6 +268,25 @@ def run_reference(args):
                   "F_written": False, "l2": "flushed between timed steps (256 MiB write)",
                   "parallelism": "sky shards x%d" % args.gpus, "graph": "one CUDA graph per batch, two branches"}
         what = "one template of each of the %d segment kinds with its preparation" % len(data)
+        per_unit = 1.0
+    elif args.workload == "lattice_2d":
+        from oracle import fstat as ofs, grid as og, resample as ors
+        wl = W.WORKLOADS["grid_2d"]
+        det = W.detector_for(wl)
+        x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float64)
+        G = og.linear_model_fisher(wl.n, wl.dt, det)
+        B, _, _ = og.constrained_lattice(G, LATTICE_MATCH, 2 * math.pi / (wl.nfft * wl.dt))
+        T = og.lattice_templates(B, det, wl.fl, wl.nfft, wl.dt, *wl.f1_range, box=LATTICE_BOX)
+        tm = [(al, de, fr, dr) for al, de, rows in T for fr, dr, _ in rows]
+        per_step = 16
+
+        def sample():
+            so = ors.Segment(x.astype(np.float32).astype(np.float64), wl.dt)
+            for al, de, fr, dr in tm[:per_step]:
+                ofs.fstat(so, al, de, fr, wl.fl, det, wl.S0, wl.nfft, bin_offset=dr)
+            return per_step
+        config = _lattice_config(wl, len(T), max(len(r) for _, _, r in T), args.gpus)
+        what = "segment preparation + %d lattice templates (FFT mode)" % per_step
         per_unit = 1.0
     elif args.workload == "refine_2d":
         wl = W.WORKLOADS["grid_2d"]
@@ -579,6 +614,159 @@ def main_refine(args):
         dist.destroy_process_group()
 
 
+def main_lattice(args):
+    """The constrained A4* lattice of a sky patch on the 2-day data (Sec. IV): per sky
+    node a row of spindown nodes, each line one transform whose bins are shifted by its
+    fraction of a bin (fs_search_lattice), F written for every bin.  The templates come
+    from the library's host functions (linear-model Fisher matrix, lattice, nodes);
+    with several ranks the patch's sky rows are dealt out (strong scaling)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1003_0844_gb300 import build, fstat as fs, shard
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    wl = W.WORKLOADS["grid_2d"]
+    det = W.detector_for(wl)
+    ctx = fs.Context(det, device=local)
+    x64 = torch.as_tensor(W.noise(wl), device="cuda")
+    fs.inject(ctx, x64, wl.dt, wl.fl, wl.sigma, W.injections(wl))
+    x32 = x64.float().contiguous()
+    G = fs.linear_model_fisher(det, wl.n, wl.dt)
+    B, _ = fs.lattice(G, LATTICE_MATCH, 2 * math.pi / (wl.nfft * wl.dt))
+    a, d, f1, off = fs.lattice_templates(B, det, wl.fl, wl.nfft, wl.dt, wl.f1_range, LATTICE_BOX)
+    rows = np.arange(rank, a.size, world)
+    if args.nsky:
+        rows = rows[:args.nsky]
+
+    def dev(v):
+        return torch.as_tensor(np.ascontiguousarray(v), device="cuda")
+    alpha, delta, f1d, offd = dev(a[rows]), dev(d[rows]), dev(f1[rows]), dev(off[rows])
+    nsky, nspin, nbins = rows.size, f1.shape[1], wl.nbins
+    ntempl = nsky * nspin
+    seg = fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0)
+    F_out = torch.empty((ntempl, nbins), dtype=torch.float32, device="cuda")
+    cap = 1 << 16
+    cand = torch.empty((cap, 4), dtype=torch.int32, device="cuda")
+    ncand = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+
+    def step():
+        seg.load(x32)
+        fs.search_lattice(ctx, seg, alpha, delta, f1d, offd, wl.F_thr, F_out=F_out, cand=cand, n_cand=ncand,
+                          cand_cap=cap)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    ctx.check()
+    ctx.stats(reset=True)
+    ctx.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flushed between timed steps (outside the events)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    stats = ctx.stats(reset=True)
+    ctx.set_profiling(False)
+    ctx.check()
+    total_ms = shard.max_over_ranks(total_ms, device="cuda")
+    ms_per_step = total_ms / args.steps
+    templates_all = a.size * nspin if not args.nsky else ntempl * world
+    value = templates_all / (ms_per_step / 1e3)
+    # the transform kernel (one persistent launch per sky group) against the FP32 ALU
+    # peak on 5 Nfft log2 Nfft flops per complex transform, two transforms per template
+    p = int(round(math.log2(wl.nfft)))
+    kinds = {k: (stats["ms"][k], stats["count"][k]) for k in ("prepare", "demodulate", "pass1", "pass2")}
+    roof = None
+    dom_ms, dom_n = kinds["pass2"]
+    if dom_n and kinds["pass1"][1] == 0:
+        per_launch_ms = dom_ms / dom_n
+        tpl = ntempl * args.steps / dom_n
+        achieved = 2 * 5 * wl.nfft * p * tpl / (per_launch_ms / 1e3) / 1e12
+        tpt, tnote = _profile_traffic("k_passes_lattice_2d.md")
+        roof = {"kernel": "k_passes (lattice items, persistent)", "bound": "alu", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": (tpt * tpl if tpt is not None else None), "traffic_unit": "bytes per launch",
+                "traffic_note": tnote,
+                "peak_kind": "FP32 CUDA-core peak from unit counts and max clock (152 SM x 128 x 2 x 2070 MHz)",
+                "flop_convention": "5 Nfft log2 Nfft per complex FFT, 2 FFTs per template",
+                "per_launch_ms": per_launch_ms, "templates_per_launch": tpl}
+    total_k = max(sum(v[0] for v in kinds.values()), 1e-9)
+    line = {
+        "metric": METRICS["lattice_2d"], "value": value, "unit": "templates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+        "dtype": "f32 (FP64/double-float phases)", "data": "synthetic",
+        "config": _lattice_config(wl, a.size, nspin, world),
+        "roofline": roof,
+        "hbm_alg_gbs": ntempl * nbins * 4 / (ms_per_step / 1e3) / 1e9,
+        "kernel_ms_share": {k: round(v[0] / total_k, 4) for k, v in kinds.items() if v[1]},
+        "gpu_launches": int(stats["launches"]),
+        "clocks": ck,
+        "e2e": None, "cpu_baseline": None,
+    }
+    if rank == 0 and not args.quick:
+        from oracle import fstat as ofs, resample as ors
+        xh = x32.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        so = ors.Segment(xh, wl.dt)
+        done = 0
+        for s_ in range(nsky):
+            for m_ in range(nspin):
+                if done < args.cpu_templates:
+                    ofs.fstat(so, a[rows[s_]], d[rows[s_]], f1[rows[s_], m_], wl.fl, det, wl.S0, wl.nfft,
+                              bin_offset=off[rows[s_], m_])
+                    done += 1
+        secs = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / secs, "unit": "templates/s", "cores": 1, "kind": "oracle",
+                                "sample": "segment preparation + %d lattice templates (FFT mode), %.1f s"
+                                          % (done, secs)}
+        # end to end through the public API with host buffers, as for the grid workloads
+        xh_pin = torch.empty(wl.n, dtype=torch.float32).pin_memory()
+        xh_pin.copy_(x32.cpu())
+        cand_h = torch.empty((cap, 4), dtype=torch.int32).pin_memory()
+        nc_h = torch.empty(1, dtype=torch.int64).pin_memory()
+        xd = torch.empty_like(x32)
+        ke = max(5, args.steps // 5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            xd.copy_(xh_pin, non_blocking=True)
+            seg.load(xd)
+            fs.search_lattice(ctx, seg, alpha, delta, f1d, offd, wl.F_thr, F_out=F_out, cand=cand, n_cand=ncand,
+                              cand_cap=cap)
+            nc_h.copy_(ncand, non_blocking=True)
+            cand_h.copy_(cand, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / ke
+        line["e2e"] = {"value": ntempl * world / e2e_s, "unit": "templates/s", "h2d_bytes_per_step": wl.n * 4,
+                       "d2h_bytes_per_step": cap * 16 + 8}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    seg.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -587,6 +775,8 @@ def main():
         return main_batch(args)
     if args.workload == "refine_2d":
         return main_refine(args)
+    if args.workload == "lattice_2d":
+        return main_lattice(args)
     import torch
     import torch.distributed as dist
     from paper_1003_0844_gb300 import build, fstat as fs, shard

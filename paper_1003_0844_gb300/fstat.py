@@ -533,9 +533,11 @@ def lattice_templates(basis, det, fl: float, nfft: int, dt: float, f1_range, box
 
 def search_lattice(ctx: Context, seg: Segment, alpha: torch.Tensor, delta: torch.Tensor, f1: torch.Tensor,
                    offset: torch.Tensor, F_thr: float, write_F: bool = True, cand_cap: int = 1 << 16,
-                   stream=None) -> SearchResult:
+                   F_out: torch.Tensor | None = None, cand: torch.Tensor | None = None,
+                   n_cand: torch.Tensor | None = None, stream=None) -> SearchResult:
     """fs_search_lattice: sky s and row m have spindown f1[s, m] and F at the bins
-    k + offset[s, m] (device float64 [nsky, nspin] each); returns device tensors."""
+    k + offset[s, m] (device float64 [nsky, nspin] each); returns device tensors
+    (F_out, cand, n_cand are allocated unless given, as for search)."""
     for t, nm in ((alpha, "alpha"), (delta, "delta"), (f1, "f1"), (offset, "offset")):
         _need_cuda(t, nm, torch.float64)
     nsky = alpha.numel()
@@ -543,9 +545,14 @@ def search_lattice(ctx: Context, seg: Segment, alpha: torch.Tensor, delta: torch
         raise ValueError("alpha, delta [nsky] and f1, offset [nsky, nspin] expected")
     nspin = f1.shape[1]
     nb = seg.nfft // 2
-    F_out = torch.empty((nsky * nspin, nb), dtype=torch.float32, device="cuda") if write_F else None
-    cand = torch.empty((max(cand_cap, 1), 4), dtype=torch.int32, device="cuda")
-    n_cand = torch.zeros(1, dtype=torch.int64, device="cuda")
+    if write_F and F_out is None:
+        F_out = torch.empty((nsky * nspin, nb), dtype=torch.float32, device="cuda")
+    if not write_F:
+        F_out = None
+    if cand is None:
+        cand = torch.empty((max(cand_cap, 1), 4), dtype=torch.int32, device="cuda")
+    if n_cand is None:
+        n_cand = torch.zeros(1, dtype=torch.int64, device="cuda")
     st = ctx.lib.fs_search_lattice(ctx.handle, seg.handle, _ptr(alpha), _ptr(delta), nsky, _ptr(f1), _ptr(offset),
                                    nspin, float(F_thr), _ptr(F_out) if F_out is not None else None, nb, _ptr(cand),
                                    int(cand.shape[0]) if cand_cap > 0 else 0, _ptr(n_cand), _stream(stream))

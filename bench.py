@@ -715,7 +715,7 @@ def main_lattice(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
         "dtype": "f32 (FP64/double-float phases)", "data": "synthetic",
-        "config": _lattice_config(wl, a.size, nspin, world),
+        "config": _lattice_config(wl, nsky * world if args.nsky else a.size, nspin, world),
         "roofline": roof,
         "hbm_alg_gbs": ntempl * nbins * 4 / (ms_per_step / 1e3) / 1e9,
         "kernel_ms_share": {k: round(v[0] / total_k, 4) for k, v in kinds.items() if v[1]},

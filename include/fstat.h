@@ -56,7 +56,7 @@ typedef enum {
   FS_ERR_NONFINITE = 4,   /* NaN or Inf in the data series                   */
   FS_ERR_CUDA = 5,        /* a CUDA runtime call failed                      */
   FS_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out              */
-  FS_ERR_UNSUPPORTED = 7, /* valid request this build does not implement     */
+  FS_ERR_UNSUPPORTED = 7, /* valid request the library does not implement    */
   FS_ERR_NOMEM = 8,       /* device allocation failed                        */
   FS_ERR_SCRATCH = 9      /* request needs more than FS_NOALLOC_SCRATCH_BYTES */
 } fs_status;
@@ -251,7 +251,7 @@ typedef struct {
   int32_t reserved;
 } fs_tuning;
 /* Set (t non-NULL) or clear (t NULL) the configuration for nfft.
- * FS_ERR_ARG for a split this build does not provide. */
+ * FS_ERR_ARG for a split the library does not provide. */
 FS_API fs_status fs_set_tuning(fs_ctx *ctx, int64_t nfft, const fs_tuning *t_host);
 /* Current configuration for nfft; FS_ERR_UNSUPPORTED when none is set. */
 FS_API fs_status fs_get_tuning(fs_ctx *ctx, int64_t nfft, fs_tuning *out_host);

@@ -784,7 +784,7 @@ inline int64_t ib_edge_stride(int N1, int N2, int NT) {
   return (int64_t)(N1 / R) * 4 * (N2 / 2) + 2;
 }
 // Persistent launch for an N1 x N2 split; cudaErrorInvalidValue for a split
-// this build does not instantiate (split_instantiated is false).
+// the library does not instantiate (split_instantiated is false).
 cudaError_t dispatch_passes(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,
                             cudaStream_t st);
 cudaError_t dispatch_passes_small(int N1, int N2, const Pass1Args &a1, const Pass2Args &a2, const QueueArgs &qa,

@@ -254,7 +254,7 @@ static int log2_exact(int64_t v) {
 // Default split of a sub-transform of length 2^p: N1 = 2^ceil(p/2), N2 = 2^floor(p/2).
 static FftShape default_split(int p) { return FftShape{1 << ((p + 1) / 2), 1 << (p / 2)}; }
 
-// Transform splits N1 x N2 this build instantiates for the persistent kernel.
+// Transform splits N1 x N2 the library instantiates for the persistent kernel.
 static const int kSplits[][2] = {
     {64, 64},    {128, 64},  {128, 128},  {256, 64},   {256, 128}, {256, 256},  {512, 128},
     {128, 512},  {512, 256}, {256, 512},  {1024, 128}, {512, 512}, {1024, 256}, {256, 1024},

@@ -88,7 +88,7 @@ enum { FS_X_F32 = 0, FS_X_F64 = 1 };
  * of a transform padded to 2 nfft at the cost of one of length nfft.  Searches
  * of such a segment take nbins = nfft (the F row length) and report candidate
  * bins j on that grid (also in fs_search_batch); FP32 segments need
- * nfft <= 2^20; fs_search_noalloc does not take them (FS_ERR_UNSUPPORTED). */
+ * nfft <= 2^20; the allocation-free searches do not take them (FS_ERR_UNSUPPORTED). */
 enum { FS_OPT_INTERBIN = 1 };
 
 /* One data segment: x_k = x(k dt), k < n, t = 0 at the first sample.
@@ -400,6 +400,14 @@ FS_API fs_status fs_search_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha
                                    int32_t nsky, const double *f1_dev, const double *offset_dev, int32_t nspin,
                                    float F_thr, float *F_out_dev, int64_t nbins, fs_candidate *cand_dev,
                                    int64_t cand_cap, int64_t *n_cand_dev, void *stream);
+/* fs_search_lattice from the fixed array of fs_search_noalloc, allocating
+ * nothing: same arguments and results as fs_search_lattice, one sky row per
+ * launch; the limits and FS_ERR_SCRATCH of fs_search_noalloc apply. */
+FS_API fs_status fs_search_lattice_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev,
+                                           const double *delta_dev, int32_t nsky, const double *f1_dev,
+                                           const double *offset_dev, int32_t nspin, float F_thr,
+                                           float *F_out_dev, int64_t nbins, fs_candidate *cand_dev,
+                                           int64_t cand_cap, int64_t *n_cand_dev, void *stream);
 
 /* Synchronise `stream` and return (and clear) the first device-side error
  * latched since the last call, or FS_OK. */

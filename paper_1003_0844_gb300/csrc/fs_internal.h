@@ -125,7 +125,7 @@ fs_status search32_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
                            fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st);
 fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
                            const double *f1, int nspin, float thr, float *F, int64_t nbins, fs_candidate *cand,
-                           int64_t cap, int64_t *ncand, cudaStream_t st);
+                           int64_t cap, int64_t *ncand, cudaStream_t st, const double *offset = nullptr);
 fs_status demod32_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, double *ya, double *yb,
                         double *tsrc, double *ab2, cudaStream_t st);
 fs_status demod64_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, double *ya, double *yb,

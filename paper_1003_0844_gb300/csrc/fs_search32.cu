@@ -646,14 +646,16 @@ static fs_status noalloc_scratch(unsigned char **out) {
   return FS_OK;
 }
 
+// offset non-NULL: lattice templates (f1 and offset [nsky][nspin]), one sky row per launch
 fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
                            const double *f1, int nspin, float thr, float *F, int64_t nbins, fs_candidate *cand,
-                           int64_t cap, int64_t *ncand, cudaStream_t st) {
+                           int64_t cap, int64_t *ncand, cudaStream_t st, const double *offset) {
   if (seg->d.precision != FS_PREC_F32 || nbins != seg->g.nfft / 2) return FS_ERR_UNSUPPORTED;
   int vshift = 0, ps = 0;
   if (!sub_transform(seg->g.nfft, &vshift, &ps) || seg->g.n > seg->g.nfft) return FS_ERR_SHAPE;
   if (vshift) return FS_ERR_SCRATCH;  // a 2^21 transform ring alone exceeds the array
   const FftShape sh = default_split(ps);
+  if (offset && !passes_lat_instantiated(sh.N1, sh.N2)) return FS_ERR_UNSUPPORTED;
   const int64_t n = seg->g.n;
   const int n1max = (int)((n + sh.N2 - 1) / sh.N2);
   const int64_t npad = (int64_t)n1max * sh.N2;
@@ -690,10 +692,16 @@ fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
   w.stride = stride;
   w.nblk_a1 = nblk;
   if (cudaMemsetAsync(ncand, 0, sizeof(int64_t), st) != cudaSuccess) return FS_ERR_CUDA;
-  if (f1_to_df32(f1, nspin, w.f1df, st) != cudaSuccess) return FS_ERR_CUDA;
-  ctx->launches += 1;
+  if (!offset) {
+    if (f1_to_df32(f1, nspin, w.f1df, st) != cudaSuccess) return FS_ERR_CUDA;
+    ctx->launches += 1;
+  }
   DemodArgs DA = demod_args(seg, w, npad);
   for (int g0 = 0; g0 < nsky; g0++) {
+    if (offset) {  // this sky's row of spindowns
+      if (f1_to_df32(f1 + (int64_t)g0 * nspin, nspin, w.f1df, st) != cudaSuccess) return FS_ERR_CUDA;
+      ctx->launches += 1;
+    }
     if (sky_constants32(alpha + g0, delta + g0, 1, seg->g, ctx->det, w.skyc, st) != cudaSuccess) return FS_ERR_CUDA;
     if (launch_demod(DA, 1, nblk, seg->d.interp, st) != cudaSuccess) return FS_ERR_CUDA;
     k_demod_finalize<<<1, 256, 0, st>>>(w.partial, nblk, n, seg->g.dt, seg->g.S0, w.norm, w.ab2);
@@ -721,7 +729,12 @@ fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
     // the array keeps the previous call's contents: the queue counters start at zero
     if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)nspin), st) != cudaSuccess)
       return FS_ERR_CUDA;
-    if (dispatch_passes(sh.N1, sh.N2, p1, p2, qa, st) != cudaSuccess) return FS_ERR_CUDA;
+    if (offset) {
+      p1.bin_offset = offset + (int64_t)g0 * nspin;
+      if (dispatch_passes_lat(sh.N1, sh.N2, p1, p2, qa, st) != cudaSuccess) return FS_ERR_CUDA;
+    } else if (dispatch_passes(sh.N1, sh.N2, p1, p2, qa, st) != cudaSuccess) {
+      return FS_ERR_CUDA;
+    }
     ctx->launches += 4;
   }
   return FS_OK;

@@ -28,7 +28,8 @@ EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_prepare_segment_
            "fs_get_stats", "fs_search_noalloc", "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune",
            "fs_fstat_points", "fs_refine", "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm_cell",
            "fs_false_alarm", "fs_threshold", "fs_cell_count", "fs_linear_model_fisher", "fs_lattice",
-           "fs_lattice_nodes", "fs_lattice_templates", "fs_search_lattice", "fs_selftest_wait"]
+           "fs_lattice_nodes", "fs_lattice_templates", "fs_search_lattice", "fs_search_lattice_noalloc",
+           "fs_selftest_wait"]
 PROF_KINDS = ("prepare", "demodulate", "pass1", "pass2", "other")
 
 
@@ -114,13 +115,14 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.fs_lattice_templates.argtypes = [ctypes.POINTER(f64), ctypes.POINTER(_Detector), f64, i64, f64, f64, f64,
                                          vp, vp, vp, vp, vp, i64, i32, ctypes.POINTER(i64), ctypes.POINTER(i32)]
     lib.fs_search_lattice.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, f32, vp, i64, vp, i64, vp, vp]
+    lib.fs_search_lattice_noalloc.argtypes = [vp, vp, vp, vp, i32, vp, vp, i32, f32, vp, i64, vp, i64, vp, vp]
     lib.fs_selftest_wait.argtypes = [vp, vp]
     for name in ("fs_create", "fs_prepare_segment", "fs_prepare_segment_eph", "fs_seg_load", "fs_search", "fs_search_noalloc", "fs_sync_status",
                  "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling", "fs_get_stats",
                  "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune", "fs_fstat_points", "fs_refine",
                  "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm", "fs_threshold", "fs_cell_count",
                  "fs_linear_model_fisher", "fs_lattice", "fs_lattice_nodes", "fs_lattice_templates",
-                 "fs_search_lattice", "fs_selftest_wait"):
+                 "fs_search_lattice", "fs_search_lattice_noalloc", "fs_selftest_wait"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

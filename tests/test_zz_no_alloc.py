@@ -8,7 +8,8 @@ library holds per device.  This test calls it through the C ABI twice in a row
 (the array keeps the previous call's contents, so the second call checks that
 everything that must start from zero is cleared) and compares F and the
 candidates with fs_search on the same inputs, within the FP32 parity tolerance.
-It also checks that a request larger than the fixed array is refused.
+It also checks that a request larger than the fixed array is refused, and the
+lattice search's allocation-free form against fs_search_lattice.
 """
 import ctypes
 
@@ -70,6 +71,51 @@ def test_noalloc_search_matches_search_on_two_calls_in_a_row():
         n = int(ncand.item())
         assert n == n_ref
         assert _cand_set(cand, n) == want
+
+
+def test_noalloc_lattice_search_matches_lattice_search():
+    """fs_search_lattice_noalloc (per-template spindowns and bin offsets, one sky row
+    per launch) against fs_search_lattice on the same inputs, twice in a row."""
+    import math
+    from oracle import grid as og
+    from paper_1003_0844_gb300 import build, fstat as fs
+    build.build()
+    lib = fs.load_library()
+    wl, det, x, _, _, _ = make_case("small")
+    G = og.linear_model_fisher(wl.n, wl.dt, det)
+    B, _, _ = og.constrained_lattice(G, 0.75, 2 * math.pi / (wl.nfft * wl.dt))
+    al, de, f1, off = fs.lattice_templates(B, det, wl.fl, wl.nfft, wl.dt, (-2e-9, 0.0), (0.30, 0.45, -0.10, 0.05))
+    thr = 12.0
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0)
+    a, d, f, o = _dev(al), _dev(de), _dev(f1), _dev(off)
+    ref = fs.search_lattice(ctx, seg, a, d, f, o, thr)
+    assert ctx.sync_status() == 0
+    n_ref = int(ref.n_cand.item())
+    want = _cand_set(ref.cand, n_ref)
+    nsky, nspin = f1.shape
+    nbins = wl.nfft // 2
+    cap = 1 << 16
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for call in range(2):
+        F = torch.full((nsky * nspin, nbins), float("nan"), dtype=torch.float32, device="cuda")
+        cand = torch.zeros((cap, 4), dtype=torch.int32, device="cuda")
+        ncand = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+        st = lib.fs_search_lattice_noalloc(ctx.handle, seg.handle, ctypes.c_void_p(a.data_ptr()),
+                                           ctypes.c_void_p(d.data_ptr()), nsky, ctypes.c_void_p(f.data_ptr()),
+                                           ctypes.c_void_p(o.data_ptr()), nspin, ctypes.c_float(thr),
+                                           ctypes.c_void_p(F.data_ptr()), ctypes.c_int64(nbins),
+                                           ctypes.c_void_p(cand.data_ptr()), ctypes.c_int64(cap),
+                                           ctypes.c_void_p(ncand.data_ptr()), stream)
+        assert st == 0, "call %d returned %d" % (call, st)
+        assert ctx.sync_status() == 0
+        got = F.double().cpu().numpy()
+        assert max_rel_dF(got, ref.F.double().cpu().numpy()) < F32_TOL
+        n = int(ncand.item())
+        assert n == n_ref
+        assert _cand_set(cand, n) == want
+    seg.close()
+    ctx.close()
 
 
 def test_noalloc_search_refuses_requests_larger_than_its_array():

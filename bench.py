@@ -724,6 +724,23 @@ def main_lattice(args):
         "e2e": None, "cpu_baseline": None,
     }
     if rank == 0 and not args.quick:
+        # the plain FP64 form of the lattice search on a sample of sky rows, and the FP32 error against it
+        nsk = min(args.fp64_skies, nsky)
+        seg64 = fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0, precision="f64")
+        sub = (alpha[:nsk].contiguous(), delta[:nsk].contiguous(), f1d[:nsk].contiguous(), offd[:nsk].contiguous())
+        fs.search_lattice(ctx, seg64, *sub, wl.F_thr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r64 = fs.search_lattice(ctx, seg64, *sub, wl.F_thr)
+        e1.record()
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        F32 = F_out[: nsk * nspin].double()
+        line["fp64_form"] = {"value": nsk * nspin / t64, "unit": "templates/s", "templates": nsk * nspin,
+                             "note": "plain all-FP64 lattice search (own FP64 Stockham FFT), search only"}
+        line["max_rel_dF_vs_fp64"] = float(((F32 - r64.F).abs() / torch.clamp(r64.F, min=1.0)).max().item())
+        seg64.close()
         from oracle import fstat as ofs, resample as ors
         xh = x32.cpu().numpy().astype(np.float64)
         t0 = time.perf_counter()

@@ -393,16 +393,18 @@ FS_API fs_status fs_lattice_templates(const double *basis_host, const fs_detecto
  * (k + offset_dev[s * nspin + m]) / (nfft dt) above fl (the data times
  * exp(-2 pi i d j / nfft) before the transform, Eq. eq:DFT at a shifted
  * frequency); a candidate's bin k means that frequency.  Device arrays of
- * nsky * nspin doubles, offsets in [0, 1).  FP32 segments without
- * interbinning, nbins = nfft/2, nfft <= 2^21 (2^21 as two 2^20 sub-transforms on
- * the default 1024 x 1024 split; else FS_ERR_UNSUPPORTED). */
+ * nsky * nspin doubles, offsets in [0, 1); F_out_dev holds float for
+ * FS_PREC_F32 segments, double for FS_PREC_F64.  Segments without interbinning,
+ * nbins = nfft/2; FP32 segments take nfft <= 2^21 (2^21 as two 2^20
+ * sub-transforms on the default 1024 x 1024 split); else FS_ERR_UNSUPPORTED. */
 FS_API fs_status fs_search_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const double *delta_dev,
                                    int32_t nsky, const double *f1_dev, const double *offset_dev, int32_t nspin,
-                                   float F_thr, float *F_out_dev, int64_t nbins, fs_candidate *cand_dev,
+                                   float F_thr, void *F_out_dev, int64_t nbins, fs_candidate *cand_dev,
                                    int64_t cand_cap, int64_t *n_cand_dev, void *stream);
 /* fs_search_lattice from the fixed array of fs_search_noalloc, allocating
- * nothing: same arguments and results as fs_search_lattice, one sky row per
- * launch; the limits and FS_ERR_SCRATCH of fs_search_noalloc apply. */
+ * nothing: same arguments and results as fs_search_lattice for FP32 segments,
+ * one sky row per launch; the limits and FS_ERR_SCRATCH of fs_search_noalloc
+ * apply. */
 FS_API fs_status fs_search_lattice_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev,
                                            const double *delta_dev, int32_t nsky, const double *f1_dev,
                                            const double *offset_dev, int32_t nspin, float F_thr,

@@ -261,17 +261,19 @@ fs_status fs_selftest_wait(fs_ctx *ctx, void *stream) {
 
 fs_status fs_search_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const double *delta_dev,
                             int32_t nsky, const double *f1_dev, const double *offset_dev, int32_t nspin, float F_thr,
-                            float *F_out_dev, int64_t nbins, fs_candidate *cand_dev, int64_t cand_cap,
+                            void *F_out_dev, int64_t nbins, fs_candidate *cand_dev, int64_t cand_cap,
                             int64_t *n_cand_dev, void *stream) {
   if (!ctx || !seg || !alpha_dev || !delta_dev || !f1_dev || !offset_dev || !n_cand_dev) return FS_ERR_ARG;
   if (seg->ctx != ctx) return FS_ERR_ARG;
   if (nsky < 1 || nspin < 1 || cand_cap < 0 || (cand_cap > 0 && !cand_dev)) return FS_ERR_ARG;
   if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
-  if (seg->d.precision != FS_PREC_F32 || (seg->d.options & FS_OPT_INTERBIN) || nbins != seg->g.nfft / 2)
-    return FS_ERR_UNSUPPORTED;
+  if ((seg->d.options & FS_OPT_INTERBIN) || nbins != seg->g.nfft / 2) return FS_ERR_UNSUPPORTED;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
-  return search32_lattice(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, offset_dev, nspin, F_thr, F_out_dev, nbins,
-                          cand_dev, cand_cap, n_cand_dev, as_stream(stream));
+  if (seg->d.precision == FS_PREC_F64)
+    return search64(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, (double *)F_out_dev, nbins,
+                    cand_dev, cand_cap, n_cand_dev, as_stream(stream), offset_dev);
+  return search32_lattice(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, offset_dev, nspin, F_thr,
+                          (float *)F_out_dev, nbins, cand_dev, cand_cap, n_cand_dev, as_stream(stream));
 }
 
 fs_status fs_search_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const double *delta_dev,

@@ -116,7 +116,8 @@ fs_status search32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
                    fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st);
 fs_status search64(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
                    const double *f1, int nspin, float thr, double *F, int64_t nbins,
-                   fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st);
+                   fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st,
+                   const double *offset = nullptr);
 // One bounded wait on a counter nothing increments (fs_selftest_wait).
 cudaError_t selftest_wait(uint32_t *flags, cudaStream_t st);
 // Coarse search of lattice templates (fs_search_lattice): f1 and the bin offset per template.

@@ -88,9 +88,11 @@ __global__ void k_finalize64(const double *partial, int nb, int64_t n, double dt
   }
 }
 
-// buf[(m*2 + sig)][k] = y^sig_k exp(-2 pi i f1_m Q_k) for k < n, 0 up to nfft
-__global__ void k_modulate64(const double2 *ya, const double2 *yb, const double *qq, const double *f1, int nspin,
-                             int64_t n, int64_t nfft, double2 *buf) {
+// buf[(m*2 + sig)][k] = y^sig_k exp(-2 pi i f1_m Q_k) for k < n, 0 up to nfft; with
+// lattice templates (offset non-NULL) also exp(-2 pi i d_m k / nfft), which moves bin
+// j of the transform to the frequency (j + d_m) / (nfft dt)
+__global__ void k_modulate64(const double2 *ya, const double2 *yb, const double *qq, const double *f1,
+                             const double *offset, int nspin, int64_t n, int64_t nfft, double2 *buf) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (k >= nfft || m >= nspin) return;
@@ -98,6 +100,10 @@ __global__ void k_modulate64(const double2 *ya, const double2 *yb, const double 
   if (k < n) {
     double cyc = f1[m] * qq[k];
     cyc -= floor(cyc);
+    if (offset) {
+      cyc += offset[m] * ((double)k / (double)nfft);
+      cyc -= floor(cyc);
+    }
     double sp, cp;
     sincospi(2.0 * cyc, &sp, &cp);
     const double2 c = make_double2(cp, -sp);
@@ -194,9 +200,10 @@ static fs_status workspace64(fs_ctx *ctx, const fs_seg *seg, int nspin, cudaStre
   return FS_OK;
 }
 
+// offset non-NULL: lattice templates, f1 and offset [nsky][nspin] (row sk for sky sk)
 fs_status search64(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
                    const double *f1, int nspin, float thr, double *F, int64_t nbins, fs_candidate *cand,
-                   int64_t cap, int64_t *ncand, cudaStream_t st) {
+                   int64_t cap, int64_t *ncand, cudaStream_t st, const double *offset) {
   const int64_t n = seg->g.n, nfft = seg->g.nfft;
   Ws64 w;
   fs_status s = workspace64(ctx, seg, nspin, st, &w);
@@ -211,7 +218,9 @@ fs_status search64(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *
                                                 seg->eph);
     k_finalize64<<<1, 256, 0, st>>>(w.partial, w.nblk, n, seg->g.dt, seg->g.S0, w.norm, w.ab2);
     ctx->launches += 5;  // sky constants, demodulation, finalize, modulation, F epilogue
-    k_modulate64<<<dim3((unsigned)((nfft + 255) / 256), nspin), 256, 0, st>>>(w.ya, w.yb, w.qq, f1, nspin, n,
+    const double *f1s = offset ? f1 + (int64_t)sk * nspin : f1;
+    const double *ds = offset ? offset + (int64_t)sk * nspin : nullptr;
+    k_modulate64<<<dim3((unsigned)((nfft + 255) / 256), nspin), 256, 0, st>>>(w.ya, w.yb, w.qq, f1s, ds, nspin, n,
                                                                               nfft, w.buf);
     if (fft64(w.buf, w.tmp, w.tw, nfft, 2 * nspin, -1, st, &ctx->launches) != cudaSuccess) return FS_ERR_CUDA;
     k_fstat64<<<dim3((unsigned)((nbins + 255) / 256), nspin), 256, 0, st>>>(

@@ -548,7 +548,8 @@ def search_lattice(ctx: Context, seg: Segment, alpha: torch.Tensor, delta: torch
     nspin = f1.shape[1]
     nb = seg.nfft // 2
     if write_F and F_out is None:
-        F_out = torch.empty((nsky * nspin, nb), dtype=torch.float32, device="cuda")
+        fdt = torch.float32 if seg.precision == "f32" else torch.float64
+        F_out = torch.empty((nsky * nspin, nb), dtype=fdt, device="cuda")
     if not write_F:
         F_out = None
     if cand is None:

@@ -2,8 +2,9 @@
 bin of every template (per-sky spindown rows, bins shifted by the lines' offsets)
 against the oracle, the plain product grid reproduced bit for bit with zero offsets,
 and an injection inside the searched patch recovered within the lattice's mismatch,
-at a node whose exact F confirms the reported frequency; the same on the 2^21
-transform (two 2^20 sub-transforms per template)."""
+at a node whose exact F confirms the reported frequency; the plain FP64 form of the
+lattice search; the same on the 2^21 transform (two 2^20 sub-transforms per
+template)."""
 import dataclasses
 import math
 
@@ -16,7 +17,7 @@ from oracle import grid as og
 from oracle import resample as ors
 from oracle import response as orsp
 from paper_1003_0844_gb300 import workloads as W
-from tests.helpers import F32_TOL, check_candidates, max_rel_dF
+from tests.helpers import F32_TOL, F64_TOL, check_candidates, max_rel_dF
 
 pytestmark = pytest.mark.gpu
 
@@ -67,6 +68,15 @@ def test_lattice_search_matches_oracle(fs):
     r0 = fs.search_lattice(ctx, seg, _dev(a), _dev(d), _dev(np.tile(f1s, (ns, 1))), _dev(np.zeros((ns, nm))), thr)
     r1 = fs.search(ctx, seg, _dev(a), _dev(d), _dev(f1s), thr)
     assert torch.equal(r0.F, r1.F)
+    # the plain FP64 form of the same lattice search
+    seg64 = fs.Segment(ctx, _dev(x.astype(np.float64)), wl.dt, wl.nfft, wl.fl, wl.S0, precision="f64")
+    r64 = fs.search_lattice(ctx, seg64, _dev(a), _dev(d), _dev(f1), _dev(off), thr)
+    assert ctx.sync_status() == 0
+    assert r64.F.dtype == torch.float64
+    assert max_rel_dF(r64.F.cpu().numpy(), ref) <= F64_TOL
+    missing, bad = check_candidates(*r64.candidates(), ref, thr, nm)
+    assert not missing and not bad
+    seg64.close()
     # what the lattice search refuses
     with pytest.raises(fs.FstatError) as e:
         seg_ib = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0, interbin=True)

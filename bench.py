@@ -41,11 +41,10 @@ METRICS = {
     "lattice_2d": "F-stat templates/s (N=86,164, 2^18 FFT, constrained A4* lattice of a sky patch) on 1 GB300",
 }
 
-# the constrained-lattice workload: the 2-day data of grid_2d, the A4* lattice of
-# minimal match 0.75 built by the library (Sec. IV) over this patch of ecliptic
-# (n_x, n_y) near the ecliptic pole, spindowns in the grid's range
-LATTICE_BOX = (0.30, 0.45, -0.10, 0.05)
-LATTICE_MATCH = 0.75
+# the constrained-lattice workload: the 2-day data of grid_2d and the A4* lattice of a
+# sky patch (Sec. IV), built by the library's host functions
+LATTICE_BOX = W.LATTICE_BOX
+LATTICE_MATCH = W.LATTICE_MATCH
 
 
 def metric_name(workload: str) -> str:

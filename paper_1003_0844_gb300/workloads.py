@@ -94,6 +94,12 @@ WORKLOADS = {
                       n_inj=2, snr=(25.0, 40.0), f0_range=(0.005, 0.05), F_thr=15.0),
 }
 
+# The constrained-lattice workload on the 2-day data of "grid_2d": the A4* lattice of
+# minimal match LATTICE_MATCH (Sec. IV) over this patch of ecliptic (n_x, n_y) near
+# the ecliptic pole, spindowns in the grid's range.
+LATTICE_BOX = (0.30, 0.45, -0.10, 0.05)
+LATTICE_MATCH = 0.75
+
 
 @dataclasses.dataclass(frozen=True)
 class BatchWorkload:

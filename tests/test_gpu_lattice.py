@@ -159,3 +159,41 @@ def test_lattice_search_2p21_matches_oracle(fs, n, dt):
     assert torch.equal(r0.F, r1.F)
     seg.close()
     ctx.close()
+
+
+def test_lattice_workload_full_configuration_sampled(fs):
+    """The lattice benchmark's launch configuration (every sky row of the patch, every
+    spindown node, the library's own lattice, one search call as the benchmark makes
+    it): sampled template rows against the oracle and their candidates, and for all
+    templates the count of crossings equals the number of F values above threshold."""
+    wl = W.WORKLOADS["grid_2d"]
+    det = W.detector_for(wl)
+    x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float32)
+    G = fs.linear_model_fisher(det, wl.n, wl.dt)
+    B, _ = fs.lattice(G, W.LATTICE_MATCH, 2 * math.pi / (wl.nfft * wl.dt))
+    a, d, f1, off = fs.lattice_templates(B, det, wl.fl, wl.nfft, wl.dt, wl.f1_range, W.LATTICE_BOX)
+    ns, nm = f1.shape
+    assert ns * nm > 4096
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0)
+    res = fs.search_lattice(ctx, seg, _dev(a), _dev(d), _dev(f1), _dev(off), wl.F_thr, cand_cap=1 << 20)
+    assert ctx.sync_status() == 0
+    F = res.F
+    assert F.shape == (ns * nm, wl.nbins)
+    assert bool(torch.isfinite(F).all()) and float(F.min()) >= 0.0
+    assert int(res.n_cand.item()) == int((F > wl.F_thr).sum().item())
+    sky, spin, bins, Fc = res.candidates()
+    g = np.random.default_rng(7)
+    picks = sorted({0, ns * nm - 1, *g.integers(0, ns * nm, 4).tolist()})
+    so = ors.Segment(x.astype(np.float64), wl.dt)
+    for t in picks:
+        s, m = divmod(t, nm)
+        ref = ofs.fstat(so, a[s], d[s], f1[s, m], wl.fl, det, wl.S0, wl.nfft, bin_offset=off[s, m])
+        row = F[t].double().cpu().numpy()
+        assert max_rel_dF(row, ref) <= F32_TOL, (t, max_rel_dF(row, ref))
+        mine = (sky == s) & (spin == m)
+        missing, bad = check_candidates(np.zeros(mine.sum(), dtype=np.int64), np.zeros(mine.sum(), dtype=np.int64),
+                                        bins[mine], Fc[mine], ref[None, :], wl.F_thr, 1)
+        assert not missing and not bad, (t, missing, bad)
+    seg.close()
+    ctx.close()

@@ -52,6 +52,11 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.fs_create(None, None, 0) == 1
     assert lib.fs_search(None, None, None, None, 0, None, 0, ctypes.c_float(0), None, ctypes.c_int64(0), None,
                          ctypes.c_int64(0), None, None) == 1
+    assert lib.fs_search_noalloc(None, None, None, None, 0, None, 0, ctypes.c_float(0), None, ctypes.c_int64(0),
+                                 None, ctypes.c_int64(0), None, None) == 1
+    for name in ("fs_search_lattice", "fs_search_lattice_noalloc"):
+        assert getattr(lib, name)(None, None, None, None, 0, None, None, 0, ctypes.c_float(0), None,
+                                  ctypes.c_int64(0), None, ctypes.c_int64(0), None, None) == 1, name
 
 
 def test_product_path_does_not_import_oracle():

@@ -234,6 +234,20 @@ FS_API fs_status fs_search_batch(fs_ctx *ctx, fs_seg *const *segs_host, int32_t 
                                  const double *f1_dev, int32_t nspin, float F_thr,
                                  fs_candidate *cand_dev, int64_t cand_cap, int64_t *n_cand_dev,
                                  void *stream);
+/* fs_search_batch over lattice templates (Sec. IV; see fs_search_lattice), each
+ * segment with its own lattice: segment s searches nsky_host[s] sky nodes
+ * (alpha_dev[s], delta_dev[s]) with the rows f1_dev[s], offset_dev[s] of
+ * nsky_host[s] x nspin_host[s] doubles.  The five pointer arrays and the two
+ * count arrays are host arrays of nseg entries naming device arrays; candidates,
+ * counts, the CUDA graph and its replay as for fs_search_batch (the recorded
+ * graph is replayed when every pointer and count is the same).  FP32 segments
+ * without interbinning (else FS_ERR_UNSUPPORTED), nfft as fs_search_lattice. */
+FS_API fs_status fs_search_lattice_batch(fs_ctx *ctx, fs_seg *const *segs_host, int32_t nseg,
+                                         const double *const *alpha_dev, const double *const *delta_dev,
+                                         const int32_t *nsky_host, const double *const *f1_dev,
+                                         const double *const *offset_dev, const int32_t *nspin_host,
+                                         float F_thr, fs_candidate *cand_dev, int64_t cand_cap,
+                                         int64_t *n_cand_dev, void *stream);
 
 /* Launch configuration of the FP32 search for one transform length nfft
  * (no counterpart in the paper: it changes the speed, not the result beyond

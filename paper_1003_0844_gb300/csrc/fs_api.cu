@@ -318,6 +318,26 @@ fs_status fs_search_batch(fs_ctx *ctx, fs_seg *const *segs, int32_t nseg, const 
                         n_cand_dev, as_stream(stream));
 }
 
+fs_status fs_search_lattice_batch(fs_ctx *ctx, fs_seg *const *segs, int32_t nseg, const double *const *alpha_dev,
+                                  const double *const *delta_dev, const int32_t *nsky, const double *const *f1_dev,
+                                  const double *const *offset_dev, const int32_t *nspin, float F_thr,
+                                  fs_candidate *cand_dev, int64_t cand_cap, int64_t *n_cand_dev, void *stream) {
+  if (!ctx || !segs || nseg < 1 || !alpha_dev || !delta_dev || !nsky || !f1_dev || !offset_dev || !nspin ||
+      !n_cand_dev)
+    return FS_ERR_ARG;
+  if (cand_cap < 0 || (cand_cap > 0 && !cand_dev)) return FS_ERR_ARG;
+  for (int i = 0; i < nseg; i++) {
+    if (!segs[i] || segs[i]->ctx != ctx || segs[i]->d.precision != FS_PREC_F32) return FS_ERR_ARG;
+    if (!alpha_dev[i] || !delta_dev[i] || !f1_dev[i] || !offset_dev[i] || nsky[i] < 1 || nspin[i] < 1)
+      return FS_ERR_ARG;
+    if ((int64_t)nsky[i] * nspin[i] > (int64_t)1 << 31) return FS_ERR_SHAPE;
+    if (segs[i]->d.options & FS_OPT_INTERBIN) return FS_ERR_UNSUPPORTED;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  return search32_lattice_batch(ctx, segs, nseg, alpha_dev, delta_dev, nsky, f1_dev, offset_dev, nspin, F_thr,
+                                cand_dev, cand_cap, n_cand_dev, as_stream(stream));
+}
+
 static int tune_index(int64_t nfft) {
   if (!is_pow2(nfft) || nfft < 4096 || nfft > (int64_t(1) << 21)) return -1;
   int p = 0;

@@ -18,10 +18,20 @@
 #include <vector>
 #include "fs_pass32.cuh"
 
+// The templates one segment of a batch searches: a grid (alpha, delta [nsky] x f1
+// [nspin], offset NULL) or lattice templates (f1 and offset [nsky][nspin]).
+struct SegTemplates {
+  const double *alpha = nullptr, *delta = nullptr, *f1 = nullptr, *offset = nullptr;
+  int nsky = 0, nspin = 0;
+  bool operator==(const SegTemplates &o) const {
+    return alpha == o.alpha && delta == o.delta && f1 == o.f1 && offset == o.offset && nsky == o.nsky &&
+           nspin == o.nspin;
+  }
+};
+
 struct BatchPlan {
   std::vector<uint64_t> serials;
-  const double *alpha = nullptr, *delta = nullptr, *f1 = nullptr;
-  int nsky = 0, nspin = 0;
+  std::vector<SegTemplates> tpl;
   float thr = 0.f;
   fs_candidate *cand = nullptr;
   int64_t cap = 0;
@@ -58,23 +68,23 @@ static fs_status ensure_side_streams(fs_ctx *ctx) {
   return FS_OK;
 }
 
-static bool plan_matches(const fs_ctx *ctx, const BatchPlan &p, fs_seg *const *segs, int nseg, const double *alpha,
-                         const double *delta, int nsky, const double *f1, int nspin, float thr, fs_candidate *cand,
-                         int64_t cap, int64_t *ncand) {
+static bool plan_matches(const fs_ctx *ctx, const BatchPlan &p, fs_seg *const *segs, int nseg,
+                         const SegTemplates *tpl, float thr, fs_candidate *cand, int64_t cap, int64_t *ncand) {
   if ((int)p.serials.size() != nseg) return false;
   for (int i = 0; i < nseg; i++)
-    if (p.serials[i] != segs[i]->serial) return false;
+    if (p.serials[i] != segs[i]->serial || !(p.tpl[i] == tpl[i])) return false;
   for (int i = 0; i < fs_ctx::kWsSlots; i++)
     if (p.ws[i] != ctx->ws[i]) return false;
-  return p.alpha == alpha && p.delta == delta && p.nsky == nsky && p.f1 == f1 && p.nspin == nspin &&
-         p.thr == thr && p.cand == cand && p.cap == cap && p.ncand == ncand && p.tune_version == ctx->tune_version &&
+  return p.thr == thr && p.cand == cand && p.cap == cap && p.ncand == ncand && p.tune_version == ctx->tune_version &&
          p.persistent == ctx->persistent;
 }
 
-fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const double *alpha, const double *delta,
-                         int nsky, const double *f1, int nspin, float thr, fs_candidate *cand, int64_t cap,
-                         int64_t *ncand, cudaStream_t st) {
-  if (ctx->plan && plan_matches(ctx, *ctx->plan, segs, nseg, alpha, delta, nsky, f1, nspin, thr, cand, cap, ncand)) {
+// lattice templates run from the persistent queue's lattice items (lattice_supported)
+bool lattice_supported(const Cfg32 &c);
+
+static fs_status batch_run(fs_ctx *ctx, fs_seg *const *segs, int nseg, const SegTemplates *tpl, float thr,
+                           fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st) {
+  if (ctx->plan && plan_matches(ctx, *ctx->plan, segs, nseg, tpl, thr, cand, cap, ncand)) {
     if (cudaGraphLaunch(ctx->plan->exec, st) != cudaSuccess) return FS_ERR_CUDA;
     ctx->launches += ctx->plan->launches;
     return FS_OK;
@@ -90,8 +100,9 @@ fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const doubl
   };
   std::vector<Cfg32> cfg(nseg);
   for (int i = 0; i < nseg; i++) {
-    fs_status s = config32(ctx, segs[i], nsky, seg_nbins(segs[i]), &cfg[i]);
+    fs_status s = config32(ctx, segs[i], tpl[i].nsky, seg_nbins(segs[i]), &cfg[i]);
     if (s != FS_OK) return s;
+    if (tpl[i].offset && !lattice_supported(cfg[i])) return FS_ERR_UNSUPPORTED;
   }
   // longest transforms first, each onto the branch with less work so far
   std::vector<int> order(nseg);
@@ -108,7 +119,7 @@ fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const doubl
   // size both branch workspaces before recording (no allocation inside the graph)
   for (int i : order) {
     Ws32 w;
-    fs_status s = workspace32(ctx, 1 + branch[i], segs[i], cfg[i], nsky, nspin, true, st, &w);
+    fs_status s = workspace32(ctx, 1 + branch[i], segs[i], cfg[i], tpl[i].nsky, tpl[i].nspin, true, st, &w);
     if (s != FS_OK) return s;
   }
   fs_status s = ensure_side_streams(ctx);
@@ -131,10 +142,11 @@ fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const doubl
     const int i = order[k];
     cudaStream_t sb = branch[i] ? s1 : s0;
     Ws32 w;
-    r = workspace32(ctx, 1 + branch[i], segs[i], cfg[i], nsky, nspin, false, sb, &w);
+    const SegTemplates &t = tpl[i];
+    r = workspace32(ctx, 1 + branch[i], segs[i], cfg[i], t.nsky, t.nspin, false, sb, &w);
     if (r == FS_OK)
-      r = search32_run(ctx, segs[i], cfg[i], w, alpha, delta, nsky, f1, nspin, thr, nullptr, seg_nbins(segs[i]),
-                       cand ? cand + (int64_t)i * cap : nullptr, cap, ncand + i, sb);
+      r = search32_run(ctx, segs[i], cfg[i], w, t.alpha, t.delta, t.nsky, t.f1, t.nspin, thr, nullptr,
+                       seg_nbins(segs[i]), cand ? cand + (int64_t)i * cap : nullptr, cap, ncand + i, sb, t.offset);
   }
   if (r == FS_OK && (cudaEventRecord(ctx->join[1], s1) != cudaSuccess || cudaStreamWaitEvent(s0, ctx->join[1], 0) != cudaSuccess))
     r = FS_ERR_CUDA;
@@ -152,11 +164,7 @@ fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const doubl
   }
   BatchPlan *p = new BatchPlan();
   for (int i = 0; i < nseg; i++) p->serials.push_back(segs[i]->serial);
-  p->alpha = alpha;
-  p->delta = delta;
-  p->f1 = f1;
-  p->nsky = nsky;
-  p->nspin = nspin;
+  p->tpl.assign(tpl, tpl + nseg);
   p->thr = thr;
   p->cand = cand;
   p->cap = cap;
@@ -170,6 +178,35 @@ fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const doubl
   if (cudaGraphLaunch(exec, st) != cudaSuccess) return FS_ERR_CUDA;
   ctx->launches += per_replay;
   return FS_OK;
+}
+
+fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const double *alpha, const double *delta,
+                         int nsky, const double *f1, int nspin, float thr, fs_candidate *cand, int64_t cap,
+                         int64_t *ncand, cudaStream_t st) {
+  SegTemplates t;
+  t.alpha = alpha;
+  t.delta = delta;
+  t.f1 = f1;
+  t.nsky = nsky;
+  t.nspin = nspin;
+  std::vector<SegTemplates> tpl((size_t)nseg, t);
+  return batch_run(ctx, segs, nseg, tpl.data(), thr, cand, cap, ncand, st);
+}
+
+fs_status search32_lattice_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const double *const *alpha,
+                                 const double *const *delta, const int32_t *nsky, const double *const *f1,
+                                 const double *const *offset, const int32_t *nspin, float thr, fs_candidate *cand,
+                                 int64_t cap, int64_t *ncand, cudaStream_t st) {
+  std::vector<SegTemplates> tpl((size_t)nseg);
+  for (int i = 0; i < nseg; i++) {
+    tpl[i].alpha = alpha[i];
+    tpl[i].delta = delta[i];
+    tpl[i].f1 = f1[i];
+    tpl[i].offset = offset[i];
+    tpl[i].nsky = nsky[i];
+    tpl[i].nspin = nspin[i];
+  }
+  return batch_run(ctx, segs, nseg, tpl.data(), thr, cand, cap, ncand, st);
 }
 
 // ------------------------------------------------------------------ tuner

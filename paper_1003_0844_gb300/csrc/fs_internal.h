@@ -168,6 +168,11 @@ fs_status ensure_buffer(void **buf, size_t *cur, size_t bytes, cudaStream_t st);
 fs_status search32_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const double *alpha, const double *delta,
                          int nsky, const double *f1, int nspin, float thr, fs_candidate *cand, int64_t cap,
                          int64_t *ncand, cudaStream_t st);
+// The same over lattice templates, one template set per segment (host arrays of nseg).
+fs_status search32_lattice_batch(fs_ctx *ctx, fs_seg *const *segs, int nseg, const double *const *alpha,
+                                 const double *const *delta, const int32_t *nsky, const double *const *f1,
+                                 const double *const *offset, const int32_t *nspin, float thr, fs_candidate *cand,
+                                 int64_t cap, int64_t *ncand, cudaStream_t st);
 void batch_plan_release(fs_ctx *ctx);
 
 // Fine search (fs_refine.cu).

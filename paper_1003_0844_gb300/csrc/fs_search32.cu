@@ -556,16 +556,20 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
   return FS_OK;
 }
 
+// Lattice templates run as lattice items of the persistent queue: the split's items
+// must be built, and 2^21 takes its sub-transforms on the 1024 x 1024 split only.
+bool lattice_supported(const Cfg32 &c) {
+  if (c.interbin || c.full || !c.persistent || !passes_lat_instantiated(c.sh.N1, c.sh.N2)) return false;
+  return !c.vshift || (c.vshift == 1 && c.sh.N1 == 1024 && c.sh.N2 == 1024);
+}
+
 fs_status search32_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
                            const double *f1, const double *offset, int nspin, float thr, float *F, int64_t nbins,
                            fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st) {
   Cfg32 c;
   fs_status s = config32(ctx, seg, nsky, nbins, &c);
   if (s != FS_OK) return s;
-  if (c.interbin || c.full || !c.persistent || !passes_lat_instantiated(c.sh.N1, c.sh.N2))
-    return FS_ERR_UNSUPPORTED;
-  // 2^21: sub-transforms on the 1024 x 1024 split only
-  if (c.vshift && (c.vshift != 1 || c.sh.N1 != 1024 || c.sh.N2 != 1024)) return FS_ERR_UNSUPPORTED;
+  if (!lattice_supported(c)) return FS_ERR_UNSUPPORTED;
   Ws32 w;
   s = workspace32(ctx, 0, seg, c, nsky, nspin, true, st, &w);
   if (s != FS_OK) return s;

@@ -29,7 +29,7 @@ EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_prepare_segment_
            "fs_fstat_points", "fs_refine", "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm_cell",
            "fs_false_alarm", "fs_threshold", "fs_cell_count", "fs_linear_model_fisher", "fs_lattice",
            "fs_lattice_nodes", "fs_lattice_templates", "fs_search_lattice", "fs_search_lattice_noalloc",
-           "fs_selftest_wait"]
+           "fs_search_lattice_batch", "fs_selftest_wait"]
 PROF_KINDS = ("prepare", "demodulate", "pass1", "pass2", "other")
 
 
@@ -96,6 +96,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.fs_demodulate.argtypes = [vp, vp, f64, f64, vp, vp, vp, vp, vp]
     lib.fs_inject.argtypes = [vp, vp, i64, f64, f64, f64, f64, ctypes.POINTER(_Injection), i32, vp]
     lib.fs_search_batch.argtypes = [vp, ctypes.POINTER(vp), i32, vp, vp, i32, vp, i32, f32, vp, i64, vp, vp]
+    pv, pi = ctypes.POINTER(vp), ctypes.POINTER(i32)
+    lib.fs_search_lattice_batch.argtypes = [vp, pv, i32, pv, pv, pi, pv, pv, pi, f32, vp, i64, vp, vp]
     lib.fs_set_tuning.argtypes = [vp, i64, ctypes.POINTER(_Tuning)]
     lib.fs_get_tuning.argtypes = [vp, i64, ctypes.POINTER(_Tuning)]
     lib.fs_autotune.argtypes = [vp, vp, vp, vp, i32, vp, i32, i32, ctypes.POINTER(_Tuning), vp]
@@ -122,7 +124,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                  "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune", "fs_fstat_points", "fs_refine",
                  "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm", "fs_threshold", "fs_cell_count",
                  "fs_linear_model_fisher", "fs_lattice", "fs_lattice_nodes", "fs_lattice_templates",
-                 "fs_search_lattice", "fs_search_lattice_noalloc", "fs_selftest_wait"):
+                 "fs_search_lattice", "fs_search_lattice_noalloc", "fs_search_lattice_batch",
+                 "fs_selftest_wait"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -369,6 +372,36 @@ def search_batch(ctx: Context, segs, alpha: torch.Tensor, delta: torch.Tensor, f
                                  float(F_thr), _ptr(cand), int(cand.shape[1]) if cand_cap > 0 else 0, _ptr(n_cand),
                                  _stream(stream))
     _check(st, "fs_search_batch")
+    return BatchResult(cand, n_cand)
+
+
+def search_lattice_batch(ctx: Context, segs, templates, F_thr: float, cand_cap: int = 1 << 14,
+                         cand: torch.Tensor | None = None, n_cand: torch.Tensor | None = None,
+                         stream=None) -> BatchResult:
+    """fs_search_lattice_batch: segment s searches its own lattice templates[s] =
+    (alpha, delta, f1, offset), device float64 tensors with alpha, delta [nsky] and
+    f1, offset [nsky, nspin] (as for search_lattice); candidates only."""
+    nseg = len(segs)
+    if len(templates) != nseg:
+        raise ValueError("one template set per segment expected")
+    for a, d, f, o in templates:
+        for t, nm in ((a, "alpha"), (d, "delta"), (f, "f1"), (o, "offset")):
+            _need_cuda(t, nm, torch.float64)
+        if d.numel() != a.numel() or f.dim() != 2 or f.shape[0] != a.numel() or tuple(o.shape) != tuple(f.shape):
+            raise ValueError("alpha, delta [nsky] and f1, offset [nsky, nspin] expected")
+    if cand is None:
+        cand = torch.empty((nseg, max(cand_cap, 1), 4), dtype=torch.int32, device="cuda")
+    if n_cand is None:
+        n_cand = torch.zeros(nseg, dtype=torch.int64, device="cuda")
+    P, I = ctypes.c_void_p * nseg, ctypes.c_int32 * nseg
+    handles = P(*[sg.handle.value for sg in segs])
+    ptrs = [P(*[t[k].data_ptr() for t in templates]) for k in range(4)]
+    nsky = I(*[t[0].numel() for t in templates])
+    nspin = I(*[t[2].shape[1] for t in templates])
+    st = ctx.lib.fs_search_lattice_batch(ctx.handle, handles, nseg, ptrs[0], ptrs[1], nsky, ptrs[2], ptrs[3], nspin,
+                                         float(F_thr), _ptr(cand), int(cand.shape[1]) if cand_cap > 0 else 0,
+                                         _ptr(n_cand), _stream(stream))
+    _check(st, "fs_search_lattice_batch")
     return BatchResult(cand, n_cand)
 
 

@@ -54,6 +54,8 @@ def test_null_arguments_rejected_without_device(lib):
                          ctypes.c_int64(0), None, None) == 1
     assert lib.fs_search_noalloc(None, None, None, None, 0, None, 0, ctypes.c_float(0), None, ctypes.c_int64(0),
                                  None, ctypes.c_int64(0), None, None) == 1
+    assert lib.fs_search_lattice_batch(None, None, 0, None, None, None, None, None, None, ctypes.c_float(0), None,
+                                       ctypes.c_int64(0), None, None) == 1
     for name in ("fs_search_lattice", "fs_search_lattice_noalloc"):
         assert getattr(lib, name)(None, None, None, None, 0, None, None, 0, ctypes.c_float(0), None,
                                   ctypes.c_int64(0), None, ctypes.c_int64(0), None, None) == 1, name

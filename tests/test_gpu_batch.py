@@ -163,6 +163,46 @@ def test_batch_matches_oracle_and_single_searches(fs):
     assert max_rel_dF(F0, ref) > 10 * F32_TOL
 
 
+def test_lattice_batch_matches_single_lattice_searches(fs):
+    """fs_search_lattice_batch: every segment of the uneven batch with its own lattice
+    of the same sky patch (its own Fisher matrix at its epoch, so its own counts of sky
+    rows and spindown nodes) reports the same candidates as fs_search_lattice on that
+    segment alone (same kernels, same configuration: bit-exact), on the first call and
+    on the recorded graph's replay; an interbinning segment is refused."""
+    import math
+    b, det, segs, t0, xs, _, _, _ = _batch_case()
+    ctx = fs.Context(det)
+    handles = [fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0, t0=t0[i])
+               for i, (wl, x) in enumerate(zip(segs, xs))]
+    tpl = []
+    for i, wl in enumerate(segs):
+        G = fs.linear_model_fisher(det, wl.n, wl.dt, float(t0[i]))
+        B, _ = fs.lattice(G, 0.75, 2 * math.pi / (wl.nfft * wl.dt))
+        a, d, f1, off = fs.lattice_templates(B, det, wl.fl, wl.nfft, wl.dt, (-2e-9, 0.0), (0.30, 0.45, -0.10, 0.05))
+        tpl.append(tuple(_dev(v) for v in (a, d, f1, off)))
+    assert len({tuple(t[2].shape) for t in tpl}) > 2
+    key = lambda c: sorted(zip(c[0].tolist(), c[1].tolist(), c[2].tolist(), c[3].tolist()))
+    res = fs.search_lattice_batch(ctx, handles, tpl, b.F_thr, cand_cap=1 << 14)
+    assert ctx.sync_status() == 0
+    first = [key(res.candidates(i)) for i in range(len(segs))]
+    assert sum(len(c) for c in first) > 0
+    res.cand.zero_()
+    res.n_cand.fill_(-1)
+    res2 = fs.search_lattice_batch(ctx, handles, tpl, b.F_thr, cand_cap=1 << 14, cand=res.cand, n_cand=res.n_cand)
+    assert ctx.sync_status() == 0
+    assert [key(res2.candidates(i)) for i in range(len(segs))] == first
+    for i, h in enumerate(handles):
+        single = fs.search_lattice(ctx, h, *tpl[i], b.F_thr, write_F=False, cand_cap=1 << 14)
+        assert ctx.sync_status() == 0
+        assert first[i] == key(single.candidates()), i
+    wl = segs[0]
+    ib = fs.Segment(ctx, _dev(xs[0], torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0, t0=t0[0], interbin=True)
+    with pytest.raises(fs.FstatError) as e:
+        fs.search_lattice_batch(ctx, [ib] + handles[1:], tpl, b.F_thr)
+    assert e.value.status == 7
+    ctx.close()
+
+
 def test_batch_full_configuration_sampled(fs):
     """The benchmark's batch (64 segments of 1/2/3/6 days, 2^16-2^20, 64 skies x 64
     spindowns, one graph): for one template of each segment kind, the crossings the

@@ -182,17 +182,17 @@ def test_lattice_batch_matches_single_lattice_searches(fs):
         tpl.append(tuple(_dev(v) for v in (a, d, f1, off)))
     assert len({tuple(t[2].shape) for t in tpl}) > 2
     key = lambda c: sorted(zip(c[0].tolist(), c[1].tolist(), c[2].tolist(), c[3].tolist()))
-    res = fs.search_lattice_batch(ctx, handles, tpl, b.F_thr, cand_cap=1 << 14)
+    res = fs.search_lattice_batch(ctx, handles, tpl, b.F_thr, cand_cap=1 << 20)
     assert ctx.sync_status() == 0
     first = [key(res.candidates(i)) for i in range(len(segs))]
     assert sum(len(c) for c in first) > 0
     res.cand.zero_()
     res.n_cand.fill_(-1)
-    res2 = fs.search_lattice_batch(ctx, handles, tpl, b.F_thr, cand_cap=1 << 14, cand=res.cand, n_cand=res.n_cand)
+    res2 = fs.search_lattice_batch(ctx, handles, tpl, b.F_thr, cand_cap=1 << 20, cand=res.cand, n_cand=res.n_cand)
     assert ctx.sync_status() == 0
     assert [key(res2.candidates(i)) for i in range(len(segs))] == first
     for i, h in enumerate(handles):
-        single = fs.search_lattice(ctx, h, *tpl[i], b.F_thr, write_F=False, cand_cap=1 << 14)
+        single = fs.search_lattice(ctx, h, *tpl[i], b.F_thr, write_F=False, cand_cap=1 << 20)
         assert ctx.sync_status() == 0
         assert first[i] == key(single.candidates()), i
     wl = segs[0]

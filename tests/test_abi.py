@@ -41,6 +41,20 @@ def test_binding_lists_every_export():
     assert sorted(fstat.EXPORTS) == _declared_symbols() or set(_declared_symbols()) <= set(fstat.EXPORTS)
 
 
+def test_header_is_plain_c(tmp_path):
+    """include/fstat.h compiles as strict C99 on its own (no CUDA or C++ headers)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "fstat.h"\nint main(void) { return fs_strerror(0) == 0; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_strerror_is_host_only(lib):
     lib.fs_strerror.restype = ctypes.c_char_p
     assert lib.fs_strerror(0) == b"ok"

@@ -55,6 +55,41 @@ def test_header_is_plain_c(tmp_path):
     assert r.returncode == 0, r.stderr
 
 
+def test_c_program_links_and_calls_host_entry_points(lib, tmp_path):
+    """A plain C program links against libfstat.so and calls host-only entry points:
+    the false-alarm probability of Eqs. PF, FP, 1 - (1 - (1 + F0) exp(-F0))^n, and its
+    inverse, against the closed form."""
+    import math
+    import shutil
+    import subprocess
+    from paper_1003_0844_gb300 import build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(build.build())
+    src = tmp_path / "use_lib.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "fstat.h"\n'
+        'int main(void) {\n'
+        '  double pf = 0.0, nf = 0.0, thr = 0.0;\n'
+        '  if (fs_false_alarm(20.0, 1e6, &pf, &nf) != FS_OK) return 1;\n'
+        '  if (fs_threshold(0.01, 1e6, &thr) != FS_OK) return 2;\n'
+        '  printf("%.17g %.17g %.17g\\n", pf, nf, thr);\n'
+        '  return 0;\n}\n')
+    exe = str(tmp_path / "use_lib")
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lfstat",
+                        "-Wl,-rpath," + libdir, "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr
+    pf, nf, thr = map(float, r.stdout.split())
+    cell = 21.0 * math.exp(-20.0)
+    assert pf == pytest.approx(-math.expm1(1e6 * math.log1p(-cell)), rel=1e-12)
+    assert nf == pytest.approx(1e6 * cell, rel=1e-12)
+    back = -math.expm1(1e6 * math.log1p(-(1.0 + thr) * math.exp(-thr)))
+    assert back == pytest.approx(0.01, rel=1e-9)
+
+
 def test_strerror_is_host_only(lib):
     lib.fs_strerror.restype = ctypes.c_char_p
     assert lib.fs_strerror(0) == b"ok"

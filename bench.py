@@ -639,7 +639,7 @@ def main_lattice(args):
     G = fs.linear_model_fisher(det, wl.n, wl.dt)
     B, _ = fs.lattice(G, LATTICE_MATCH, 2 * math.pi / (wl.nfft * wl.dt))
     a, d, f1, off = fs.lattice_templates(B, det, wl.fl, wl.nfft, wl.dt, wl.f1_range, LATTICE_BOX)
-    rows = np.arange(rank, a.size, world)
+    rows = shard.row_shard(a.size, rank, world)
     if args.nsky:
         rows = rows[:args.nsky]
 

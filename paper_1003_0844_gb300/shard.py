@@ -3,7 +3,8 @@
 Templates (sky position, spindown) are independent, so the search shards with
 no data-path exchange: rank r of W takes every W-th point of a sky lattice of
 W * nsky points (each rank keeps whole skies, so its per-sky demodulation is
-shared by all of its spindowns).  The only cross-rank steps are the timing
+shared by all of its spindowns); a fixed template set such as a lattice patch is
+dealt out by sky rows instead.  The only cross-rank steps are the timing
 reduction of a benchmark and, in a real search, merging the candidate lists.
 """
 from __future__ import annotations
@@ -16,6 +17,15 @@ def sky_shard(n_per_rank: int, rank: int, world: int) -> np.ndarray:
     if not 0 <= rank < world:
         raise ValueError("rank %d outside world %d" % (rank, world))
     return np.arange(rank, n_per_rank * world, world, dtype=np.int64)
+
+
+def row_shard(nrows: int, rank: int, world: int) -> np.ndarray:
+    """Rows of a fixed template set (the sky rows of a lattice patch, each with its
+    spindown nodes) owned by `rank`: every world-th row, so the ranks split one
+    search (strong scaling) with nearly equal shares."""
+    if not 0 <= rank < world:
+        raise ValueError("rank %d outside world %d" % (rank, world))
+    return np.arange(rank, nrows, world, dtype=np.int64)
 
 
 def max_over_ranks(value: float, device=None) -> float:

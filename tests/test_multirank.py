@@ -1,6 +1,6 @@
-"""Two processes over gloo (CPU): the sky sharding partitions the lattice, the
-benchmark's max-over-ranks timing reduction, and the candidate merge that is the
-only cross-rank exchange of a sharded search."""
+"""Two processes over gloo (CPU): the sky sharding partitions the lattice, the row
+dealing of a fixed lattice patch, the benchmark's max-over-ranks timing reduction,
+and the candidate merge that is the only cross-rank exchange of a sharded search."""
 import os
 import socket
 
@@ -38,7 +38,14 @@ def _worker(rank, world, port, out):
         F = rng.uniform(20, 40, k)
         gs, gm, gb, gF = shard.gather_candidates(sky, spin, bins, F, idx)
         t = shard.max_over_ranks(10.0 + rank)
-        out[rank] = (parts, (gs.tolist(), gm.tolist(), gb.tolist(), gF.tolist()), t)
+        # a fixed lattice patch of 11 sky rows dealt out by rows; candidates merge by row index
+        rows = shard.row_shard(11, rank, world)
+        rparts = [None] * world
+        dist.all_gather_object(rparts, rows.tolist())
+        lsky = np.arange(rows.size)
+        rs, _, _, _ = shard.gather_candidates(lsky, np.zeros(rows.size), np.zeros(rows.size), np.ones(rows.size),
+                                              rows)
+        out[rank] = (parts, (gs.tolist(), gm.tolist(), gb.tolist(), gF.tolist()), t, rparts, rs.tolist())
     finally:
         dist.destroy_process_group()
 
@@ -55,6 +62,10 @@ def test_two_rank_sharding_timing_and_candidate_merge():
     assert allidx == list(range(7 * world))          # complete
     assert not set(parts0[0]) & set(parts0[1])        # disjoint
     assert res[0][2] == res[1][2] == 11.0             # max over ranks
+    rparts = res[0][3]
+    assert sorted(rparts[0] + rparts[1]) == list(range(11)) and not set(rparts[0]) & set(rparts[1])
+    assert abs(len(rparts[0]) - len(rparts[1])) <= 1  # nearly equal shares
+    assert res[0][4] == res[1][4] == list(range(11))  # one candidate per row, merged in row order
     assert res[0][1] == res[1][1]                     # every rank holds the same merged list
     gs, gm, gb, gF = res[0][1]
     assert len(gs) == 5 + 6
@@ -78,3 +89,6 @@ def test_single_process_shard_is_identity():
     assert shard.max_over_ranks(3.5) == 3.5
     with pytest.raises(ValueError):
         shard.sky_shard(5, 2, 2)
+    assert shard.row_shard(5, 0, 1).tolist() == list(range(5))
+    with pytest.raises(ValueError):
+        shard.row_shard(5, -1, 2)

@@ -65,11 +65,14 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x ma
 
 def _args():
     p = argparse.ArgumentParser()
-    p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=100)
-    p.add_argument("--warmup", type=int, default=5)
-    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="grid_2d")
+    p.add_argument("--gpus", type=int, default=1, help="GPUs (one process each under torchrun)")
+    p.add_argument("--steps", type=int, default=100, help="timed steps")
+    p.add_argument("--warmup", type=int, default=5, help="untimed warm-up steps (at least 3 for a valid number)")
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"],
+                   help="ours: the CUDA library; reference: the CPU oracle on the host cores")
+    p.add_argument("--workload", default="grid_2d",
+                   help="grid_2d (default), grid_2d_ib, wide_6d, lattice_2d, refine_2d, a batch (uneven_64, "
+                        "uneven_small) or a test-size workload (tiny, small)")
     p.add_argument("--cpu-templates", type=int, default=320, help="oracle sample size (templates, ~10 s on one core)")
     p.add_argument("--fp64-skies", type=int, default=2, help="skies of the plain FP64 form comparison")
     p.add_argument("--quick", action="store_true", help="skip the CPU baseline and FP64 comparison")

@@ -80,7 +80,63 @@ def _args():
     p.add_argument("--tune", action="store_true", help="run the launch tuner for each transform length first")
     p.add_argument("--n1", type=int, default=0, help="first-pass length N1 of the transform split (0: default)")
     p.add_argument("--cands", type=int, default=1024, help="fine-search workload: candidates refined per step")
+    p.add_argument("--stub", action="store_true",
+                   help="launcher self-test on the CPU: every rank takes its sky shard and reports it over gloo; "
+                        "no GPU work")
     return p.parse_args()
+
+
+def _free_port() -> int:
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def launch_ranks(args):
+    """--gpus N: one process per GPU.  Under torchrun (WORLD_SIZE set) the world size
+    must equal N.  Without it and N > 1, this script re-runs itself under
+    torch.distributed.run with N ranks on this node (rendezvous on 127.0.0.1) and
+    returns their exit status; None means: run here as the only rank or as a rank."""
+    ws = os.environ.get("WORLD_SIZE")
+    if ws is not None:
+        if int(ws) != args.gpus:
+            raise SystemExit("bench.py: WORLD_SIZE=%s but --gpus %d" % (ws, args.gpus))
+        return None
+    if args.gpus <= 1:
+        return None
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(args.gpus),
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
+def run_stub(args):
+    """Launcher self-test without a GPU: each rank takes its sky shard of the workload
+    exactly as the GPU path does, the shards and a per-rank time go through gloo, and
+    rank 0 prints the line the GPU path would print with the shard of every rank."""
+    import torch.distributed as dist
+    from paper_1003_0844_gb300 import shard
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    wl = W.WORKLOADS[args.workload]
+    mine = shard.sky_shard(wl.nsky, rank, world)
+    parts = [mine.tolist()]
+    if world > 1:
+        parts = [None] * world
+        dist.all_gather_object(parts, mine.tolist())
+    ms = shard.max_over_ranks(1.0 + rank)
+    if rank == 0:
+        print(json.dumps({"metric": metric_name(args.workload), "value": None, "unit": "templates/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "stub": True, "rank_shards": parts,
+                          "config": {"workload": wl.name, "nsky": wl.nsky, "nspin": wl.nspin,
+                                     "parallelism": "sky shards x%d" % world}}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def _profile_traffic(kernel_profile: str):
@@ -786,8 +842,104 @@ def main_lattice(args):
         dist.destroy_process_group()
 
 
+def grid_e2e(fs, ctx, seg, wl, x32, alpha, delta, f1, F_dev, cand, ncand, cap, steps):
+    """End to end through the public API with host buffers, every step: the data from
+    pinned host memory to the device, segment preparation, the search, and its whole
+    result back on the host: the F map of every template and bin, the candidates and
+    their count.  Two ways of returning F are timed: the transform kernel writing F
+    straight into a pinned host buffer (the device writes over the host link, no
+    staging), and F written to device memory by sky chunks with each chunk copied to
+    the pinned host buffer on a second stream while the next chunk runs.  The faster
+    is "e2e"; the other and the candidates-only figure (F left on the device) are
+    reported beside it.  Returns the fields for the JSON line."""
+    import torch
+    ntempl, nbins = F_dev.shape
+    nsky, nspin = alpha.numel(), f1.numel()
+    xh_pin = torch.empty(wl.n, dtype=torch.float32).pin_memory()
+    xh_pin.copy_(x32.cpu())
+    cand_h = torch.empty((cap, 4), dtype=torch.int32).pin_memory()
+    nc_h = torch.empty(1, dtype=torch.int64).pin_memory()
+    F_host = torch.empty((ntempl, nbins), dtype=torch.float32).pin_memory()
+    xd = torch.empty_like(x32)
+    ke = max(5, steps // 5)
+    main_st = torch.cuda.current_stream()
+    copy_st = torch.cuda.Stream()
+    chunk = max(1, min(nsky, 32))  # skies per chunk of the staged variant
+    nchunk = (nsky + chunk - 1) // chunk
+    cand_c = torch.empty((nchunk, cap, 4), dtype=torch.int32, device="cuda")  # per chunk: its own list
+    ncand_c = torch.zeros(nchunk, dtype=torch.int64, device="cuda")
+    cand_ch = torch.empty((nchunk, cap, 4), dtype=torch.int32).pin_memory()
+    nc_ch = torch.empty(nchunk, dtype=torch.int64).pin_memory()
+
+    def direct():
+        fs.search(ctx, seg, alpha, delta, f1, wl.F_thr, F_out=F_host, cand=cand, n_cand=ncand, cand_cap=cap)
+        nc_h.copy_(ncand, non_blocking=True)
+        cand_h.copy_(cand, non_blocking=True)
+
+    def staged():
+        for i, s0 in enumerate(range(0, nsky, chunk)):
+            s1 = min(nsky, s0 + chunk)
+            rows = slice(s0 * nspin, s1 * nspin)
+            # chunks write distinct rows; a step's copies end before the next step (synchronised)
+            fs.search(ctx, seg, alpha[s0:s1], delta[s0:s1], f1, wl.F_thr, F_out=F_dev[rows], cand=cand_c[i],
+                      n_cand=ncand_c[i:i + 1], cand_cap=cap)
+            copy_st.wait_stream(main_st)
+            with torch.cuda.stream(copy_st):
+                F_host[rows].copy_(F_dev[rows], non_blocking=True)
+        main_st.wait_stream(copy_st)
+        nc_ch.copy_(ncand_c, non_blocking=True)
+        cand_ch.copy_(cand_c, non_blocking=True)
+
+    def cands_only():
+        fs.search(ctx, seg, alpha, delta, f1, wl.F_thr, F_out=F_dev, cand=cand, n_cand=ncand, cand_cap=cap)
+        nc_h.copy_(ncand, non_blocking=True)
+        cand_h.copy_(cand, non_blocking=True)
+
+    def timed(search):
+        search()  # untimed first call
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            xd.copy_(xh_pin, non_blocking=True)
+            seg.load(xd)
+            search()
+            torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / ke
+
+    out = {}
+    t_direct = timed(direct)
+    # the host map equals the device map of the same search (sampled rows)
+    cands_only()
+    torch.cuda.synchronize()
+    rows = torch.linspace(0, ntempl - 1, 16).long()
+    same_direct = bool(torch.equal(F_host[rows], F_dev[rows].cpu()))
+    F_host.zero_()
+    t_staged = timed(staged)
+    same_staged = bool(torch.equal(F_host[rows], F_dev[rows].cpu()))
+    t_cands = timed(cands_only)
+    f_bytes = ntempl * nbins * 4
+    ways = {"direct": (t_direct, "the transform kernel writes F into a pinned host buffer", same_direct,
+                       cap * 16 + 8),
+            "staged": (t_staged, "F to device memory by chunks of %d skies, each copied to a pinned host buffer "
+                                 "on a second stream" % chunk, same_staged, nchunk * (cap * 16 + 8))}
+    best = min(ways, key=lambda k: ways[k][0])
+    for k, (t, how, same, cbytes) in ways.items():
+        rec = {"value": ntempl / t, "unit": "templates/s", "h2d_bytes_per_step": wl.n * 4,
+               "d2h_bytes_per_step": f_bytes + cbytes, "F_returned": True, "how": how,
+               "F_host_equals_device": same}
+        out["e2e" if k == best else "e2e_F_" + k] = rec
+    out["e2e_candidates_only"] = {"value": ntempl / t_cands, "unit": "templates/s", "h2d_bytes_per_step": wl.n * 4,
+                                  "d2h_bytes_per_step": cap * 16 + 8, "F_returned": False}
+    return out
+
+
 def main():
     args = _args()
+    rc = launch_ranks(args)
+    if rc is not None:
+        sys.exit(rc)
+    if args.stub:
+        return run_stub(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload in W.BATCHES:
@@ -963,26 +1115,7 @@ def main():
                                            W.spin_grid(wl.nspin, *wl.f1_range), ntc)
         line["cpu_baseline"] = {"value": rate, "unit": "templates/s", "cores": 1, "kind": "oracle",
                                 "sample": "segment preparation + %d templates (FFT mode), %.1f s" % (done, secs)}
-        # end to end through the public API with host buffers: pinned x -> device,
-        # prepare + search, candidates and their count -> host, every step
-        xh_pin = torch.empty(wl.n, dtype=torch.float32).pin_memory()
-        xh_pin.copy_(x32.cpu())
-        cand_h = torch.empty((cap, 4), dtype=torch.int32).pin_memory()
-        nc_h = torch.empty(1, dtype=torch.int64).pin_memory()
-        xd = torch.empty_like(x32)
-        ke = max(5, args.steps // 5)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(ke):
-            xd.copy_(xh_pin, non_blocking=True)
-            seg.load(xd)
-            fs.search(ctx, seg, alpha, delta, f1, wl.F_thr, F_out=F_out, cand=cand, n_cand=ncand, cand_cap=cap)
-            nc_h.copy_(ncand, non_blocking=True)
-            cand_h.copy_(cand, non_blocking=True)
-            torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / ke
-        line["e2e"] = {"value": ntempl / e2e_s, "unit": "templates/s", "h2d_bytes_per_step": wl.n * 4,
-                       "d2h_bytes_per_step": cap * 16 + 8}
+        line.update(grid_e2e(fs, ctx, seg, wl, x32, alpha, delta, f1, F_out, cand, ncand, cap, args.steps))
     else:
         line.setdefault("e2e", None)
         line.setdefault("cpu_baseline", None)

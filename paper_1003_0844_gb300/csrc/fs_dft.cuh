@@ -8,7 +8,7 @@ namespace fs {
 
 // Compile-time loop: calls f(std::integral_constant<int, I>) for I = B..E-1.
 template <int B, int E, typename F>
-__device__ __forceinline__ void sfor(F &&f) {
+__host__ __device__ __forceinline__ void sfor(F &&f) {
   if constexpr (B < E) {
     f(std::integral_constant<int, B>{});
     sfor<B + 1, E>(f);
@@ -41,12 +41,12 @@ constexpr double cx_sin64(int k) {  // sin(2 pi k / 64)
   return q == 0 ? s : q == 1 ? c : q == 2 ? -s : -c;
 }
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
 // z * exp(-2 pi i K / M), M a power of two dividing 64, 0 <= K < M/2.
 template <int M, int K>
-__device__ __forceinline__ float2 twmul(float2 z) {
+__host__ __device__ __forceinline__ float2 twmul(float2 z) {
   constexpr float r2 = 0.70710678118654752440f;
   if constexpr (K == 0) {
     return z;
@@ -71,43 +71,115 @@ constexpr int cx_bitrev(int i, int bits) {
   return r;
 }
 
-// In-place DFT of v[0..N) (N = 2..32), natural order in and out: radix-2
-// decimation in frequency, then a compile-time bit-reversal (register renaming).
-// NZ: the inputs v[NZ..N) are known to be zero.  After each stage the nonzero
-// entries of every group (2 span entries) stay at offsets below
-// min(NZ, 2 span), so a pair whose both entries lie beyond that is left alone,
-// and a pair whose second entry does reduces to a copy and a twiddle product.
-// NOUT: only outputs X[0..NOUT) are needed (NOUT = N or N/2); with NOUT = N/2
-// the last stage skips the differences (they land on odd bit-reversed positions).
+// Radix-2 decimation in time with the butterflies written as fused multiply-adds.
+// A butterfly (a, b) -> (a + w b, a - w b) with a general twiddle w = c + i s costs
+// six FMAs instead of a complex product and four additions: w b is factored as
+// c (u + i v) with u = b.x - (s/c) b.y, v = b.y + (s/c) b.x when |c| >= |s| (else
+// as s (u + i v) with the ratio c/s), and a +- c u, a +- c v are FMAs (the
+// "tangent" factorisation of Linzer and Feig for FMA machines).  w = 1 and
+// w = -i need four additions.  The ratios and factors are rounded once at
+// compile time from the double-precision table above.
+template <int M, int K>
+__host__ __device__ __forceinline__ void bfly_dit(float2 &a, float2 &b) {
+  if constexpr (K == 0) {
+    const float2 t = b;
+    b = csub(a, t);
+    a = cadd(a, t);
+  } else if constexpr (4 * K == M) {  // w = -i: w b = (b.y, -b.x)
+    const float2 t = b;
+    b = make_float2(a.x - t.y, a.y + t.x);
+    a = make_float2(a.x + t.y, a.y - t.x);
+  } else {
+    constexpr int k64 = K * (64 / M);
+    constexpr double c = cx_cos64(k64), s = -cx_sin64(k64);
+    constexpr bool cbig = (c >= 0 ? c : -c) >= (s >= 0 ? s : -s);
+    constexpr float f = (float)(cbig ? c : s);
+    constexpr float r = (float)(cbig ? s / c : c / s);
+    float u, v;
+    if constexpr (cbig) {
+      u = fmaf(-r, b.y, b.x);
+      v = fmaf(r, b.x, b.y);
+    } else {
+      u = fmaf(r, b.x, -b.y);
+      v = fmaf(r, b.y, b.x);
+    }
+    b = make_float2(fmaf(-f, u, a.x), fmaf(-f, v, a.y));
+    a = make_float2(fmaf(f, u, a.x), fmaf(f, v, a.y));
+  }
+}
+// w b alone (the first operand of the butterfly is known to be zero).
+template <int M, int K>
+__host__ __device__ __forceinline__ float2 twmul_dit(float2 b) {
+  if constexpr (K == 0) {
+    return b;
+  } else if constexpr (4 * K == M) {
+    return make_float2(b.y, -b.x);
+  } else {
+    constexpr int k64 = K * (64 / M);
+    constexpr float c = (float)cx_cos64(k64), s = (float)(-cx_sin64(k64));
+    return make_float2(fmaf(c, b.x, -s * b.y), fmaf(s, b.x, c * b.y));
+  }
+}
+
+// Compile-time bookkeeping of the DIT stages: bit i of dit_nonzero(N, NZ, st) is set
+// when working entry i may be nonzero after st stages, for inputs v[NZ..N) = 0
+// (entry i starts as v[bitrev(i)]; a butterfly's outputs are nonzero when either
+// input is).
+constexpr unsigned dit_nonzero(int N, int NZ, int st) {
+  const int LG = cx_log2(N);
+  unsigned m = 0;
+  for (int i = 0; i < N; i++)
+    if (cx_bitrev(i, LG) < NZ) m |= 1u << i;
+  for (int q = 0; q < st; q++) {
+    const int h = 1 << q;
+    unsigned r = 0;
+    for (int i = 0; i < N; i++)
+      if (((m >> i) & 1u) || ((m >> (i ^ h)) & 1u)) r |= 1u << i;
+    m = r;
+  }
+  return m;
+}
+
+// In-place DFT of v[0..N) (N = 2..32), natural order in and out: the inputs are
+// renamed into bit-reversed order at compile time, then log2 N DIT stages.
+// NZ: the inputs v[NZ..N) are known to be zero (butterflies with a zero operand
+// become copies or a single twiddle product).  NOUT: only X[0..NOUT) are needed
+// (NOUT = N or N/2); with NOUT = N/2 the last stage forms the sums only.
 template <int N, int NZ = N, int NOUT = N>
-__device__ __forceinline__ void dft_inplace(float2 *v) {
+__host__ __device__ __forceinline__ void dft_inplace(float2 *v) {
   static_assert(NZ >= 1 && NZ <= N, "NZ leading inputs may be nonzero");
   static_assert(NOUT == N || 2 * NOUT == N, "output pruning keeps the lower half only");
   constexpr int LG = cx_log2(N);
+  float2 u[N];
+  sfor<0, N>([&](auto i) {
+    if constexpr (cx_bitrev(i, LG) < NZ) u[i] = v[cx_bitrev(i, LG)];
+  });
   sfor<0, LG>([&](auto st) {
-    constexpr int span = N >> (st + 1);
-    constexpr int nz = NZ < 2 * span ? NZ : 2 * span;  // nonzero prefix of each group
-    sfor<0, N / (2 * span)>([&](auto g) {
-      sfor<0, span>([&](auto k) {
-        constexpr int i0 = g * 2 * span + k;
-        if constexpr (k >= nz) {
-          // both entries are zero
-        } else if constexpr (k + span >= nz) {
-          const float2 a = v[i0];
-          v[i0 + span] = twmul<2 * span, k>(a);
-        } else if constexpr (st == LG - 1 && NOUT < N) {
-          v[i0] = cadd(v[i0], v[i0 + span]);
+    constexpr int h = 1 << st;
+    constexpr unsigned m = dit_nonzero(N, NZ, st);
+    sfor<0, N / (2 * h)>([&](auto g) {
+      sfor<0, h>([&](auto k) {
+        constexpr int i0 = g * 2 * h + k, i1 = i0 + h;
+        constexpr bool z0 = !((m >> i0) & 1u), z1 = !((m >> i1) & 1u);
+        constexpr bool last_pruned = (st == LG - 1) && (NOUT < N);
+        if constexpr (z0 && z1) {
+          // both zero
+        } else if constexpr (z1) {
+          if constexpr (!last_pruned) u[i1] = u[i0];
+        } else if constexpr (z0) {
+          const float2 t = twmul_dit<2 * h, k>(u[i1]);
+          u[i0] = t;
+          if constexpr (!last_pruned) u[i1] = make_float2(-t.x, -t.y);
+        } else if constexpr (last_pruned) {
+          const float2 t = twmul_dit<2 * h, k>(u[i1]);
+          u[i0] = cadd(u[i0], t);
         } else {
-          float2 a = v[i0], b = v[i0 + span];
-          v[i0] = cadd(a, b);
-          v[i0 + span] = twmul<2 * span, k>(csub(a, b));
+          bfly_dit<2 * h, k>(u[i0], u[i1]);
         }
       });
     });
   });
-  float2 tmp[N];
-  sfor<0, N>([&](auto i) { tmp[i] = v[cx_bitrev(i, LG)]; });
-  sfor<0, N>([&](auto i) { v[i] = tmp[i]; });
+  sfor<0, NOUT>([&](auto i) { v[i] = u[i]; });
 }
 
 }  // namespace fs

@@ -73,8 +73,10 @@ def _args():
     p.add_argument("--workload", default="grid_2d",
                    help="grid_2d (default), grid_2d_ib, wide_6d, lattice_2d, refine_2d, a batch (uneven_64, "
                         "uneven_small) or a test-size workload (tiny, small)")
-    p.add_argument("--cpu-templates", type=int, default=320, help="oracle sample size (templates, ~10 s on one core)")
-    p.add_argument("--fp64-skies", type=int, default=2, help="skies of the plain FP64 form comparison")
+    p.add_argument("--cpu-templates", type=int, default=320,
+                   help="oracle sample size: templates of the 2-day size per 20 host cores (~10 s)")
+    p.add_argument("--fp64-skies", type=int, default=16,
+                   help="skies of the plain FP64 form comparison (the FP32 error is taken over all their templates)")
     p.add_argument("--quick", action="store_true", help="skip the CPU baseline and FP64 comparison")
     p.add_argument("--nsky", type=int, default=None, help="override the sky count (profiling runs, batch sky subset)")
     p.add_argument("--tune", action="store_true", help="run the launch tuner for each transform length first")
@@ -256,25 +258,112 @@ def cufft_comparison(nfft, nbins, reps=10):
     return out
 
 
-def cpu_oracle_rate(x, wl, det, alpha, delta, f1, ntempl):
-    """Oracle (as it stands) on a bounded sample: segment preparation + ntempl templates, FFT mode."""
+# ------------------------------------------------------------------ the oracle on the host cores
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def host_cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker_init():
+    import oracle.fstat, oracle.refine, oracle.resample  # noqa: F401  (imports before any timed region)
+
+
+def _oracle_worker_ready(_):
+    return os.getpid()
+
+
+def _oracle_templates(task):
+    """One worker's share of a sample, the oracle as it stands: its own preparation
+    of the segment, then F of its templates (FFT mode; items are (alpha, delta, f1,
+    bin offset or None))."""
+    x, wl, det, items = task
     from oracle import fstat as ofs, resample as ors
-    t0 = time.perf_counter()
     seg = ors.Segment(np.asarray(x, dtype=np.float64), wl.dt)
-    done = 0
-    for s in range(len(alpha)):
-        for m in range(len(f1)):
-            if done >= ntempl:
-                break
-            if getattr(wl, "interbin", False):
-                ofs.fstat_interbinned(seg, alpha[s], delta[s], f1[m], wl.fl, det, wl.S0, wl.nfft)
-            else:
-                ofs.fstat(seg, alpha[s], delta[s], f1[m], wl.fl, det, wl.S0, wl.nfft)
-            done += 1
-        if done >= ntempl:
-            break
-    dt = time.perf_counter() - t0
-    return done / dt, dt, done
+    for a, d, f, off in items:
+        if getattr(wl, "interbin", False):
+            ofs.fstat_interbinned(seg, a, d, f, wl.fl, det, wl.S0, wl.nfft)
+        elif off is None:
+            ofs.fstat(seg, a, d, f, wl.fl, det, wl.S0, wl.nfft)
+        else:
+            ofs.fstat(seg, a, d, f, wl.fl, det, wl.S0, wl.nfft, bin_offset=off)
+    return len(items)
+
+
+def _oracle_points(task):
+    """One worker's share of fine-search work: exact-F passes with gradient and
+    Hessian at points (kind "pass"), or Nelder-Mead climbs from points ("climb")."""
+    kind, x, dt, pts, fl, det, S0 = task
+    from oracle import refine as orf
+    for p in pts:
+        if kind == "pass":
+            orf.fstat_point(np.asarray(x), dt, p, fl, det, S0, grad=True, hess=True)
+        else:
+            orf.fine_search(np.asarray(x), dt, p, fl, det, S0)
+    return len(pts)
+
+
+class OraclePool:
+    """The oracle as it stands on every host core: one worker process per core
+    (started with spawn, so no CUDA state is inherited), BLAS/OpenMP threads at one
+    per worker.  Work is dealt round-robin; a timed call is one pool.map."""
+
+    def __init__(self, cores: int | None = None):
+        import multiprocessing as mp
+        self.cores = int(cores or host_cores())
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(k, "1")
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init)
+        self.pool.map(_oracle_worker_ready, range(self.cores), chunksize=1)  # every worker up
+
+    def deal(self, items):
+        return [items[i::self.cores] for i in range(self.cores) if items[i::self.cores]]
+
+    def templates(self, tasks):
+        """tasks: [(x, wl, det, items)], one per worker -> (templates, seconds)."""
+        t0 = time.perf_counter()
+        n = sum(self.pool.map(_oracle_templates, tasks, chunksize=1))
+        return n, time.perf_counter() - t0
+
+    def points(self, tasks):
+        t0 = time.perf_counter()
+        n = sum(self.pool.map(_oracle_points, tasks, chunksize=1))
+        return n, time.perf_counter() - t0
+
+    def record(self, value, unit, sample):
+        return {"value": value, "unit": unit, "cores": self.cores, "cpu": host_cpu_model(), "kind": "oracle",
+                "sample": sample}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_grid_baseline(x, wl, det, alpha, delta, f1, ntempl):
+    """cpu_baseline of a grid workload: ntempl templates of the grid (sky-major)
+    dealt over the host cores, each worker preparing the segment itself."""
+    items = [(float(alpha[s]), float(delta[s]), float(f1[m]), None) for s in range(len(alpha))
+             for m in range(len(f1))][:ntempl]
+    pool = OraclePool()
+    try:
+        n, secs = pool.templates([(x, wl, det, it) for it in pool.deal(items)])
+        return pool.record(n / secs, "templates/s", "%d templates (FFT mode) over %d worker processes, each with its "
+                           "own segment preparation, %.1f s" % (n, pool.cores, secs))
+    finally:
+        pool.close()
 
 
 def _grid_config(wl, nsky, nspin, world):
@@ -294,15 +383,19 @@ def _lattice_config(wl, nsky, nspin, world):
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle as it stands, on the host cores, each step a
-    bounded sample of the workload (grid workloads: segment preparation plus a few
-    templates; batches: preparation plus one template of each segment kind; the fine
-    search: one exact-F pass with gradient and Hessian, 1/21 of a candidate's work)."""
+    """Reference arm: the CPU oracle as it stands, on every host core (one worker
+    process per core), each step a bounded sample of the workload dealt over the
+    workers, each worker preparing its segment itself (grid and lattice workloads:
+    templates of the grid; batches: one template of each segment kind per worker;
+    the fine search: exact-F passes with gradient and Hessian, 1/21 of a
+    candidate's climb each)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import earth as oe, refine as orf, response as orsp
+    from oracle import earth as oe, response as orsp
     metric, unit = metric_name(args.workload), "templates/s"
+    pool = OraclePool()
+    C = pool.cores
     if args.workload in W.BATCHES:
         b = W.BATCHES[args.workload]
         det = W.detector_for(b)
@@ -311,40 +404,41 @@ def run_reference(args):
             kinds.setdefault((wl.days, wl.nfft), (wl, float(t0)))
         a_all, d_all = W.sky_grid(b.nsky)
         f1 = W.spin_grid(b.nspin, *b.f1_range)
-        data = []
+        tasks = []
         for wl, t0 in kinds.values():
             dk = oe.detector_at_epoch(det, t0)
             x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, dk, wl.sigma)).astype(np.float32)
-            data.append((x, wl, dk))
+            tasks += [(x, wl, dk, [(float(a_all[i % b.nsky]), float(d_all[i % b.nsky]), float(f1[0]), None)])
+                      for i in range(C)]
 
         def sample():
-            return sum(cpu_oracle_rate(x, wl, dk, a_all[:1], d_all[:1], f1[:1], 1)[2] for x, wl, dk in data)
+            return pool.templates(tasks)[0]
         nsub = min(args.nsky or 64, b.nsky)
         config = {"workload": args.workload, "segments": len(b.segments()),
                   "segment_kinds": [list(p) for p in b.parts], "dt": b.dt, "nsky": nsub, "nsky_lattice": b.nsky,
                   "nspin": b.nspin, "templates_per_gpu": len(b.segments()) * nsub * b.nspin, "F_thr": b.F_thr,
                   "F_written": False, "l2": "flushed between timed steps (256 MiB write)",
                   "parallelism": "sky shards x%d" % args.gpus, "graph": "one CUDA graph per batch, two branches"}
-        what = "one template of each of the %d segment kinds with its preparation" % len(data)
+        what = "one template of each of the %d segment kinds with its preparation, on each of %d workers" % (
+            len(kinds), C)
         per_unit = 1.0
     elif args.workload == "lattice_2d":
-        from oracle import fstat as ofs, grid as og, resample as ors
+        from oracle import grid as og
         wl = W.WORKLOADS["grid_2d"]
         det = W.detector_for(wl)
-        x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float64)
+        x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float32)
         G = og.linear_model_fisher(wl.n, wl.dt, det)
         B, _, _ = og.constrained_lattice(G, LATTICE_MATCH, 2 * math.pi / (wl.nfft * wl.dt))
         T = og.lattice_templates(B, det, wl.fl, wl.nfft, wl.dt, *wl.f1_range, box=LATTICE_BOX)
-        tm = [(al, de, fr, dr) for al, de, rows in T for fr, dr, _ in rows]
-        per_step = 16
+        tm = [(float(al), float(de), float(fr), float(dr)) for al, de, rows in T for fr, dr, _ in rows]
+        per_worker = 16
+        tasks = [(x, wl, det, it) for it in pool.deal(tm[:per_worker * C])]
 
         def sample():
-            so = ors.Segment(x.astype(np.float32).astype(np.float64), wl.dt)
-            for al, de, fr, dr in tm[:per_step]:
-                ofs.fstat(so, al, de, fr, wl.fl, det, wl.S0, wl.nfft, bin_offset=dr)
-            return per_step
+            return pool.templates(tasks)[0]
         config = _lattice_config(wl, len(T), max(len(r) for _, _, r in T), args.gpus)
-        what = "segment preparation + %d lattice templates (FFT mode)" % per_step
+        what = "%d lattice templates (FFT mode) over %d workers, each with its own segment preparation" % (
+            min(len(tm), per_worker * C), C)
         per_unit = 1.0
     elif args.workload == "refine_2d":
         wl = W.WORKLOADS["grid_2d"]
@@ -352,15 +446,15 @@ def run_reference(args):
         x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float64)
         inj = W.injections(wl)[0]
         th = np.array([inj.f0, inj.f1, inj.alpha, inj.delta])
+        tasks = [("pass", x, wl.dt, [th], wl.fl, det, wl.S0) for _ in range(C)]
 
         def sample():
-            orf.fstat_point(x, wl.dt, th, wl.fl, det, wl.S0, grad=True, hess=True)
-            return 1
+            return pool.points(tasks)[0]
         metric, unit = METRICS["refine_2d"], "candidates/s"
         config = {"workload": "refine_2d", "n": wl.n, "candidates": args.cands, "newton_steps": 20,
                   "coarse": "grid_2d search (256 sky x 16 spindowns), strongest %d crossings" % args.cands,
                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky shards x%d" % args.gpus}
-        what = "one exact-F pass with gradient and Hessian (a candidate's climb takes 21)"
+        what = "one exact-F pass with gradient and Hessian on each of %d workers (a candidate's climb takes 21)" % C
         per_unit = 1.0 / 21.0
     else:
         wl = W.WORKLOADS[args.workload]
@@ -368,20 +462,26 @@ def run_reference(args):
         x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float32)
         alpha, delta = W.sky_grid(wl.nsky)
         f1 = W.spin_grid(wl.nspin, *wl.f1_range)
-        per_step = max(2, int(16 * 86164 / wl.n))
+        per_worker = max(1, int(16 * 86164 / wl.n))
+        items = [(float(alpha[s]), float(delta[s]), float(f1[m]), None) for s in range(len(alpha))
+                 for m in range(len(f1))][:per_worker * C]
+        tasks = [(x, wl, det, it) for it in pool.deal(items)]
 
         def sample():
-            return cpu_oracle_rate(x, wl, det, alpha, delta, f1, per_step)[2]
+            return pool.templates(tasks)[0]
         config = _grid_config(wl, wl.nsky, wl.nspin, args.gpus)
-        what = "segment preparation + %d templates (FFT mode)" % per_step
+        what = "%d templates (FFT mode) over %d workers, each with its own segment preparation" % (len(items), C)
         per_unit = 1.0
-    for _ in range(args.warmup):
-        sample()
-    t0 = time.perf_counter()
-    total = 0
-    for _ in range(args.steps):
-        total += sample()
-    wall = time.perf_counter() - t0
+    try:
+        for _ in range(args.warmup):
+            sample()
+        t0 = time.perf_counter()
+        total = 0
+        for _ in range(args.steps):
+            total += sample()
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
     value = total * per_unit / wall
     config["sample_per_step"] = what
     line = {
@@ -389,8 +489,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config,
-        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
-                         "sample": "%s per step, %d steps" % (what, args.steps)},
+        "cpu_baseline": pool.record(value, unit, "%s per step, %d steps" % (what, args.steps)),
         "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -498,26 +597,28 @@ def main_batch(args):
     if tuning:
         line["tuning"] = tuning
     if rank == 0 and not args.quick:
-        # the oracle on the host cores: segment preparation + ntk templates per segment kind
-        # (the kinds are equally frequent in the batch, so the sample follows its mix)
-        from oracle import fstat as ofs, resample as ors  # noqa: F401
-        ntk = max(1, args.cpu_templates // 8)
-        t0 = time.perf_counter()
-        done = 0
-        kinds_seen = set()
+        # the oracle on the host cores: one template of each segment kind per worker, each
+        # worker preparing its segment (the kinds are equally frequent in the batch, so the
+        # sample follows its mix)
+        from oracle import earth as oe
+        f1h = W.spin_grid(b.nspin, *b.f1_range)
+        kinds_seen, tasks = set(), []
+        pool = OraclePool()
         for i, wl in enumerate(segs_wl):
             if (wl.days, wl.nfft) in kinds_seen:
                 continue
             kinds_seen.add((wl.days, wl.nfft))
-            from oracle import earth as oe
-            r, _, n = cpu_oracle_rate(xs[i].cpu().numpy(), wl, oe.detector_at_epoch(det, float(t0s[i])),
-                                      a_all[mine][:1], d_all[mine][:1], W.spin_grid(b.nspin, *b.f1_range)[:ntk],
-                                      ntk)
-            done += n
-        secs = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": done / secs, "unit": "templates/s", "cores": 1, "kind": "oracle",
-                                "sample": "%d templates of each of the %d segment kinds, preparation included, %.1f s"
-                                          % (ntk, len(kinds_seen), secs)}
+            dk = oe.detector_at_epoch(det, float(t0s[i]))
+            xh_k = xs[i].cpu().numpy()
+            tasks += [(xh_k, wl, dk, [(float(a_all[mine][0]), float(d_all[mine][0]), float(f1h[c % len(f1h)]), None)])
+                      for c in range(pool.cores)]
+        try:
+            done, secs = pool.templates(tasks)
+            line["cpu_baseline"] = pool.record(done / secs, "templates/s",
+                                               "one template of each of the %d segment kinds on each of %d workers, "
+                                               "preparation included, %.1f s" % (len(kinds_seen), pool.cores, secs))
+        finally:
+            pool.close()
         # end to end: pinned host data of every segment -> device, load, batch, candidates -> host
         xh = [torch.empty(x.numel(), dtype=torch.float32).pin_memory() for x in xs]
         for h, x in zip(xh, xs):
@@ -638,16 +739,18 @@ def main_refine(args):
         "F_gain": {"median": float(np.median(gain)), "max": float(np.max(gain))},
     }
     if rank == 0 and not args.quick:
-        # oracle: Nelder-Mead fine search (Sec. VI.C) from the first two starting points
-        from oracle import refine as orf
-        pts0 = fs.points_from_candidates(ctx, seg, cand, 2, alpha, delta, f1).cpu().numpy()
+        # oracle: Nelder-Mead fine search (Sec. VI.C) from the first starting points, one
+        # climb per host core
+        pool = OraclePool()
+        pts0 = fs.points_from_candidates(ctx, seg, cand, min(npt, pool.cores), alpha, delta, f1).cpu().numpy()
         xh = x32.double().cpu().numpy()
-        t0 = time.perf_counter()
-        for p in pts0:
-            orf.fine_search(xh, wl.dt, p, wl.fl, det, wl.S0)
-        secs = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": len(pts0) / secs, "unit": "candidates/s", "cores": 1, "kind": "oracle",
-                                "sample": "Nelder-Mead on the exact F from 2 candidates, %.1f s" % secs}
+        try:
+            done, secs = pool.points([("climb", xh, wl.dt, list(pt), wl.fl, det, wl.S0) for pt in pool.deal(list(pts0))])
+            line["cpu_baseline"] = pool.record(done / secs, "candidates/s",
+                                               "Nelder-Mead on the exact F from %d candidates over %d workers, %.1f s"
+                                               % (done, pool.cores, secs))
+        finally:
+            pool.close()
         # end to end: candidates from the host, refined points and F back to the host
         ch = cand.cpu().pin_memory()
         ke = max(2, steps)
@@ -799,21 +902,18 @@ def main_lattice(args):
                              "note": "plain all-FP64 lattice search (own FP64 Stockham FFT), search only"}
         line["max_rel_dF_vs_fp64"] = float(((F32 - r64.F).abs() / torch.clamp(r64.F, min=1.0)).max().item())
         seg64.close()
-        from oracle import fstat as ofs, resample as ors
-        xh = x32.cpu().numpy().astype(np.float64)
-        t0 = time.perf_counter()
-        so = ors.Segment(xh, wl.dt)
-        done = 0
-        for s_ in range(nsky):
-            for m_ in range(nspin):
-                if done < args.cpu_templates:
-                    ofs.fstat(so, a[rows[s_]], d[rows[s_]], f1[rows[s_], m_], wl.fl, det, wl.S0, wl.nfft,
-                              bin_offset=off[rows[s_], m_])
-                    done += 1
-        secs = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": done / secs, "unit": "templates/s", "cores": 1, "kind": "oracle",
-                                "sample": "segment preparation + %d lattice templates (FFT mode), %.1f s"
-                                          % (done, secs)}
+        xh = x32.cpu().numpy()
+        items = [(float(a[rows[s_]]), float(d[rows[s_]]), float(f1[rows[s_], m_]), float(off[rows[s_], m_]))
+                 for s_ in range(nsky) for m_ in range(nspin)]
+        pool = OraclePool()
+        try:
+            items = items[:max(pool.cores, min(len(items), pool.cores * args.cpu_templates // 16))]
+            done, secs = pool.templates([(xh, wl, det, it) for it in pool.deal(items)])
+            line["cpu_baseline"] = pool.record(done / secs, "templates/s",
+                                               "%d lattice templates (FFT mode) over %d workers, each with its own "
+                                               "segment preparation, %.1f s" % (done, pool.cores, secs))
+        finally:
+            pool.close()
         # end to end through the public API with host buffers, as for the grid workloads
         xh_pin = torch.empty(wl.n, dtype=torch.float32).pin_memory()
         xh_pin.copy_(x32.cpu())
@@ -1107,14 +1207,12 @@ def main():
         line["max_rel_dF_vs_fp64"] = drel
         seg64.close()
         line["cufft_comparison"] = cufft_comparison(wl.nfft, nbins)
-        # the oracle on the host cores, bounded sample
-        xh = x32.cpu().numpy()
-        # bounded sample: about 10-30 s of oracle time (a template costs ~N)
-        ntc = max(2, min(args.cpu_templates, int(args.cpu_templates * 86164 / wl.n)))
-        rate, secs, done = cpu_oracle_rate(xh, wl, det, a_all[mine], d_all[mine],
-                                           W.spin_grid(wl.nspin, *wl.f1_range), ntc)
-        line["cpu_baseline"] = {"value": rate, "unit": "templates/s", "cores": 1, "kind": "oracle",
-                                "sample": "segment preparation + %d templates (FFT mode), %.1f s" % (done, secs)}
+        # the oracle on every host core, bounded sample: about 16 templates of the 2-day
+        # size per core (a template costs ~N), each worker preparing the segment itself
+        ncores = host_cores()
+        ntc = max(ncores, min(nsky * nspin, int(ncores * args.cpu_templates / 20 * 86164 / wl.n)))
+        line["cpu_baseline"] = oracle_grid_baseline(x32.cpu().numpy(), wl, det, a_all[mine], d_all[mine],
+                                                    W.spin_grid(wl.nspin, *wl.f1_range), ntc)
         line.update(grid_e2e(fs, ctx, seg, wl, x32, alpha, delta, f1, F_out, cand, ncand, cap, args.steps))
     else:
         line.setdefault("e2e", None)

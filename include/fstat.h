@@ -58,7 +58,9 @@ typedef enum {
   FS_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out              */
   FS_ERR_UNSUPPORTED = 7, /* valid request the library does not implement    */
   FS_ERR_NOMEM = 8,       /* device allocation failed                        */
-  FS_ERR_SCRATCH = 9      /* request needs more than FS_NOALLOC_SCRATCH_BYTES */
+  FS_ERR_SCRATCH = 9,     /* request needs more than FS_NOALLOC_SCRATCH_BYTES */
+  FS_ERR_CORRUPT = 10     /* debug build (-DFS_DEBUG) only: a device index outside
+                             its buffer, or a workspace guard word overwritten */
 } fs_status;
 
 /* Detector site and analytic-Earth parameters, radians.
@@ -193,18 +195,24 @@ FS_API fs_status fs_seg_load(fs_seg *seg, const void *x_dev, void *stream);
  * synchronisation that cudaFree implies.
  *
  * Same arguments and results as fs_search, restricted to segments prepared
- * with FS_PREC_F32 and nbins = nfft/2 (else FS_ERR_UNSUPPORTED).  Its working
- * memory is one fixed array of FS_NOALLOC_SCRATCH_BYTES that the library
- * holds on every device where it is loaded, until the process exits; a request
- * whose per-sky arrays, transform ring and counters do not fit returns
- * FS_ERR_SCRATCH before launching anything (roughly: nfft up to 2^17).  The
- * call allocates nothing: no cudaMalloc, no cudaFree, no library allocator.
- * The first call on a device looks up the array's device address (no
- * allocation); make that first call before any stream capture.  Every call
- * shares the one array and the array keeps the last call's contents (the call
- * clears what must start at zero itself): calls whose work overlaps on the GPU,
- * from any context or stream, race with each other and must be serialised by
- * the caller. */
+ * with FS_PREC_F32 and nbins = nfft/2 (else FS_ERR_UNSUPPORTED).  It serves
+ * callers that cannot allocate device memory while they search: an application
+ * whose framework already owns the GPU's memory through its own caching pool, or
+ * a latency-bound loop that cannot absorb the device-wide synchronisation of
+ * cudaFree.  The paper has no counterpart: it is a property of this library's
+ * interface.  Its working memory is one fixed array of
+ * FS_NOALLOC_SCRATCH_BYTES that the library holds on every device where it is
+ * loaded, until the process exits; a request whose per-sky arrays, transform
+ * ring and counters do not fit returns FS_ERR_SCRATCH before launching
+ * anything (roughly: nfft up to 2^17).  The call allocates nothing: no
+ * cudaMalloc, no cudaFree, no library allocator; fs_create looks up the
+ * array's device address for its context (a lookup, no allocation).  The first
+ * launches of a process may still make the CUDA driver load the library's
+ * kernels (lazy module loading), which is the driver's own memory, not this
+ * call's.  Every call shares the one array and the array keeps the last call's
+ * contents (the call clears what must start at zero itself): calls whose work
+ * overlaps on the GPU, from any context or stream, race with each other and
+ * must be serialised by the caller. */
 #define FS_NOALLOC_SCRATCH_BYTES (16u << 20)
 FS_API fs_status fs_search_noalloc(fs_ctx *ctx, fs_seg *seg,
                                    const double *alpha_dev, const double *delta_dev, int32_t nsky,
@@ -445,12 +453,16 @@ FS_API fs_status fs_selftest_wait(fs_ctx *ctx, void *stream);
  * the device).  Kinds: 0 segment preparation (all of it), 1 per-sky
  * demodulation, 2 transform pass 1 (per-batch launches), 3 transform
  * pass 2 + F epilogue (per-batch launches) or both passes (the persistent
- * launch used for nbins = nfft/2), 4 other. */
+ * launch used for nbins = nfft/2), 4 other.
+ * workspace_bytes: device bytes the context currently holds in the search and
+ * fine-search workspaces it grows on demand (not reset; segments and the fixed
+ * array of the allocation-free searches are not included). */
 #define FS_PROF_KINDS 5
 typedef struct {
   int64_t launches;
   double ms[FS_PROF_KINDS];
   int64_t count[FS_PROF_KINDS];
+  int64_t workspace_bytes;
 } fs_stats;
 FS_API fs_status fs_set_profiling(fs_ctx *ctx, int32_t on);
 FS_API fs_status fs_get_stats(fs_ctx *ctx, fs_stats *out, int32_t reset);

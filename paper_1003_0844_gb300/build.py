@@ -65,7 +65,7 @@ def build(verbose: bool = False, extra=(), lib: str = LIB, out_dir: str = OUT_DI
     if os.path.exists(LIB_) and all(os.path.getmtime(LIB_) >= os.path.getmtime(o) for o in objs):
         return LIB_
     tmp = LIB_ + ".tmp"
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
@@ -73,5 +73,19 @@ def build(verbose: bool = False, extra=(), lib: str = LIB, out_dir: str = OUT_DI
     return LIB_
 
 
+DEBUG_DIR = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_DIR, "libfstat_debug.so")
+
+
+def build_debug(verbose: bool = False) -> str:
+    """The debug build (-DFS_DEBUG) beside the release library: the transform
+    kernels check every workspace and output index against its buffer (an index
+    outside latches FS_ERR_CORRUPT and skips the access) and the search
+    workspaces carry guard words around the transform ring and the queue
+    counters, checked after every search.  Load it with FSTAT_LIB or
+    fstat.load_library(path)."""
+    return build(verbose=verbose, extra=["-DFS_DEBUG"], lib=DEBUG_LIB, out_dir=DEBUG_DIR)
+
+
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build_debug(verbose="-v" in sys.argv) if "--debug" in sys.argv else build(verbose="-v" in sys.argv))

@@ -56,6 +56,7 @@ const char *fs_strerror(fs_status s) {
     case FS_ERR_UNSUPPORTED: return "unsupported request";
     case FS_ERR_NOMEM: return "device allocation failed";
     case FS_ERR_SCRATCH: return "request exceeds the fixed scratch array of fs_search_noalloc";
+    case FS_ERR_CORRUPT: return "debug build: an index outside its buffer or an overwritten guard word";
   }
   return "unknown status";
 }
@@ -70,6 +71,7 @@ fs_status fs_create(fs_ctx **ctx, const fs_detector *det, int32_t device) {
   c->det = *det;
   if (cudaMalloc(&c->d_flags, sizeof(uint32_t)) != cudaSuccess) { delete c; cudaGetLastError(); return FS_ERR_NOMEM; }
   if (cudaMemset(c->d_flags, 0, sizeof(uint32_t)) != cudaSuccess) { cudaFree(c->d_flags); delete c; return FS_ERR_CUDA; }
+  if (noalloc_address(&c->noalloc) != FS_OK) { cudaFree(c->d_flags); delete c; return FS_ERR_CUDA; }
   const char *bt = getenv("FSTAT_BATCH_TEMPLATES");
   if (bt && atoi(bt) > 0) c->batch_templates = atoi(bt);
   const char *gs = getenv("FSTAT_GROUP_SKIES");
@@ -214,6 +216,7 @@ fs_status fs_seg_load(fs_seg *s, const void *x_dev, void *stream) {
   if (!s || !x_dev) return FS_ERR_ARG;
   if (cudaSetDevice(s->ctx->device) != cudaSuccess) return FS_ERR_CUDA;
   cudaStream_t st = as_stream(stream);
+  NvtxRange nv("fs.prepare");
   ProfScope ps(s->ctx, PROF_PREP, st);
   fs_status r = FS_OK;
   if (s->d.precision == FS_PREC_F32) r = prepare_tables(s, st);
@@ -245,6 +248,7 @@ fs_status fs_search(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, const dou
   if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
   cudaStream_t st = as_stream(stream);
+  NvtxRange nv("fs.search");
   if (seg->d.precision == FS_PREC_F32)
     return search32(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, (float *)F_out_dev, nbins,
                     cand_dev, cand_cap, n_cand_dev, st);
@@ -286,6 +290,7 @@ fs_status fs_search_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha_dev, c
   if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
   if (seg->d.options & FS_OPT_INTERBIN) return FS_ERR_UNSUPPORTED;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  NvtxRange nv("fs.search_noalloc");
   return search32_noalloc(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, F_out_dev, nbins, cand_dev,
                           cand_cap, n_cand_dev, as_stream(stream));
 }
@@ -300,6 +305,7 @@ fs_status fs_search_lattice_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alph
   if ((int64_t)nsky * nspin > (int64_t)1 << 31) return FS_ERR_SHAPE;
   if (seg->d.options & FS_OPT_INTERBIN) return FS_ERR_UNSUPPORTED;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  NvtxRange nv("fs.search_lattice_noalloc");
   return search32_noalloc(ctx, seg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, F_out_dev, nbins, cand_dev,
                           cand_cap, n_cand_dev, as_stream(stream), offset_dev);
 }
@@ -314,6 +320,7 @@ fs_status fs_search_batch(fs_ctx *ctx, fs_seg *const *segs, int32_t nseg, const 
     if (!segs[i] || segs[i]->ctx != ctx || segs[i]->d.precision != FS_PREC_F32) return FS_ERR_ARG;
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  NvtxRange nv("fs.search_batch");
   return search32_batch(ctx, segs, nseg, alpha_dev, delta_dev, nsky, f1_dev, nspin, F_thr, cand_dev, cand_cap,
                         n_cand_dev, as_stream(stream));
 }
@@ -386,6 +393,7 @@ fs_status fs_fstat_points(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int
   if (!ctx || !seg || !pts_dev || !F_dev || seg->ctx != ctx) return FS_ERR_ARG;
   if (npt < 1) return FS_ERR_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  NvtxRange nv("fs.fstat_points");
   return fstat_points(ctx, seg, pts_dev, npt, F_dev, grad_dev, hess_dev, metric_dev, as_stream(stream));
 }
 
@@ -394,6 +402,7 @@ fs_status fs_refine(fs_ctx *ctx, fs_seg *seg, fs_point *pts_dev, int32_t npt, in
   if (!ctx || !seg || !pts_dev || !F_dev || seg->ctx != ctx) return FS_ERR_ARG;
   if (npt < 1 || nsteps < 0 || nsteps > 10000) return FS_ERR_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  NvtxRange nv("fs.refine");
   return refine_points(ctx, seg, pts_dev, npt, nsteps, F_dev, as_stream(stream));
 }
 
@@ -422,6 +431,7 @@ fs_status fs_sync_status(fs_ctx *ctx, void *stream) {
   uint32_t f = 0;
   if (cudaMemcpy(&f, ctx->d_flags, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess) return FS_ERR_CUDA;
   if (f) cudaMemset(ctx->d_flags, 0, sizeof(uint32_t));
+  if (f & ERRF_CORRUPT) return FS_ERR_CORRUPT;
   if (f & ERRF_TIMEOUT) return FS_ERR_TIMEOUT;
   if (f & ERRF_NONFINITE) return FS_ERR_NONFINITE;
   if (f & ERRF_CAPACITY) return FS_ERR_CAPACITY;
@@ -440,6 +450,9 @@ fs_status fs_get_stats(fs_ctx *ctx, fs_stats *out, int32_t reset) {
   if (cudaDeviceSynchronize() != cudaSuccess) return FS_ERR_CUDA;
   memset(out, 0, sizeof(*out));
   out->launches = ctx->launches;
+  int64_t wb = (int64_t)(ctx->ws64_bytes + ctx->scratch_bytes + ctx->rws_bytes);
+  for (int i = 0; i < fs_ctx::kWsSlots; i++) wb += (int64_t)ctx->ws_bytes[i];
+  out->workspace_bytes = wb;
   for (const auto &r : ctx->recs) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return FS_ERR_CUDA;

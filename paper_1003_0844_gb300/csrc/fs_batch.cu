@@ -272,6 +272,7 @@ fs_status autotune32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double
     if (cudaStreamSynchronize(st) != cudaSuccess) { r = FS_ERR_CUDA; break; }
     uint32_t fl = 0;
     if ((r = read_clear_flags(ctx, &fl)) != FS_OK) break;
+    if (fl & ERRF_CORRUPT) { r = FS_ERR_CORRUPT; break; }
     if (fl & ERRF_TIMEOUT) { r = FS_ERR_TIMEOUT; break; }
     if (fl & ERRF_NONFINITE) { r = FS_ERR_NONFINITE; break; }
     cudaEventRecord(e0, st);

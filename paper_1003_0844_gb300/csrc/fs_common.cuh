@@ -22,7 +22,29 @@ constexpr double kMaxDelay = 500.0;                // bound on |phi_m| [s] (AU/c
 constexpr double kMaxDelayEph = 600.0;             // bound on |r_d/c| [s] accepted from a caller's table
 
 // Device-side error bits latched in the context flag word.
-enum : uint32_t { ERRF_CAPACITY = 1u, ERRF_NONFINITE = 2u, ERRF_TIMEOUT = 4u };
+enum : uint32_t { ERRF_CAPACITY = 1u, ERRF_NONFINITE = 2u, ERRF_TIMEOUT = 4u, ERRF_CORRUPT = 8u };
+
+// Debug builds (-DFS_DEBUG): the transform kernels check every workspace and
+// output index against the extent of its buffer; an index outside [0, limit)
+// latches ERRF_CORRUPT and the access is skipped (no trap, the context stays
+// usable).  Release builds compile the checks out.
+#ifdef FS_DEBUG
+constexpr bool kDebug = true;
+#else
+constexpr bool kDebug = false;
+#endif
+__device__ __forceinline__ bool dbg_in(int64_t i, int64_t limit, uint32_t *flags) {
+  if constexpr (kDebug) {
+    if (i < 0 || i >= limit) {
+      atomicOr(flags, ERRF_CORRUPT);
+      return false;
+    }
+  }
+  return true;
+}
+// Guard words around debug-build workspace buffers.
+constexpr uint32_t kGuardWord = 0xA5C3E10Fu;
+constexpr size_t kGuardBytes = 256;
 
 // ------------------------------------------------------------------ double-float (df32) arithmetic
 // A value is represented as hi + lo with |lo| <= ulp(hi)/2.  The error-free

@@ -5,6 +5,8 @@
 #include <unordered_set>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fs_common.cuh"
 
 struct fs_ctx {
@@ -25,6 +27,9 @@ struct fs_ctx {
   // fine-search workspace
   size_t rws_bytes = 0;
   void *rws = nullptr;
+  // device address of the fixed array of the allocation-free searches, looked up
+  // for this context by fs_create (the address belongs to the device's context)
+  unsigned char *noalloc = nullptr;
   // tuning knobs (templates per batch, skies per group)
   int batch_templates = 16;
   int group_skies = 256;
@@ -124,6 +129,9 @@ cudaError_t selftest_wait(uint32_t *flags, cudaStream_t st);
 fs_status search32_lattice(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
                            const double *f1, const double *offset, int nspin, float thr, float *F, int64_t nbins,
                            fs_candidate *cand, int64_t cap, int64_t *ncand, cudaStream_t st);
+// Device address of the fixed array of the allocation-free searches (no allocation;
+// called by fs_create with the context's device current).
+fs_status noalloc_address(unsigned char **addr);
 fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,
                            const double *f1, int nspin, float thr, float *F, int64_t nbins, fs_candidate *cand,
                            int64_t cap, int64_t *ncand, cudaStream_t st, const double *offset = nullptr);
@@ -159,6 +167,17 @@ struct ProfScope {
       c->recs.push_back({kind, a, b});
     }
   }
+};
+
+// NVTX range over the host-side enqueue of one stage ("fs.prepare",
+// "fs.demodulate", "fs.transform", ...): a profiler or tracer attached through
+// NVTX sees the stages on the host timeline and can filter launches by them;
+// without one the calls do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // Workspace helper: grow *buf to at least `bytes` (synchronising `st` first).

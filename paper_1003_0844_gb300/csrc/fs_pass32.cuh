@@ -68,6 +68,9 @@ struct Pass1Args {
   // lattice templates (LAT items): f1df and the bin offset d per template of the group
   // (index sky * nspin + spin); the chirp gains exp(-2 pi i d j / Nfft)
   const double *bin_offset;
+  // extents checked by debug builds: Z ring and per-sky series (elements), error flags
+  int64_t z_elems, yq_elems;
+  uint32_t *flags;
 };
 
 // CW columns per CTA; a warp holds CW columns x 2 signals x TPW sub-DFT threads.
@@ -116,11 +119,15 @@ __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, i
     float2 qv[AM / 2];
     sfor<0, AM / 2>([&](auto ap) {
       const int my = Q * (2 * ap + sig) + b;
-      qv[ap] = (my < n1max) ? qq[my * N2 + n2] : make_float2(0.f, 0.f);
+      qv[ap] = (my < n1max && dbg_in(sky * A.sky_stride + my * N2 + n2, A.yq_elems, A.flags)) ? qq[my * N2 + n2]
+                                                                                            : make_float2(0.f, 0.f);
     });
     sfor<0, P>([&](auto a) {
       const int na = Q * a + b;
-      if constexpr (a < AM) v[s * P + a] = (na < n1max) ? y[na * N2 + n2] : make_float2(0.f, 0.f);
+      if constexpr (a < AM)
+        v[s * P + a] = (na < n1max && dbg_in(sky * A.sky_stride + na * N2 + n2, A.yq_elems, A.flags))
+                           ? y[na * N2 + n2]
+                           : make_float2(0.f, 0.f);
       else v[s * P + a] = make_float2(0.f, 0.f);
     });
     sfor<0, AM / 2>([&](auto ap) {
@@ -174,7 +181,10 @@ __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, i
     v[d] = cmul(v[d], wt);
   });
   float2 *Zs = A.Z + ((int64_t)zs * 2 + sig) * nf;
-  sfor<0, Q>([&](auto d) { Zs[(int64_t)(t + P * d) * N2 + n2] = v[d]; });
+  sfor<0, Q>([&](auto d) {
+    if (dbg_in(((int64_t)zs * 2 + sig) * nf + (int64_t)(t + P * d) * N2 + n2, A.z_elems, A.flags))
+      Zs[(int64_t)(t + P * d) * N2 + n2] = v[d];
+  });
 }
 
 template <int P, int Q, int CW, int AM, int VS>
@@ -210,6 +220,8 @@ struct Pass2Args {
   int64_t cap;
   unsigned long long *ncand;
   uint32_t *flags;
+  // extents checked by debug builds: Z ring and F from A.F (elements)
+  int64_t z_elems, f_elems;
 };
 
 // One pass-2 work item: template tm (within the group), row tile rt, reading Z
@@ -259,9 +271,15 @@ __device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int 
   constexpr int L2 = P * Q;
   const int64_t N1 = N1T ? (int64_t)N1T : (int64_t)A.N1;
   const int64_t nfft = N1T ? (int64_t)N1T * L2 : A.nfft;
-  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * nfft + (int64_t)k1 * L2;
+  const int64_t zoff = ((int64_t)zs * 2 + sig) * nfft + (int64_t)k1 * L2;
+  const float2 *z = A.Z + zoff;
   float2 v[Q];
-  sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = __ldcg(z + Q * a + t + P * s); }); });
+  sfor<0, S>([&](auto s) {
+    sfor<0, P>([&](auto a) {
+      v[s * P + a] = dbg_in(zoff + Q * a + t + P * s, A.z_elems, A.flags) ? __ldcg(z + Q * a + t + P * s)
+                                                                          : make_float2(0.f, 0.f);
+    });
+  });
   float2 *xw = work + w * XW;
   sfor<0, S>([&](auto s) {
     const int b = t + P * s;
@@ -270,7 +288,9 @@ __device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int 
     sfor<0, P>([&](auto c) { xw[X::at(c, b)] = v[s * P + c]; });
   });
   __syncwarp();
-  if constexpr (!XOUT) discard_row<L2, 32>(z, t);
+  if constexpr (!XOUT) {
+    if (dbg_in(zoff + L2 - 1, A.z_elems, A.flags)) discard_row<L2, 32>(z, t);
+  }
   sfor<0, Q>([&](auto bb) { v[bb] = xw[X::at(t, bb)]; });
   __syncthreads();  // every warp is done with the exchange area (reused for the F tile)
   dft_inplace<Q, Q, D>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)
@@ -320,8 +340,8 @@ __device__ __forceinline__ void pass2_item_wide(const Pass2Args &A, int tm, int 
   float *Fo = VS == 0 ? A.F + (int64_t)tm * A.nbins + rt * R : A.F + (int64_t)tr * A.nbins + par;
   for (int idx = threadIdx.x; idx < K2 * R; idx += blockDim.x) {
     const int k2 = idx / R, r = idx - k2 * R;
-    if constexpr (VS == 0) __stcs(Fo + r + N1 * k2, Fs[k2 * (R + 1) + r]);
-    else __stcs(Fo + ((rt * R + r + N1 * k2) << VS), Fs[k2 * (R + 1) + r]);
+    const int64_t fo = VS == 0 ? r + N1 * k2 : ((rt * R + r + N1 * k2) << VS);
+    if (dbg_in((Fo - A.F) + fo, A.f_elems, A.flags)) __stcs(Fo + fo, Fs[k2 * (R + 1) + r]);
   }
 }
 
@@ -348,9 +368,15 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
   constexpr int L2 = P * Q;
   const int64_t N1 = N1T ? (int64_t)N1T : (int64_t)A.N1;
   const int64_t nfft = N1T ? (int64_t)N1T * L2 : A.nfft;
-  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * nfft + (int64_t)k1 * L2;
+  const int64_t zoff = ((int64_t)zs * 2 + sig) * nfft + (int64_t)k1 * L2;
+  const float2 *z = A.Z + zoff;
   float2 v[Q];
-  sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = __ldcg(z + Q * a + t + P * s); }); });
+  sfor<0, S>([&](auto s) {
+    sfor<0, P>([&](auto a) {
+      v[s * P + a] = dbg_in(zoff + Q * a + t + P * s, A.z_elems, A.flags) ? __ldcg(z + Q * a + t + P * s)
+                                                                          : make_float2(0.f, 0.f);
+    });
+  });
   float2 *xw = work + (w * 2 * G + (sig + 2 * gr)) * XW;
   sfor<0, S>([&](auto s) {
     const int b = t + P * s;
@@ -360,7 +386,9 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
     sfor<0, P>([&](auto c) { xw[X::at(c, b)] = v[s * P + c]; });
   });
   __syncwarp();
-  if constexpr (!XOUT) discard_row<L2, T>(z, t);
+  if constexpr (!XOUT) {
+    if (dbg_in(zoff + L2 - 1, A.z_elems, A.flags)) discard_row<L2, T>(z, t);
+  }
   sfor<0, Q>([&](auto bb) { v[bb] = xw[X::at(t, bb)]; });
   if constexpr (ALIAS_F) __syncthreads();  // every warp is done with the exchange area
   dft_inplace<Q, Q, (FULLBINS ? Q : Q / 2)>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)
@@ -410,8 +438,8 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
   constexpr int K2 = D * P;
   for (int idx = threadIdx.x; idx < K2 * R; idx += blockDim.x) {
     const int k2 = idx / R, r = idx - k2 * R;
-    if constexpr (VS == 0) __stcs(Fo + r + N1 * k2, Fs[k2 * (R + 1) + r]);
-    else __stcs(Fo + ((rt * R + r + N1 * k2) << VS), Fs[k2 * (R + 1) + r]);
+    const int64_t fo = VS == 0 ? r + N1 * k2 : ((rt * R + r + N1 * k2) << VS);
+    if (dbg_in((Fo - A.F) + fo, A.f_elems, A.flags)) __stcs(Fo + fo, Fs[k2 * (R + 1) + r]);
   }
 }
 
@@ -445,9 +473,15 @@ __device__ __forceinline__ void pass2_item_ib(const Pass2Args &A, int tm, int zs
   constexpr int L2 = P * Q;
   const int64_t N1 = A.N1, nfft = A.nfft;
   const int tiles2 = (int)(N1 / R);
-  const float2 *z = A.Z + ((int64_t)zs * 2 + sig) * nfft + (int64_t)k1 * L2;
+  const int64_t zoff = ((int64_t)zs * 2 + sig) * nfft + (int64_t)k1 * L2;
+  const float2 *z = A.Z + zoff;
   float2 v[Q];
-  sfor<0, S>([&](auto s) { sfor<0, P>([&](auto a) { v[s * P + a] = __ldcg(z + Q * a + t + P * s); }); });
+  sfor<0, S>([&](auto s) {
+    sfor<0, P>([&](auto a) {
+      v[s * P + a] = dbg_in(zoff + Q * a + t + P * s, A.z_elems, A.flags) ? __ldcg(z + Q * a + t + P * s)
+                                                                          : make_float2(0.f, 0.f);
+    });
+  });
   float2 *eb = A.X + (int64_t)tm * A.eb_stride;
   if (rt == 0 && (WIDE ? w < 2 : w == 0)) {  // row k1 = 0 (gr = 0): X(Nfft/2); n2 = Q a + t + P s has t's parity
     float2 sum = make_float2(0.f, 0.f);
@@ -523,7 +557,8 @@ __device__ __forceinline__ void pass2_item_ib(const Pass2Args &A, int tm, int zs
   float *Fout = A.F + (int64_t)tm * A.nbins + 2 * rt * R;
   for (int idx = threadIdx.x; idx < 2 * R * DP; idx += blockDim.x) {
     const int k2 = idx / (2 * R), q = idx - k2 * (2 * R);
-    if (q != 2 * R - 1) __stcs(Fout + q + 2 * N1 * k2, Fs[k2 * FP + q]);
+    if (q != 2 * R - 1 && dbg_in((Fout - A.F) + q + 2 * N1 * k2, A.f_elems, A.flags))
+      __stcs(Fout + q + 2 * N1 * k2, Fs[k2 * FP + q]);
   }
 }
 
@@ -850,6 +885,8 @@ struct Ws32 {
   unsigned *counters;
   int64_t stride;
   int nblk_a1;
+  // debug builds: guard words before and after the Z ring and after the counters
+  uint32_t *guard[3];
 };
 fs_status config32(const fs_ctx *ctx, const fs_seg *seg, int nsky, int64_t nbins, Cfg32 *c);
 // Lay out (and, if may_alloc, grow) context workspace `slot` for a search.

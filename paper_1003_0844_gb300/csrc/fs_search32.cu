@@ -8,7 +8,6 @@
 // the spindown phase argument Q_j = t_j^2/2 + t_j phi_m(t_j) (Eq. phas) kept
 // as a double-float.  Output per sky: y^a_j, y^b_j (float2) and Q_j.
 #include <stdio.h>
-#include <mutex>
 #include "fs_pass32.cuh"
 
 namespace fs {
@@ -364,12 +363,16 @@ fs_status workspace32(fs_ctx *ctx, int slot, const fs_seg *seg, const Cfg32 &c, 
   size_t o_ab = off; off = align256(off + sizeof(double2) * G);
   size_t o_pa = off; off = align256(off + sizeof(float2) * (size_t)nblk * G);
   size_t o_f1 = off; off = align256(off + sizeof(float2) * (size_t)nsky * nspin);
+  const size_t gb = kDebug ? kGuardBytes : 0;  // debug builds: guard words around the ring
+  size_t o_g0 = off; off = align256(off + gb);
   size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)c.nsub * c.B);
+  size_t o_g1 = off; off = align256(off + gb);
   const size_t xn = !c.interbin ? 0
                     : c.persistent ? vt * (size_t)ib_edge_stride(c.sh.N1, c.sh.N2, kPersistThreads)
                                    : 2 * (size_t)c.nsub * c.B;
   size_t o_x = off; off = align256(off + sizeof(float2) * xn);
   size_t o_ct = off; off = align256(off + sizeof(unsigned) * (1 + 2 * vt));
+  size_t o_g2 = off; off = align256(off + gb);
   if (may_alloc) {
     fs_status s = ensure_buffer(&ctx->ws[slot], &ctx->ws_bytes[slot], off, st);
     if (s != FS_OK) return s;
@@ -390,7 +393,28 @@ fs_status workspace32(fs_ctx *ctx, int slot, const fs_seg *seg, const Cfg32 &c, 
   w->counters = (unsigned *)(base + o_ct);
   w->stride = stride;
   w->nblk_a1 = nblk;
+  w->guard[0] = kDebug ? (uint32_t *)(base + o_g0) : nullptr;
+  w->guard[1] = kDebug ? (uint32_t *)(base + o_g1) : nullptr;
+  w->guard[2] = kDebug ? (uint32_t *)(base + o_g2) : nullptr;
   return FS_OK;
+}
+
+// Debug builds: fill the guard words of a workspace before a search and check
+// them after it (an overwritten word latches ERRF_CORRUPT).
+__global__ void k_guard(uint32_t *g0, uint32_t *g1, uint32_t *g2, int check, uint32_t *flags) {
+  constexpr int W = (int)(kGuardBytes / sizeof(uint32_t));
+  uint32_t *g[3] = {g0, g1, g2};
+  for (int i = threadIdx.x; i < 3 * W; i += blockDim.x) {
+    uint32_t *p = g[i / W] + (i % W);
+    if (!check) *p = kGuardWord;
+    else if (*p != kGuardWord) atomicOr(flags, ERRF_CORRUPT);
+  }
+}
+
+static cudaError_t guards(const Ws32 &w, bool check, uint32_t *flags, cudaStream_t st) {
+  if (!w.guard[0]) return cudaSuccess;
+  k_guard<<<1, 256, 0, st>>>(w.guard[0], w.guard[1], w.guard[2], check ? 1 : 0, flags);
+  return cudaGetLastError();
 }
 
 static DemodArgs demod_args(const fs_seg *seg, const Ws32 &w, int64_t npad) {
@@ -449,6 +473,9 @@ static void pass_args(const fs_seg *seg, const Cfg32 &c, const Ws32 &w, int nspi
   p1->vshift = c.vshift;
   p1->inv_nfft_total = (float)(1.0 / (double)seg->g.nfft);
   p1->Z = w.Z;
+  p1->z_elems = 2 * c.nsub * (int64_t)c.B;
+  p1->yq_elems = w.stride * (int64_t)c.G;
+  p1->flags = flags;
   *p2 = Pass2Args{};
   p2->Z = w.Z;
   p2->N1 = c.sh.N1;
@@ -463,6 +490,7 @@ static void pass_args(const fs_seg *seg, const Cfg32 &c, const Ws32 &w, int nspi
   p2->cap = cap;
   p2->ncand = (unsigned long long *)ncand;
   p2->flags = flags;
+  p2->z_elems = 2 * c.nsub * (int64_t)c.B;
 }
 
 fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, const double *alpha,
@@ -472,6 +500,7 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
   if (lat_offset && !c.persistent) return FS_ERR_UNSUPPORTED;
   const int64_t n = seg->g.n;
   if (cudaMemsetAsync(ncand, 0, sizeof(int64_t), st) != cudaSuccess) return FS_ERR_CUDA;
+  if (guards(w, false, ctx->d_flags, st) != cudaSuccess) return FS_ERR_CUDA;
   DemodArgs DA = demod_args(seg, w, c.npad);
   {
     ProfScope ps(ctx, PROF_OTHER, st);
@@ -488,10 +517,11 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
     const int gs = (nsky - g0) < c.G ? (nsky - g0) : c.G;
     DA.sky = w.skyc + g0;
     {
-      ProfScope ps(ctx, PROF_DEMOD, st);
-      if (launch_demod(DA, gs, w.nblk_a1, seg->d.interp, st) != cudaSuccess) return FS_ERR_CUDA;
-    }
-    {
+      NvtxRange nv("fs.demodulate");
+      {
+        ProfScope ps(ctx, PROF_DEMOD, st);
+        if (launch_demod(DA, gs, w.nblk_a1, seg->d.interp, st) != cudaSuccess) return FS_ERR_CUDA;
+      }
       ProfScope ps(ctx, PROF_OTHER, st);
       k_demod_finalize<<<gs, 256, 0, st>>>(w.partial, w.nblk_a1, n, seg->g.dt, seg->g.S0, w.norm, w.ab2);
     }
@@ -503,6 +533,7 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
       p1.bin_offset = lat_offset + (int64_t)g0 * nspin;
     }
     p2.F = F ? F + (int64_t)g0 * nspin * nbins : nullptr;
+    p2.f_elems = (int64_t)(nsky - g0) * nspin * nbins;
     if (c.persistent) {
       QueueArgs qa{};
       qa.ntm = ntm;
@@ -517,6 +548,7 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
       if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)ntm), st) != cudaSuccess)
         return FS_ERR_CUDA;
       {
+        NvtxRange nv("fs.transform");
         ProfScope ps(ctx, PROF_PASS2, st);
         if (c.interbin) {
           p2.X = w.X;
@@ -532,6 +564,7 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
       ctx->launches += 1;
       continue;
     }
+    NvtxRange nv("fs.transform");
     for (int b0 = 0; b0 < ntm; b0 += c.B) {
       const int nb = (ntm - b0) < c.B ? (ntm - b0) : c.B;
       p1.tmpl0 = b0;
@@ -553,6 +586,7 @@ fs_status search32_run(fs_ctx *ctx, fs_seg *seg, const Cfg32 &c, const Ws32 &w, 
       ctx->launches += 2;
     }
   }
+  if (guards(w, true, ctx->d_flags, st) != cudaSuccess) return FS_ERR_CUDA;
   return FS_OK;
 }
 
@@ -626,27 +660,20 @@ fs_status demod32_debug(fs_ctx *ctx, fs_seg *seg, double alpha, double delta, do
 
 // ------------------------------------------------------------------ allocation-free search
 // The working memory of fs_search_noalloc: one fixed array per device, alive
-// until the process exits.  Host code never dereferences the symbol; it looks up
-// the array's device address once per device and passes that address on.
+// until the process exits.  In host code the symbol is only a host-side stand-in
+// for the array: fs_create looks up its device address once for each context,
+// with the context's device current, and the searches pass that address on.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FS_NOALLOC_SCRATCH_BYTES];
 
-static std::mutex g_noalloc_mu;
-static unsigned char *g_noalloc_addr[256];
-
-static fs_status noalloc_scratch(unsigned char **out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return FS_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return FS_ERR_CUDA;
-    }
-    g_noalloc_addr[dev] = (unsigned char *)p;
+fs_status noalloc_address(unsigned char **addr) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    *addr = nullptr;
+    return FS_ERR_CUDA;
   }
-  *out = g_noalloc_addr[dev];
+  *addr = (unsigned char *)p;
   return FS_OK;
 }
 
@@ -679,9 +706,8 @@ fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
   const size_t o_z = off; off = align256(off + sizeof(float2) * 2 * (size_t)seg->g.nfft * slots);
   const size_t o_ct = off; off = align256(off + sizeof(unsigned) * (1 + 2 * (size_t)nspin));
   if (off > (size_t)FS_NOALLOC_SCRATCH_BYTES) return FS_ERR_SCRATCH;
-  unsigned char *base = nullptr;
-  fs_status s = noalloc_scratch(&base);
-  if (s != FS_OK) return s;
+  unsigned char *base = ctx->noalloc;
+  if (!base) return FS_ERR_CUDA;
   Ws32 w{};
   w.skyc = (SkyConst32 *)(base + o_sky);
   w.ya = (float2 *)(base + o_ya);
@@ -706,9 +732,20 @@ fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
       if (f1_to_df32(f1 + (int64_t)g0 * nspin, nspin, w.f1df, st) != cudaSuccess) return FS_ERR_CUDA;
       ctx->launches += 1;
     }
-    if (sky_constants32(alpha + g0, delta + g0, 1, seg->g, ctx->det, w.skyc, st) != cudaSuccess) return FS_ERR_CUDA;
-    if (launch_demod(DA, 1, nblk, seg->d.interp, st) != cudaSuccess) return FS_ERR_CUDA;
-    k_demod_finalize<<<1, 256, 0, st>>>(w.partial, nblk, n, seg->g.dt, seg->g.S0, w.norm, w.ab2);
+    {
+      ProfScope ps(ctx, PROF_OTHER, st);
+      if (sky_constants32(alpha + g0, delta + g0, 1, seg->g, ctx->det, w.skyc, st) != cudaSuccess)
+        return FS_ERR_CUDA;
+    }
+    {
+      NvtxRange nv("fs.demodulate");
+      ProfScope ps(ctx, PROF_DEMOD, st);
+      if (launch_demod(DA, 1, nblk, seg->d.interp, st) != cudaSuccess) return FS_ERR_CUDA;
+    }
+    {
+      ProfScope ps(ctx, PROF_OTHER, st);
+      k_demod_finalize<<<1, 256, 0, st>>>(w.partial, nblk, n, seg->g.dt, seg->g.S0, w.norm, w.ab2);
+    }
     Cfg32 c{};
     c.sh = sh;
     c.vshift = 0;
@@ -721,6 +758,9 @@ fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
     p2.sky_base = g0;
     p2.F = F ? F + (int64_t)g0 * nspin * nbins : nullptr;
     p2.nbins = nbins;
+    p1.z_elems = p2.z_elems = 2 * seg->g.nfft * (int64_t)slots;
+    p1.yq_elems = stride;
+    p2.f_elems = (int64_t)(nsky - g0) * nspin * nbins;
     QueueArgs qa{};
     qa.ntm = nspin;
     queue_tiles(sh.N1, sh.N2, kPersistThreads, &qa.tiles1, &qa.tiles2);
@@ -733,11 +773,15 @@ fs_status search32_noalloc(fs_ctx *ctx, fs_seg *seg, const double *alpha, const 
     // the array keeps the previous call's contents: the queue counters start at zero
     if (cudaMemsetAsync(w.counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)nspin), st) != cudaSuccess)
       return FS_ERR_CUDA;
-    if (offset) {
-      p1.bin_offset = offset + (int64_t)g0 * nspin;
-      if (dispatch_passes_lat(sh.N1, sh.N2, p1, p2, qa, st) != cudaSuccess) return FS_ERR_CUDA;
-    } else if (dispatch_passes(sh.N1, sh.N2, p1, p2, qa, st) != cudaSuccess) {
-      return FS_ERR_CUDA;
+    {
+      NvtxRange nv("fs.transform");
+      ProfScope ps(ctx, PROF_PASS2, st);
+      if (offset) {
+        p1.bin_offset = offset + (int64_t)g0 * nspin;
+        if (dispatch_passes_lat(sh.N1, sh.N2, p1, p2, qa, st) != cudaSuccess) return FS_ERR_CUDA;
+      } else if (dispatch_passes(sh.N1, sh.N2, p1, p2, qa, st) != cudaSuccess) {
+        return FS_ERR_CUDA;
+      }
     }
     ctx->launches += 4;
   }

@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libfstat.so")
 
 FS_OK = 0
 STATUS = {0: "FS_OK", 1: "FS_ERR_ARG", 2: "FS_ERR_SHAPE", 3: "FS_ERR_CAPACITY", 4: "FS_ERR_NONFINITE",
-          5: "FS_ERR_CUDA", 6: "FS_ERR_TIMEOUT", 7: "FS_ERR_UNSUPPORTED", 8: "FS_ERR_NOMEM", 9: "FS_ERR_SCRATCH"}
+          5: "FS_ERR_CUDA", 6: "FS_ERR_TIMEOUT", 7: "FS_ERR_UNSUPPORTED", 8: "FS_ERR_NOMEM", 9: "FS_ERR_SCRATCH",
+          10: "FS_ERR_CORRUPT"}
 PREC = {"f32": 0, "f64": 1}
 INTERP = {"spline": 0, "nearest": 1}
 EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_prepare_segment_eph", "fs_seg_destroy", "fs_seg_load", "fs_search",
@@ -56,7 +57,8 @@ class _Tuning(ctypes.Structure):
 
 
 class _Stats(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double * 5), ("count", ctypes.c_int64 * 5)]
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double * 5), ("count", ctypes.c_int64 * 5),
+                ("workspace_bytes", ctypes.c_int64)]
 
 
 class _Injection(ctypes.Structure):
@@ -195,10 +197,11 @@ class Context:
         _check(self.lib.fs_set_profiling(self.handle, 1 if on else 0), "fs_set_profiling")
 
     def stats(self, reset: bool = True) -> dict:
-        """Launch count and, with profiling on, summed event time / launches per kind."""
+        """Launch count, the bytes held by the context's workspaces and, with
+        profiling on, summed event time / launches per kind."""
         st = _Stats()
         _check(self.lib.fs_get_stats(self.handle, ctypes.byref(st), 1 if reset else 0), "fs_get_stats")
-        return {"launches": st.launches,
+        return {"launches": st.launches, "workspace_bytes": st.workspace_bytes,
                 "ms": {k: st.ms[i] for i, k in enumerate(PROF_KINDS)},
                 "count": {k: st.count[i] for i, k in enumerate(PROF_KINDS)}}
 

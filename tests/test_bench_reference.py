@@ -1,4 +1,4 @@
-"""The benchmark's reference arm (the CPU oracle on the host cores) prints one JSON
+"""The benchmark's reference arm (the CPU oracle on every host core) prints one JSON
 line with the workload's own metric, unit and config, for a single segment, a batch,
 the fine search and the constrained lattice, without a GPU."""
 import json
@@ -21,5 +21,7 @@ def test_reference_arm_line(workload, unit):
     assert d["impl"] == "reference" and d["unit"] == unit and d["value"] > 0
     assert d["higher_is_better"] is True and d["steps"] == 1
     assert d["config"]["workload"] == workload
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    # the oracle runs on every host core (one worker process per core), core count and CPU named
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+    assert d["cpu_baseline"]["cpu"] and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

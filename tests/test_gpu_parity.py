@@ -143,6 +143,20 @@ def test_search_f64_matches_oracle(fs, name):
     assert not missing and not bad
 
 
+def test_search_f64_headline_shape_matches_oracle(fs):
+    """The plain FP64 form at the 2-sidereal-day shape of the benchmark (N = 86,164,
+    Nfft = 2^18, every bin up to Nyquist): two templates against the oracle."""
+    wl, det, x, alpha, delta, f1 = make_case("grid_2d", nsky=2, nspin=1)
+    F, (cs, cm, cb, cF), ncand, status = _run(fs, wl, det, x, alpha, delta, f1, precision="f64",
+                                              x_dtype=torch.float64)
+    assert status == 0
+    assert F.shape == (2, wl.nfft // 2)
+    Fref = oracle_F(x, wl, det, alpha, delta, f1)
+    assert max_rel_dF(F, Fref) < F64_TOL
+    missing, bad = check_candidates(cs, cm, cb, cF, Fref, wl.F_thr, len(f1), rel=1e-7)
+    assert not missing and not bad
+
+
 def test_search_all_bins_and_nearest(fs):
     wl, det, x, alpha, delta, f1 = make_case("tiny")
     x32 = x.astype(np.float32).astype(np.float64)

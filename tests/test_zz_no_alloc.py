@@ -8,8 +8,12 @@ library holds per device.  This test calls it through the C ABI twice in a row
 (the array keeps the previous call's contents, so the second call checks that
 everything that must start from zero is cleared) and compares F and the
 candidates with fs_search on the same inputs, within the FP32 parity tolerance.
-It also checks that a request larger than the fixed array is refused, and the
-lattice search's allocation-free form against fs_search_lattice.
+It shows that the calls allocate nothing: on a fresh context that never ran
+fs_search, the context's workspaces do not grow and the device's free memory is
+the same before and after the calls (after one first call, which may make the
+CUDA driver load the library's kernels).  It also checks that a
+request larger than the fixed array is refused, and the lattice search's
+allocation-free form against fs_search_lattice.
 """
 import ctypes
 
@@ -31,6 +35,50 @@ def _dev(a, dtype=torch.float64):
 def _cand_set(cand, n):
     c = cand[: min(n, cand.shape[0])].cpu().numpy()
     return set(map(tuple, c[:, :3].tolist()))
+
+
+def _noalloc_call(lib, ctx, seg, a, d, f, nsky, nspin, thr, F, nbins, cand, cap, ncand, stream):
+    return lib.fs_search_noalloc(ctx.handle, seg.handle, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(d.data_ptr()),
+                                 nsky, ctypes.c_void_p(f.data_ptr()), nspin, ctypes.c_float(thr),
+                                 ctypes.c_void_p(F.data_ptr()), ctypes.c_int64(nbins),
+                                 ctypes.c_void_p(cand.data_ptr()), ctypes.c_int64(cap),
+                                 ctypes.c_void_p(ncand.data_ptr()), stream)
+
+
+def test_noalloc_search_allocates_nothing_on_a_fresh_context():
+    """A context that never ran fs_search: its workspaces do not grow across the
+    calls (segment preparation holds the only one), and the device's free memory
+    does not move between the second and the fourth call (every output is
+    allocated before the first reading)."""
+    if not torch.cuda.is_available():
+        pytest.fail("needs a CUDA device")
+    from paper_1003_0844_gb300 import build, fstat as fs
+    build.build()
+    lib = fs.load_library()
+    wl, det, x, alpha, delta, _ = make_case("single_fp64", n=30011, nfft=1 << 16, nsky=3, nspin=4)
+    f1 = np.linspace(-1e-8, 0.0, 4)
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0)
+    a, d, f = _dev(alpha), _dev(delta), _dev(f1)
+    nbins, cap = wl.nfft // 2, 1 << 12
+    outs = [(torch.empty((len(alpha) * len(f1), nbins), dtype=torch.float32, device="cuda"),
+             torch.zeros((cap, 4), dtype=torch.int32, device="cuda"),
+             torch.zeros((1,), dtype=torch.int64, device="cuda")) for _ in range(4)]
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ws0 = ctx.stats(reset=False)["workspace_bytes"]
+    free = []
+    for i, (F, cand, ncand) in enumerate(outs):
+        st = _noalloc_call(lib, ctx, seg, a, d, f, len(alpha), len(f1), 15.0, F, nbins, cand, cap, ncand, stream)
+        assert st == 0, "call %d returned %d" % (i, st)
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+    assert ctx.sync_status() == 0
+    assert ctx.stats(reset=False)["workspace_bytes"] == ws0
+    assert free[1] == free[2] == free[3], free
+    for F, cand, ncand in outs[1:]:
+        assert torch.equal(F, outs[0][0]) and int(ncand.item()) == int(outs[0][2].item())
+    seg.close()
+    ctx.close()
 
 
 def test_noalloc_search_matches_search_on_two_calls_in_a_row():

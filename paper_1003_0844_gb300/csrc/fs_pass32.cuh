@@ -358,7 +358,8 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
   constexpr int D = FULLBINS ? Q : Q / 2;  // d values with k2 = t + P d in the output band
   using X = Xch2<P, Q>;
   constexpr int XW = X::SIZE;              // exchange float2s per sub-DFT
-  float *Fs = (float *)(ALIAS_F ? work : work + WARPS * 2 * G * XW);  // [D*P][R+1]
+  constexpr int FPITCH = R + 1;  // odd pitch: conflict-free column writes
+  float *Fs = (float *)(ALIAS_F ? work : work + WARPS * 2 * G * XW);  // [D*P][FPITCH]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int t = lane % T, sig = (lane / T) & 1, gr = lane / (2 * T);
   const int row = w * G + gr;
@@ -408,7 +409,7 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
     const float Fv = mine + __shfl_xor_sync(kFull, send, T);
     const int d = dp + sig * (D / 2);
     const int k2 = t + P * d;
-    Fs[k2 * (R + 1) + row] = Fv;
+    Fs[k2 * FPITCH + row] = Fv;
     const bool hit = Fv > A.thr;
     const unsigned m = __ballot_sync(kFull, hit);
     if (m) {
@@ -431,6 +432,8 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
       }
     }
   });
+  // (storing each warp's F values directly, without the tile and its two barriers,
+  // measured 16% slower: scattered 4-byte stores)
   if (A.F == nullptr) return;
   __syncthreads();
   // VS = 0: template row plus the item's first row; VS > 0: interleaved sub-transform bins
@@ -439,7 +442,7 @@ __device__ __forceinline__ void pass2_item(const Pass2Args &A, int tm, int zs, i
   for (int idx = threadIdx.x; idx < K2 * R; idx += blockDim.x) {
     const int k2 = idx / R, r = idx - k2 * R;
     const int64_t fo = VS == 0 ? r + N1 * k2 : ((rt * R + r + N1 * k2) << VS);
-    if (dbg_in((Fo - A.F) + fo, A.f_elems, A.flags)) __stcs(Fo + fo, Fs[k2 * (R + 1) + r]);
+    if (dbg_in((Fo - A.F) + fo, A.f_elems, A.flags)) __stcs(Fo + fo, Fs[k2 * FPITCH + r]);
   }
 }
 
@@ -699,11 +702,12 @@ __global__ void __launch_bounds__(NT, MINB) k_passes(Pass1Args A1, Pass2Args A2,
         }
         __syncthreads();
       }
-      // the items take N1, N2 at run time: compiled in, they measured 5.5% slower here
       const int zs = d.tm - fdiv(d.tm, Qa.slots_fd) * Qa.slots;
+      // N1 compiled into the second pass (0.5% faster); N2 in the first pass measured slower
+      constexpr int N1C = P1 * Q1;
       if (d.is1) pass1_item<P1, Q1, CW, AM, VS, 0, LAT>(A1, d.tm, zs, d.j, work, twL);
       else if constexpr (IB) pass2_item_ib<P2, Q2, NT / 32>(A2, d.tm, zs, d.j - T1, work, twM);
-      else pass2_item<P2, Q2, NT / 32, false, true, VS, false, 0>(A2, d.tm, zs, d.j - T1, work, twM);
+      else pass2_item<P2, Q2, NT / 32, false, true, VS, false, N1C>(A2, d.tm, zs, d.j - T1, work, twM);
     }
     if (threadIdx.x == 0) {
       s_next[buf ^ 1] = nxt;

@@ -100,6 +100,7 @@ static void seg_release(fs_seg *s) {
   cudaFree(s->blu_tw);
   cudaFree(s->blu_chirp);
   cudaFree(s->etab64);
+  cudaFree(s->etab32);
   cudaFree(s->eph);
   cudaFree(s->eph0);
   cudaFree(s->eph1);

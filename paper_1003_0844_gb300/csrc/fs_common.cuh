@@ -54,34 +54,38 @@ struct df32 { float hi, lo; };
 __host__ __device__ inline df32 df_from_double(double x) {
   df32 r; r.hi = (float)x; r.lo = (float)(x - (double)r.hi); return r;
 }
-__device__ __forceinline__ df32 two_sum(float a, float b) {  // Knuth
+__host__ __device__ __forceinline__ df32 two_sum(float a, float b) {  // Knuth
   float s = a + b; float bb = s - a; float e = (a - (s - bb)) + (b - bb);
   df32 r; r.hi = s; r.lo = e; return r;
 }
-__device__ __forceinline__ df32 quick_two_sum(float a, float b) {  // requires |a| >= |b|
+__host__ __device__ __forceinline__ df32 quick_two_sum(float a, float b) {  // requires |a| >= |b|
   float s = a + b; float e = b - (s - a); df32 r; r.hi = s; r.lo = e; return r;
 }
-__device__ __forceinline__ df32 two_prod(float a, float b) {  // Dekker with FMA
+__host__ __device__ __forceinline__ df32 two_prod(float a, float b) {  // Dekker with FMA
   float p = a * b; float e = fmaf(a, b, -p); df32 r; r.hi = p; r.lo = e; return r;
 }
-__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
+__host__ __device__ __forceinline__ df32 df_add(df32 a, df32 b) {
   df32 s = two_sum(a.hi, b.hi);
   float lo = s.lo + a.lo + b.lo;
   return quick_two_sum(s.hi, lo);
 }
-__device__ __forceinline__ df32 df_add_f(df32 a, float b) {
+__host__ __device__ __forceinline__ df32 df_add_f(df32 a, float b) {
   df32 s = two_sum(a.hi, b);
   return quick_two_sum(s.hi, s.lo + a.lo);
 }
-__device__ __forceinline__ df32 df_mul(df32 a, df32 b) {
+__host__ __device__ __forceinline__ df32 df_mul(df32 a, df32 b) {
   df32 p = two_prod(a.hi, b.hi);
   float lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
   return quick_two_sum(p.hi, lo);
 }
-__device__ __forceinline__ df32 df_mul_f(df32 a, float b) {
+__host__ __device__ __forceinline__ df32 df_mul_f(df32 a, float b) {
   df32 p = two_prod(a.hi, b);
   return quick_two_sum(p.hi, fmaf(a.lo, b, p.lo));
 }
+__host__ __device__ inline df32 df_neg(df32 a) { return df32{-a.hi, -a.lo}; }
+__host__ __device__ __forceinline__ df32 df_sub(df32 a, df32 b) { return df_add(a, df_neg(b)); }
+// a * b for a df32 and an exactly representable power-of-two or small-integer factor
+__host__ __device__ __forceinline__ df32 df_scale(df32 a, float b) { return df32{a.hi * b, a.lo * b}; }
 // Fractional part of a df32 number of cycles, in [-0.5, 0.5].
 __device__ __forceinline__ float df_frac_cycles(df32 c) {
   float r = c.hi - rintf(c.hi);  // exact: c.hi and its nearest integer are close

@@ -80,6 +80,9 @@ struct fs_seg {
   // FP64 (cos, sin) of the orbital and sidereal angles on t_k = k dt, built by
   // the first fine-search call
   void *etab64 = nullptr;
+  // the same angles and the data as double-floats, with the 257-entry table of
+  // exp(-2 pi i j / 256), for the fine search's double-float kernels (same call)
+  void *etab32 = nullptr;
   // caller's position table (fs_prepare_segment_eph), else NULL:
   //   eph[2m] = (r_m, 0), eph[2m + 1] = (v_m, 0), m < n (light-seconds, SSB ecliptic frame)
   fs::dbl4 *eph = nullptr;

@@ -288,6 +288,439 @@ __global__ void __launch_bounds__(kPtThreads) k_points(SegGeom g, const dbl4 *__
   }
 }
 
+// ------------------------------------------------------------------ double-float form
+// The same sums with the analytic Earth, arranged for the FP32 pipe (the FP64 pipe
+// runs at 1/64 of its rate on this GPU).  Only the one term whose size needs more
+// than the 48 bits of a double-float stays in FP64: the orbital part of the phase,
+// (f0 + fl) (AU/c) n0 . (cos lambda, sin lambda) + f0 t, ~2.5e5 cycles, reduced to a
+// fraction of a cycle (eight FP64 operations per sample).  The diurnal delay, the
+// spindown term, exp(-2 pi i Phi) (a 257-entry table of exp(-2 pi i j/256) times a
+// short series of the remainder), a, b and the F sums are double-floats; terms that
+// enter a sum at ~1e-6 of its dominant part (the derivatives of a and b, the
+// cross terms of the Hessian) are FP32.  Sums are kept as double-floats per thread
+// and combined in FP64 in a fixed order, as in k_points.
+//
+// Layout of seg->etab32 (one allocation): L[n], T[n]: double-floats (cos hi, cos lo,
+// sin hi, sin lo) of the orbital longitude and of the sidereal angle at t_k; X[n]:
+// the data as double-floats; SC[257]: exp(-2 pi i j / 256) as (cos hi, cos lo, sin hi,
+// sin lo), j = -128..128.
+struct Etab32 {
+  float4 *L, *T;
+  float2 *X;
+  float4 *SC;
+};
+
+static size_t etab32_bytes(int64_t n) {
+  return ((sizeof(float4) * 2 * n + sizeof(float2) * n + 255) & ~(size_t)255) + sizeof(float4) * 257;
+}
+static Etab32 etab32_view(const fs_seg *seg) {
+  const int64_t n = seg->g.n;
+  char *b = (char *)seg->etab32;
+  Etab32 e;
+  e.L = (float4 *)b;
+  e.T = e.L + n;
+  e.X = (float2 *)(e.T + n);
+  e.SC = (float4 *)(b + ((sizeof(float4) * 2 * n + sizeof(float2) * n + 255) & ~(size_t)255));
+  return e;
+}
+
+__global__ void k_earth_table32(int64_t n, const dbl4 *e64, Etab32 e) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) {
+    const dbl4 v = e64[k];
+    const df32 cl = df_from_double(v.x), sl = df_from_double(v.y), ct = df_from_double(v.z),
+               st = df_from_double(v.w);
+    e.L[k] = make_float4(cl.hi, cl.lo, sl.hi, sl.lo);
+    e.T[k] = make_float4(ct.hi, ct.lo, st.hi, st.lo);
+  }
+  if (k < 257) {
+    double sj, cj;
+    sincospi((double)(k - 128) / 128.0, &sj, &cj);  // angle 2 pi (k - 128) / 256
+    const df32 c = df_from_double(cj), s = df_from_double(sj);
+    e.SC[k] = make_float4(c.hi, c.lo, s.hi, s.lo);
+  }
+}
+
+// The data as double-floats (rebuilt by every fine-search call: fs_seg_load may
+// have replaced it).
+__global__ void k_data32(int64_t n, const double *x64, float2 *X) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) {
+    const df32 v = df_from_double(x64[k]);
+    X[k] = make_float2(v.hi, v.lo);
+  }
+}
+
+// Per-point constants of the double-float kernels (from PointConst).
+struct FastConst {
+  double F0L, f0, nxA, nyA;                       // FP64 phase: f0 + fl, f0, (AU/c) nx, (AU/c) nyp
+  df32 F0L2, f0d, f1, dt, ca, sa, nxA2, nyA2, rcd, zsd;
+  df32 nxAa, nyAa, nxAd, nyAd, rcd_d, zsd_d;      // the alpha / delta derivatives of the delay
+  df32 ea[5], eb[4];
+  df32 nxAaa, nyAaa, nxAad, nyAad, nxAdd, nyAdd, rcd_dd, zsd_dd;  // second derivatives
+  float eaf[5], ebf[4], ea_d[5], eb_d[4], ea_dd[5], eb_dd[4];
+};
+
+__host__ __device__ inline FastConst fast_const(const PointConst &p, const SegGeom &g) {
+  FastConst c;
+  c.F0L = p.f0 + g.fl;
+  c.f0 = p.f0;
+  c.nxA = kAUls * p.nx;
+  c.nyA = kAUls * p.nyp;
+  c.F0L2 = df_from_double(c.F0L);
+  c.f0d = df_from_double(p.f0);
+  c.f1 = df_from_double(p.f1);
+  c.dt = df_from_double(g.dt);
+  c.ca = df_from_double(p.ca);
+  c.sa = df_from_double(p.sa);
+  c.nxA2 = df_from_double(c.nxA);
+  c.nyA2 = df_from_double(c.nyA);
+  c.rcd = df_from_double(p.rcd);
+  c.zsd = df_from_double(p.zsd);
+  c.nxAa = df_from_double(kAUls * p.nx_a);
+  c.nyAa = df_from_double(kAUls * p.nyp_a);
+  c.nxAd = df_from_double(kAUls * p.nx_d);
+  c.nyAd = df_from_double(kAUls * p.nyp_d);
+  c.rcd_d = df_from_double(p.rcd_d);
+  c.zsd_d = df_from_double(p.zsd_d);
+  c.nxAaa = df_from_double(kAUls * p.nx_aa);
+  c.nyAaa = df_from_double(kAUls * p.nyp_aa);
+  c.nxAad = df_from_double(kAUls * p.nx_ad);
+  c.nyAad = df_from_double(kAUls * p.nyp_ad);
+  c.nxAdd = df_from_double(kAUls * p.nx_dd);
+  c.nyAdd = df_from_double(kAUls * p.nyp_dd);
+  c.rcd_dd = df_from_double(p.rcd_dd);
+  c.zsd_dd = df_from_double(p.zsd_dd);
+  for (int i = 0; i < 5; i++) {
+    c.ea[i] = df_from_double(p.ea[i]);
+    c.eaf[i] = (float)p.ea[i];
+    c.ea_d[i] = (float)p.ea_d[i];
+    c.ea_dd[i] = (float)p.ea_dd[i];
+  }
+  for (int i = 0; i < 4; i++) {
+    c.eb[i] = df_from_double(p.eb[i]);
+    c.ebf[i] = (float)p.eb[i];
+    c.eb_d[i] = (float)p.eb_d[i];
+    c.eb_dd[i] = (float)p.eb_dd[i];
+  }
+  return c;
+}
+
+// 2 pi and -4 pi^2 as double-floats
+__host__ __device__ __forceinline__ df32 df_two_pi() { return df32{6.2831854820251465f, -1.7484555314695172e-07f}; }
+__host__ __device__ __forceinline__ df32 df_m4pi2() { return df32{-39.478416442871094f, -1.1614863524300745e-06f}; }
+
+// exp(-2 pi i f) = cp - i sp for a double-float f (cycles): the nearest table angle
+// j / 256 and the remainder x = 2 pi (f - j/256), |x| <= pi/256, by cos x - 1 =
+// -x^2/2 + x^4/24 and sin x - x = -x^3/6 + x^5/120 (dropped terms < 5e-15).
+__host__ __device__ __forceinline__ void df_expm(df32 f, const float4 *sc, df32 *cp, df32 *sp) {
+  // two reductions: for |f| ~ 1e5 the low word can carry the first remainder past 1/2
+  f = df_add_f(f, -rintf(f.hi));
+  f = df_add_f(f, -rintf(f.hi));
+  // the table index stays inside [-128, 128] whatever f is (the remainder is then
+  // at most slightly beyond 1/512, where the series is still accurate)
+  const float jf = fminf(fmaxf(rintf(f.hi * 256.f), -128.f), 128.f);
+  const df32 r = df_add_f(f, -jf * (1.f / 256.f));
+  const df32 x = df_mul(df_two_pi(), r);
+  const float x2 = x.hi * x.hi;
+  const float cm1 = x2 * fmaf(x2, 1.f / 24.f, -0.5f);
+  const float sm = x.hi * x2 * fmaf(x2, 1.f / 120.f, -1.f / 6.f);
+  const df32 sn = df_add_f(x, sm);
+  const float4 q = sc[(int)jf + 128];
+  const df32 C{q.x, q.y}, S{q.z, q.w};
+  *cp = df_sub(df_add_f(C, C.hi * cm1), df_mul(S, sn));  // cos(2 pi f) = C cos x - S sin x
+  *sp = df_add(df_add_f(S, S.hi * cm1), df_mul(C, sn));  // sin(2 pi f) = S cos x + C sin x
+}
+
+// Per-sample quantities shared by the double-float kernels.
+struct FastSample {
+  df32 x, t, cx, sx, c2, s2, cl, sl, phid, phi, tu, a, b, cp, sp;
+};
+
+// PHASE64: the orbital phase term in FP64 (both kernels use it: F needs it, and the
+// Hessian's terms cancel to ~1e-4 near a maximum); otherwise all double-float (error
+// ~2e-9 cycles).
+template <bool PHASE64>
+__host__ __device__ __forceinline__ FastSample fast_sample(const FastConst &c, const SegGeom &g, const dbl4 *__restrict__ etab,
+                                                  const Etab32 &et, const float4 *sc, int64_t k) {
+  FastSample s;
+  double P = 0.0;
+  if constexpr (PHASE64) {
+    const dbl4 e4 = etab[k];
+    P = fma(c.F0L, fma(c.nxA, e4.x, c.nyA * e4.y), c.f0 * ((double)k * g.dt));
+    P -= rint(P);
+  }
+  const float4 Lq = et.L[k], Tq = et.T[k];
+  const float2 Xq = et.X[k];
+  s.cl = df32{Lq.x, Lq.y};
+  s.sl = df32{Lq.z, Lq.w};
+  const df32 ct{Tq.x, Tq.y}, st{Tq.z, Tq.w};
+  s.x = df32{Xq.x, Xq.y};
+  s.t = df_mul_f(c.dt, (float)k);  // k < 2^24 is exact as a float
+  s.cx = df_add(df_mul(c.ca, ct), df_mul(c.sa, st));  // cos(alpha - theta)
+  s.sx = df_sub(df_mul(c.sa, ct), df_mul(c.ca, st));  // sin(alpha - theta)
+  s.phid = df_add(df_mul(c.rcd, s.cx), c.zsd);        // diurnal delay
+  const df32 phio = df_add(df_mul(c.nxA2, s.cl), df_mul(c.nyA2, s.sl));
+  s.phi = df_add(phio, s.phid);
+  s.tu = df_mul(s.t, df_add(df_scale(s.t, 0.5f), s.phi));  // t (t/2 + phi)
+  df32 f;
+  if constexpr (PHASE64) {
+    const float Ph = (float)P;
+    f = df_add(df32{Ph, (float)(P - (double)Ph)}, df_add(df_mul(c.F0L2, s.phid), df_mul(c.f1, s.tu)));
+  } else {
+    f = df_add(df_add(df_mul(c.F0L2, s.phi), df_mul(c.f0d, s.t)), df_mul(c.f1, s.tu));
+  }
+  df_expm(f, sc, &s.cp, &s.sp);
+  s.c2 = df_sub(df_mul(s.cx, s.cx), df_mul(s.sx, s.sx));
+  s.s2 = df_scale(df_mul(s.sx, s.cx), 2.f);
+  s.a = df_add(df_add(df_add(df_mul(c.ea[0], s.c2), df_mul(c.ea[1], s.s2)),
+                      df_add(df_mul(c.ea[2], s.cx), df_mul(c.ea[3], s.sx))), c.ea[4]);
+  s.b = df_add(df_add(df_mul(c.eb[0], s.c2), df_mul(c.eb[1], s.s2)),
+               df_add(df_mul(c.eb[2], s.cx), df_mul(c.eb[3], s.sx)));
+  return s;
+}
+
+// Sums of the double-float kernels to FP64 block partials, in a fixed order.
+template <int NQ>
+__device__ __forceinline__ void fast_reduce(const df32 *acc, int q0, int NA, double *partial, int pt) {
+  __shared__ double red[kPtThreads / 32][NQ];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; q++) {
+    double v = (double)acc[q].hi + (double)acc[q].lo;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wp][q] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < NQ; q += kPtThreads) {
+    double v = 0.0;
+    for (int w2 = 0; w2 < kPtThreads / 32; w2++) v += red[w2][q];
+    partial[((int64_t)pt * gridDim.y + blockIdx.y) * NA + q0 + q] = v;
+  }
+}
+
+// One sample's terms of F's and the gradient's accumulators (k_points_fg).
+__host__ __device__ __forceinline__ void fg_sample(const FastConst &c, const FastSample &s, df32 *acc) {
+    const df32 ua = df_mul(s.x, s.a), ub = df_mul(s.x, s.b);
+  acc[0] = df_add(acc[0], df_mul(ua, s.cp));
+  acc[1] = df_sub(acc[1], df_mul(ua, s.sp));
+  acc[2] = df_add(acc[2], df_mul(ub, s.cp));
+  acc[3] = df_sub(acc[3], df_mul(ub, s.sp));
+  // derivatives of a, b (FP32: their terms are ~1e-6 of the phase-derivative terms)
+  const float cx = s.cx.hi, sx = s.sx.hi, c2 = s.c2.hi, s2 = s.s2.hi, xf = s.x.hi;
+  const float a_a = -2.f * c.eaf[0] * s2 + 2.f * c.eaf[1] * c2 - c.eaf[2] * sx + c.eaf[3] * cx;
+  const float b_a = -2.f * c.ebf[0] * s2 + 2.f * c.ebf[1] * c2 - c.ebf[2] * sx + c.ebf[3] * cx;
+  const float a_d = c.ea_d[0] * c2 + c.ea_d[1] * s2 + c.ea_d[2] * cx + c.ea_d[3] * sx + c.ea_d[4];
+  const float b_d = c.eb_d[0] * c2 + c.eb_d[1] * s2 + c.eb_d[2] * cx + c.eb_d[3] * sx;
+  // phase derivatives [cycles per unit]: t + phi, t (t/2 + phi), w phi_alpha, w phi_delta
+  const df32 w = df_add(c.F0L2, df_mul(c.f1, s.t));
+  const df32 phia = df_sub(df_add(df_mul(c.nxAa, s.cl), df_mul(c.nyAa, s.sl)), df_mul(c.rcd, s.sx));
+  const df32 phide = df_add(df_add(df_add(df_mul(c.nxAd, s.cl), df_mul(c.nyAd, s.sl)), df_mul(c.rcd_d, s.cx)),
+                            c.zsd_d);
+  const df32 dP[4] = {df_add(s.t, s.phi), s.tu, df_mul(w, phia), df_mul(w, phide)};
+  const float da[4] = {0.f, 0.f, a_a, a_d}, db[4] = {0.f, 0.f, b_a, b_d};
+  const float cpf = s.cp.hi, spf = s.sp.hi;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    // x (da_i - 2 pi i a dP_i) (cp - i sp)
+    const df32 ra = df_mul(df_neg(df_two_pi()), df_mul(ua, dP[i]));
+    const df32 rb = df_mul(df_neg(df_two_pi()), df_mul(ub, dP[i]));
+    acc[4 + 2 * i] = df_add(acc[4 + 2 * i], df_mul(ra, s.sp));
+    acc[5 + 2 * i] = df_add(acc[5 + 2 * i], df_mul(ra, s.cp));
+    acc[12 + 2 * i] = df_add(acc[12 + 2 * i], df_mul(rb, s.sp));
+    acc[13 + 2 * i] = df_add(acc[13 + 2 * i], df_mul(rb, s.cp));
+    if (i >= 2) {
+      const float qa = xf * da[i], qb = xf * db[i];
+      acc[4 + 2 * i] = df_add_f(acc[4 + 2 * i], qa * cpf);
+      acc[5 + 2 * i] = df_add_f(acc[5 + 2 * i], -qa * spf);
+      acc[12 + 2 * i] = df_add_f(acc[12 + 2 * i], qb * cpf);
+      acc[13 + 2 * i] = df_add_f(acc[13 + 2 * i], -qb * spf);
+    }
+  }
+  acc[20] = df_add(acc[20], df_mul(s.a, s.a));
+  acc[21] = df_add(acc[21], df_mul(s.b, s.b));
+  const float af = s.a.hi, bf = s.b.hi;
+  acc[22] = df_add_f(acc[22], af * a_a);
+  acc[23] = df_add_f(acc[23], af * a_d);
+  acc[24] = df_add_f(acc[24], bf * b_a);
+  acc[25] = df_add_f(acc[25], bf * b_d);
+}
+
+// F and its gradient: accumulators [0, 26) of PtLayout (Sa, Sb, dSa_i, dSb_i, sums of
+// a^2, b^2 and a da, b db).  NA: stride of a block's partials.
+__global__ void __launch_bounds__(kPtThreads) k_points_fg(SegGeom g, const dbl4 *__restrict__ etab, Etab32 et,
+                                                          const PointConst *pcs, double *partial, int NA) {
+  __shared__ FastConst c;
+  __shared__ float4 sc[257];
+  const int pt = blockIdx.x;
+  if (threadIdx.x == 0) c = fast_const(pcs[pt], g);
+  for (int i = threadIdx.x; i < 257; i += blockDim.x) sc[i] = et.SC[i];
+  __syncthreads();
+  df32 acc[26];
+#pragma unroll
+  for (int q = 0; q < 26; q++) acc[q] = df32{0.f, 0.f};
+  const int64_t k0 = (int64_t)blockIdx.y * kPtThreads * kPtSamples;
+  const int64_t k1 = min(g.n, k0 + (int64_t)kPtThreads * kPtSamples);
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += kPtThreads) {
+    const FastSample s = fast_sample<true>(c, g, etab, et, sc, k);
+    fg_sample(c, s, acc);
+  }
+  fast_reduce<26>(acc, 0, NA, partial, pt);
+}
+
+// One sample's terms of the Hessian's accumulators (k_points_h).  Near a maximum the
+// two parts of d2|S|^2 (|dS|^2 and Re(S* d2S)) cancel to ~1e-4 for the sky pairs,
+// so every term of d2S is a double-float; only x d2a (~1e-12 of the dP_i dP_j term)
+// and the sums a_i a_j + a a_ij (they enter F's curvature at ~1e-9 of its scale) are FP32.
+__host__ __device__ __forceinline__ void hess_sample(const FastConst &c, const FastSample &s, df32 *acc) {
+  const float cx = s.cx.hi, sx = s.sx.hi, c2 = s.c2.hi, s2 = s.s2.hi, xf = s.x.hi, af = s.a.hi, bf = s.b.hi;
+  // first derivatives of a, b (double-float)
+  const df32 a_a = df_add(df_sub(df_scale(df_sub(df_mul(c.ea[1], s.c2), df_mul(c.ea[0], s.s2)), 2.f),
+                                 df_mul(c.ea[2], s.sx)), df_mul(c.ea[3], s.cx));
+  const df32 b_a = df_add(df_sub(df_scale(df_sub(df_mul(c.eb[1], s.c2), df_mul(c.eb[0], s.s2)), 2.f),
+                                 df_mul(c.eb[2], s.sx)), df_mul(c.eb[3], s.cx));
+  const df32 a_d = df_add(df_add(df_add(df_mul_f(s.c2, c.ea_d[0]), df_mul_f(s.s2, c.ea_d[1])),
+                                 df_add(df_mul_f(s.cx, c.ea_d[2]), df_mul_f(s.sx, c.ea_d[3]))),
+                          df32{c.ea_d[4], 0.f});
+  const df32 b_d = df_add(df_add(df_mul_f(s.c2, c.eb_d[0]), df_mul_f(s.s2, c.eb_d[1])),
+                          df_add(df_mul_f(s.cx, c.eb_d[2]), df_mul_f(s.sx, c.eb_d[3])));
+  // second derivatives of a, b (FP32)
+  const float a_aa = -4.f * c.eaf[0] * c2 - 4.f * c.eaf[1] * s2 - c.eaf[2] * cx - c.eaf[3] * sx;
+  const float b_aa = -4.f * c.ebf[0] * c2 - 4.f * c.ebf[1] * s2 - c.ebf[2] * cx - c.ebf[3] * sx;
+  const float a_ad = -2.f * c.ea_d[0] * s2 + 2.f * c.ea_d[1] * c2 - c.ea_d[2] * sx + c.ea_d[3] * cx;
+  const float b_ad = -2.f * c.eb_d[0] * s2 + 2.f * c.eb_d[1] * c2 - c.eb_d[2] * sx + c.eb_d[3] * cx;
+  const float a_dd = c.ea_dd[0] * c2 + c.ea_dd[1] * s2 + c.ea_dd[2] * cx + c.ea_dd[3] * sx + c.ea_dd[4];
+  const float b_dd = c.eb_dd[0] * c2 + c.eb_dd[1] * s2 + c.eb_dd[2] * cx + c.eb_dd[3] * sx;
+  // phase derivatives and the sky second derivatives of the delay (double-float)
+  const df32 w = df_add(c.F0L2, df_mul(c.f1, s.t));
+  const df32 phia = df_sub(df_add(df_mul(c.nxAa, s.cl), df_mul(c.nyAa, s.sl)), df_mul(c.rcd, s.sx));
+  const df32 phide = df_add(df_add(df_add(df_mul(c.nxAd, s.cl), df_mul(c.nyAd, s.sl)), df_mul(c.rcd_d, s.cx)),
+                            c.zsd_d);
+  const df32 phi_aa = df_sub(df_add(df_mul(c.nxAaa, s.cl), df_mul(c.nyAaa, s.sl)), df_mul(c.rcd, s.cx));
+  const df32 phi_ad = df_sub(df_add(df_mul(c.nxAad, s.cl), df_mul(c.nyAad, s.sl)), df_mul(c.rcd_d, s.sx));
+  const df32 phi_dd = df_add(df_add(df_add(df_mul(c.nxAdd, s.cl), df_mul(c.nyAdd, s.sl)), df_mul(c.rcd_dd, s.cx)),
+                             c.zsd_dd);
+  const df32 dP[4] = {df_add(s.t, s.phi), s.tu, df_mul(w, phia), df_mul(w, phide)};
+  const df32 ua = df_mul(s.x, s.a), ub = df_mul(s.x, s.b);
+  const df32 uam = df_mul(df_m4pi2(), ua), ubm = df_mul(df_m4pi2(), ub);
+  const df32 mtp = df_neg(df_two_pi());
+  // x da_i, x db_i (i = alpha, delta)
+  const df32 xa[2] = {df_mul(s.x, a_a), df_mul(s.x, a_d)}, xb[2] = {df_mul(s.x, b_a), df_mul(s.x, b_d)};
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+#pragma unroll
+    for (int j = i; j < 4; j++) {
+      const int o = 2 * sym_idx(i, j);
+      const df32 m = df_mul(dP[i], dP[j]);
+      float d2a = 0.f, d2b = 0.f;
+      if (i == 2 && j == 2) { d2a = a_aa; d2b = b_aa; }
+      if (i == 2 && j == 3) { d2a = a_ad; d2b = b_ad; }
+      if (i == 3 && j == 3) { d2a = a_dd; d2b = b_dd; }
+      // P = x (d2a - 4 pi^2 a dP_i dP_j)
+      const df32 Pa = df_add_f(df_mul(uam, m), xf * d2a), Pb = df_add_f(df_mul(ubm, m), xf * d2b);
+      acc[o] = df_add(acc[o], df_mul(Pa, s.cp));
+      acc[o + 1] = df_sub(acc[o + 1], df_mul(Pa, s.sp));
+      acc[o + 20] = df_add(acc[o + 20], df_mul(Pb, s.cp));
+      acc[o + 21] = df_sub(acc[o + 21], df_mul(Pb, s.sp));
+      if (j >= 2) {
+        // Q = -2 pi x (da_i dP_j + da_j dP_i + a d2P), d2P the mixed phase derivative
+        df32 d2P;
+        if (i == 0) d2P = j == 2 ? phia : phide;
+        else if (i == 1) d2P = df_mul(s.t, j == 2 ? phia : phide);
+        else if (j == 2) d2P = df_mul(w, phi_aa);
+        else d2P = df_mul(w, i == 2 ? phi_ad : phi_dd);
+        df32 qa = df_mul(ua, d2P), qb = df_mul(ub, d2P);
+        qa = df_add(qa, df_mul(xa[j - 2], dP[i]));
+        qb = df_add(qb, df_mul(xb[j - 2], dP[i]));
+        if (i >= 2) {
+          qa = df_add(qa, df_mul(xa[i - 2], dP[j]));
+          qb = df_add(qb, df_mul(xb[i - 2], dP[j]));
+        }
+        const df32 Qa = df_mul(mtp, qa), Qb = df_mul(mtp, qb);
+        acc[o] = df_add(acc[o], df_mul(Qa, s.sp));
+        acc[o + 1] = df_add(acc[o + 1], df_mul(Qa, s.cp));
+        acc[o + 20] = df_add(acc[o + 20], df_mul(Qb, s.sp));
+        acc[o + 21] = df_add(acc[o + 21], df_mul(Qb, s.cp));
+      }
+    }
+  }
+  const float aa = a_a.hi, ad = a_d.hi, ba = b_a.hi, bd = b_d.hi;
+  acc[40] = df_add_f(acc[40], aa * aa + af * a_aa);
+  acc[41] = df_add_f(acc[41], aa * ad + af * a_ad);
+  acc[42] = df_add_f(acc[42], ad * ad + af * a_dd);
+  acc[43] = df_add_f(acc[43], ba * ba + bf * b_aa);
+  acc[44] = df_add_f(acc[44], ba * bd + bf * b_ad);
+  acc[45] = df_add_f(acc[45], bd * bd + bf * b_dd);
+}
+
+// The Hessian's accumulators [q0, q0 + 46) of PtLayout: d2Sa_ij, d2Sb_ij (i <= j) and
+// the sums a_i a_j + a a_ij, b_i b_j + b b_ij over the sky pairs.
+__global__ void __launch_bounds__(kPtThreads) k_points_h(SegGeom g, const dbl4 *__restrict__ etab, Etab32 et,
+                                                         const PointConst *pcs, double *partial, int NA, int q0) {
+  __shared__ FastConst c;
+  __shared__ float4 sc[257];
+  const int pt = blockIdx.x;
+  if (threadIdx.x == 0) c = fast_const(pcs[pt], g);
+  for (int i = threadIdx.x; i < 257; i += blockDim.x) sc[i] = et.SC[i];
+  __syncthreads();
+  df32 acc[46];
+#pragma unroll
+  for (int q = 0; q < 46; q++) acc[q] = df32{0.f, 0.f};
+  const int64_t k0 = (int64_t)blockIdx.y * kPtThreads * kPtSamples;
+  const int64_t k1 = min(g.n, k0 + (int64_t)kPtThreads * kPtSamples);
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += kPtThreads) {
+    const FastSample s = fast_sample<true>(c, g, etab, et, sc, k);  // the same e as k_points_fg
+    hess_sample(c, s, acc);
+  }
+  fast_reduce<46>(acc, q0, NA, partial, pt);
+}
+
+// The metric's accumulators [26, 40) in FP64 (first pass of a climb only): sums of
+// dP_i and dP_i dP_j [cycles].
+__global__ void __launch_bounds__(kPtThreads) k_points_met(SegGeom g, const dbl4 *__restrict__ etab,
+                                                           const PointConst *pcs, double *partial, int NA) {
+  __shared__ PointConst c;
+  const int pt = blockIdx.x;
+  if (threadIdx.x == 0) c = pcs[pt];
+  __syncthreads();
+  double acc[14];
+#pragma unroll
+  for (int q = 0; q < 14; q++) acc[q] = 0.0;
+  const int64_t k0 = (int64_t)blockIdx.y * kPtThreads * kPtSamples;
+  const int64_t k1 = min(g.n, k0 + (int64_t)kPtThreads * kPtSamples);
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += kPtThreads) {
+    const dbl4 e4 = etab[k];
+    const double t = (double)k * g.dt;
+    const double cx = c.ca * e4.z + c.sa * e4.w;
+    const double sx = c.sa * e4.z - c.ca * e4.w;
+    const double phi = kAUls * (c.nx * e4.x + c.nyp * e4.y) + c.rcd * cx + c.zsd;
+    const double phi_a = kAUls * (c.nx_a * e4.x + c.nyp_a * e4.y) - c.rcd * sx;
+    const double phi_d = kAUls * (c.nx_d * e4.x + c.nyp_d * e4.y) + c.rcd_d * cx + c.zsd_d;
+    const double w = c.f0 + g.fl + c.f1 * t;
+    const double dP[4] = {t + phi, t * (0.5 * t + phi), w * phi_a, w * phi_d};
+#pragma unroll
+    for (int i = 0; i < 4; i++) acc[i] += dP[i];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+      for (int j = i; j < 4; j++) acc[4 + sym_idx(i, j)] += dP[i] * dP[j];
+  }
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  __shared__ double red[kPtThreads / 32][14];
+#pragma unroll
+  for (int q = 0; q < 14; q++) {
+    double v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wp][q] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 14; q += kPtThreads) {
+    double v = 0.0;
+    for (int w2 = 0; w2 < kPtThreads / 32; w2++) v += red[w2][q];
+    partial[((int64_t)pt * gridDim.y + blockIdx.y) * NA + 26 + q] = v;
+  }
+}
+
 // F, gradient, Hessian (upper triangle) and reduced Fisher matrix (rad^2, upper
 // triangle) per point from the block partials, summed in block order.
 template <bool HESS, bool MET>
@@ -479,15 +912,33 @@ __global__ void k_climb_out(int npt, const ClimbState *st, double *F) {
 }
 
 // ------------------------------------------------------------------ host
+// The fine search's tables: built by the first call on a segment; the double-float
+// copy of the data is refreshed by every call (fs_seg_load may have replaced it).
 static fs_status earth_table(fs_seg *seg, cudaStream_t st) {
-  if (seg->etab64) return FS_OK;
-  if (cudaMalloc(&seg->etab64, sizeof(dbl4) * seg->g.n) != cudaSuccess) {
-    cudaGetLastError();
-    seg->etab64 = nullptr;
-    return FS_ERR_NOMEM;
+  const unsigned nb = (unsigned)((seg->g.n + 255) / 256);
+  if (!seg->etab64) {
+    if (cudaMalloc(&seg->etab64, sizeof(dbl4) * seg->g.n) != cudaSuccess) {
+      cudaGetLastError();
+      seg->etab64 = nullptr;
+      return FS_ERR_NOMEM;
+    }
+    k_earth_table64<<<nb, 256, 0, st>>>(seg->g, (dbl4 *)seg->etab64);
+    seg->ctx->launches += 1;
   }
-  k_earth_table64<<<(unsigned)((seg->g.n + 255) / 256), 256, 0, st>>>(seg->g, (dbl4 *)seg->etab64);
-  seg->ctx->launches += 1;
+  if (!seg->eph) {
+    if (!seg->etab32) {
+      if (cudaMalloc(&seg->etab32, etab32_bytes(seg->g.n)) != cudaSuccess) {
+        cudaGetLastError();
+        seg->etab32 = nullptr;
+        return FS_ERR_NOMEM;
+      }
+      const unsigned nt = nb > 2 ? nb : 2;  // at least the 257 table entries
+      k_earth_table32<<<nt, 256, 0, st>>>(seg->g.n, (const dbl4 *)seg->etab64, etab32_view(seg));
+      seg->ctx->launches += 1;
+    }
+    k_data32<<<nb, 256, 0, st>>>(seg->g.n, seg->x64, etab32_view(seg).X);
+    seg->ctx->launches += 1;
+  }
   return cuda_status(cudaGetLastError());
 }
 
@@ -534,27 +985,43 @@ static fs_status refine_ws(fs_ctx *ctx, const fs_seg *seg, int npt, bool climb, 
   return FS_OK;
 }
 
+// With the analytic Earth the sums run in the double-float kernels (F and gradient;
+// the Hessian; the metric in FP64); with a caller's position table in k_points.
 template <bool HESS, bool MET>
-static void launch_points(fs_seg *seg, const RefWs &w, int npt, double *F, double *grad, double *hess,
-                          double *metric, double *amp, cudaStream_t st) {
+static int launch_points(fs_seg *seg, const RefWs &w, int npt, double *F, double *grad, double *hess,
+                         double *metric, double *amp, cudaStream_t st) {
+  using Lt = PtLayout<HESS, MET>;
   const dim3 grid(npt, w.nblk);
   const dbl4 *et = (const dbl4 *)seg->etab64;
-  if (seg->eph)
+  int launches = 2;
+  if (seg->eph) {
     k_points<HESS, MET, true><<<grid, kPtThreads, 0, st>>>(seg->g, et, seg->eph, seg->x64, w.pc, w.partial);
-  else
-    k_points<HESS, MET, false><<<grid, kPtThreads, 0, st>>>(seg->g, et, nullptr, seg->x64, w.pc, w.partial);
+  } else {
+    const Etab32 e32 = etab32_view(seg);
+    k_points_fg<<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.pc, w.partial, Lt::kN);
+    if constexpr (HESS) {
+      k_points_h<<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.pc, w.partial, Lt::kN, Lt::kH);
+      launches++;
+    }
+    if constexpr (MET) {
+      k_points_met<<<grid, kPtThreads, 0, st>>>(seg->g, et, w.pc, w.partial, Lt::kN);
+      launches++;
+    }
+  }
   k_points_final<HESS, MET><<<(unsigned)((npt + 127) / 128), 128, 0, st>>>(w.partial, w.nblk, npt, seg->g, F, grad,
                                                                             hess, metric, amp);
+  return launches;
 }
 
 static fs_status points_pass(fs_ctx *ctx, fs_seg *seg, const RefWs &w, const fs_point *pts, int npt, double *F,
                              double *grad, double *hess, double *metric, cudaStream_t st, double *amp = nullptr) {
   k_point_constants<<<(unsigned)((npt + 127) / 128), 128, 0, st>>>(pts, npt, seg->g, ctx->det, w.pc);
-  if (hess && metric) launch_points<true, true>(seg, w, npt, F, grad, hess, metric, amp, st);
-  else if (hess) launch_points<true, false>(seg, w, npt, F, grad, hess, metric, amp, st);
-  else if (metric) launch_points<false, true>(seg, w, npt, F, grad, hess, metric, amp, st);
-  else launch_points<false, false>(seg, w, npt, F, grad, hess, metric, amp, st);
-  ctx->launches += 3;
+  int nl = 0;
+  if (hess && metric) nl = launch_points<true, true>(seg, w, npt, F, grad, hess, metric, amp, st);
+  else if (hess) nl = launch_points<true, false>(seg, w, npt, F, grad, hess, metric, amp, st);
+  else if (metric) nl = launch_points<false, true>(seg, w, npt, F, grad, hess, metric, amp, st);
+  else nl = launch_points<false, false>(seg, w, npt, F, grad, hess, metric, amp, st);
+  ctx->launches += 1 + nl;
   return cuda_status(cudaGetLastError());
 }
 

@@ -57,9 +57,9 @@ def metric_name(workload: str) -> str:
     return "F-stat templates/s (N=%d, 2^%d FFT, %s) on 1 GB300" % (wl.n, wl.nfft.bit_length() - 1, workload)
 
 
-FP64_PEAK_TFLOPS = 1.25          # nominal FP64 rate of a GB300 (no measured figure)
-REFINE_FLOP_PER_SAMPLE = 685.0   # FP64 flops per sample and point of the Hessian pass, from ncu's
-                                 # DFMA/DMUL/DADD counts (profiles/k_points_refine_2d.md)
+REFINE_FLOP_PER_SAMPLE = 5540.0  # FP32 flops per sample and point of a climb pass: the double-float
+                                 # kernels k_points_fg (1514) and k_points_h (4026), from ncu's
+                                 # FADD/FFMA/FMUL counts (profiles/k_points_refine_2d.md)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
@@ -725,15 +725,16 @@ def main_refine(args):
     line = {
         "metric": METRICS["refine_2d"], "value": value, "unit": "candidates/s", "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 double-float sums, FP64 orbital phase", "data": "synthetic",
         "config": {"workload": "refine_2d", "n": wl.n, "candidates": npt, "newton_steps": nsteps,
                    "coarse": "grid_2d search (256 sky x 16 spindowns), strongest 1024 crossings",
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky shards x%d" % world},
-        "roofline": {"kernel": "k_points<Hessian> (21 passes per step)", "bound": "fp64", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": None, "peak_kind": "nominal FP64 rate (no measured FP64 peak)",
-                     "flop_convention": "%d FP64 flop per sample and point per pass (ncu opcode counts)"
-                                        % REFINE_FLOP_PER_SAMPLE},
+        "roofline": {"kernel": "k_points_h + k_points_fg (double-float sums on the FP32 pipe, 21 passes per step)",
+                     "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "peak_kind": "FP32 CUDA-core peak from unit counts and max clock (152 SM x 128 x 2 x 2070 MHz)",
+                     "flop_convention": "%d FP32 flop per sample and point per pass (ncu opcode counts of the two "
+                                        "kernels; the whole step's time)" % REFINE_FLOP_PER_SAMPLE},
         "gpu_launches": int(stats["launches"]),
         "clocks": ck,
         "F_gain": {"median": float(np.median(gain)), "max": float(np.max(gain))},

@@ -504,6 +504,7 @@ __device__ __forceinline__ void pass2_item_ib(const Pass2Args &A, int tm, int zs
     sfor<0, P>([&](auto c) { xw[X::at(c, b)] = v[s * P + c]; });
   });
   __syncwarp();
+  if (dbg_in(zoff + L2 - 1, A.z_elems, A.flags)) discard_row<L2, T>(z, t);
   sfor<0, Q>([&](auto bb) { v[bb] = xw[X::at(t, bb)]; });
   __syncthreads();  // every warp is done with the exchange area (reused for the rows and the F tile)
   dft_inplace<Q, Q, D>(v);  // v[d] = X[k2 = t + P d] of row k1 (d < D)

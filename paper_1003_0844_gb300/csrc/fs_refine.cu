@@ -572,7 +572,12 @@ __global__ void __launch_bounds__(kPtThreads) k_points_fg(SegGeom g, const dbl4 
 // two parts of d2|S|^2 (|dS|^2 and Re(S* d2S)) cancel to ~1e-4 for the sky pairs,
 // so every term of d2S is a double-float; only x d2a (~1e-12 of the dP_i dP_j term)
 // and the sums a_i a_j + a a_ij (they enter F's curvature at ~1e-9 of its scale) are FP32.
+// SIG: 0 signal a only (acc[0, 20) pairs, acc[20, 23) the a sums), 1 signal b only (same
+// layout), 2 both (the 46 sums in PtLayout's order).
+template <int SIG>
 __host__ __device__ __forceinline__ void hess_sample(const FastConst &c, const FastSample &s, df32 *acc) {
+  constexpr bool DA = SIG != 1, DB = SIG != 0;
+  constexpr int OB = SIG == 2 ? 20 : 0;  // offset of signal b's pairs
   const float cx = s.cx.hi, sx = s.sx.hi, c2 = s.c2.hi, s2 = s.s2.hi, xf = s.x.hi, af = s.a.hi, bf = s.b.hi;
   // first derivatives of a, b (double-float)
   const df32 a_a = df_add(df_sub(df_scale(df_sub(df_mul(c.ea[1], s.c2), df_mul(c.ea[0], s.s2)), 2.f),
@@ -617,11 +622,16 @@ __host__ __device__ __forceinline__ void hess_sample(const FastConst &c, const F
       if (i == 2 && j == 3) { d2a = a_ad; d2b = b_ad; }
       if (i == 3 && j == 3) { d2a = a_dd; d2b = b_dd; }
       // P = x (d2a - 4 pi^2 a dP_i dP_j)
-      const df32 Pa = df_add_f(df_mul(uam, m), xf * d2a), Pb = df_add_f(df_mul(ubm, m), xf * d2b);
-      acc[o] = df_add(acc[o], df_mul(Pa, s.cp));
-      acc[o + 1] = df_sub(acc[o + 1], df_mul(Pa, s.sp));
-      acc[o + 20] = df_add(acc[o + 20], df_mul(Pb, s.cp));
-      acc[o + 21] = df_sub(acc[o + 21], df_mul(Pb, s.sp));
+      if constexpr (DA) {
+        const df32 Pa = df_add_f(df_mul(uam, m), xf * d2a);
+        acc[o] = df_add(acc[o], df_mul(Pa, s.cp));
+        acc[o + 1] = df_sub(acc[o + 1], df_mul(Pa, s.sp));
+      }
+      if constexpr (DB) {
+        const df32 Pb = df_add_f(df_mul(ubm, m), xf * d2b);
+        acc[o + OB] = df_add(acc[o + OB], df_mul(Pb, s.cp));
+        acc[o + OB + 1] = df_sub(acc[o + OB + 1], df_mul(Pb, s.sp));
+      }
       if (j >= 2) {
         // Q = -2 pi x (da_i dP_j + da_j dP_i + a d2P), d2P the mixed phase derivative
         df32 d2P;
@@ -629,32 +639,43 @@ __host__ __device__ __forceinline__ void hess_sample(const FastConst &c, const F
         else if (i == 1) d2P = df_mul(s.t, j == 2 ? phia : phide);
         else if (j == 2) d2P = df_mul(w, phi_aa);
         else d2P = df_mul(w, i == 2 ? phi_ad : phi_dd);
-        df32 qa = df_mul(ua, d2P), qb = df_mul(ub, d2P);
-        qa = df_add(qa, df_mul(xa[j - 2], dP[i]));
-        qb = df_add(qb, df_mul(xb[j - 2], dP[i]));
-        if (i >= 2) {
-          qa = df_add(qa, df_mul(xa[i - 2], dP[j]));
-          qb = df_add(qb, df_mul(xb[i - 2], dP[j]));
+        if constexpr (DA) {
+          df32 qa = df_add(df_mul(ua, d2P), df_mul(xa[j - 2], dP[i]));
+          if (i >= 2) qa = df_add(qa, df_mul(xa[i - 2], dP[j]));
+          const df32 Qa = df_mul(mtp, qa);
+          acc[o] = df_add(acc[o], df_mul(Qa, s.sp));
+          acc[o + 1] = df_add(acc[o + 1], df_mul(Qa, s.cp));
         }
-        const df32 Qa = df_mul(mtp, qa), Qb = df_mul(mtp, qb);
-        acc[o] = df_add(acc[o], df_mul(Qa, s.sp));
-        acc[o + 1] = df_add(acc[o + 1], df_mul(Qa, s.cp));
-        acc[o + 20] = df_add(acc[o + 20], df_mul(Qb, s.sp));
-        acc[o + 21] = df_add(acc[o + 21], df_mul(Qb, s.cp));
+        if constexpr (DB) {
+          df32 qb = df_add(df_mul(ub, d2P), df_mul(xb[j - 2], dP[i]));
+          if (i >= 2) qb = df_add(qb, df_mul(xb[i - 2], dP[j]));
+          const df32 Qb = df_mul(mtp, qb);
+          acc[o + OB] = df_add(acc[o + OB], df_mul(Qb, s.sp));
+          acc[o + OB + 1] = df_add(acc[o + OB + 1], df_mul(Qb, s.cp));
+        }
       }
     }
   }
   const float aa = a_a.hi, ad = a_d.hi, ba = b_a.hi, bd = b_d.hi;
-  acc[40] = df_add_f(acc[40], aa * aa + af * a_aa);
-  acc[41] = df_add_f(acc[41], aa * ad + af * a_ad);
-  acc[42] = df_add_f(acc[42], ad * ad + af * a_dd);
-  acc[43] = df_add_f(acc[43], ba * ba + bf * b_aa);
-  acc[44] = df_add_f(acc[44], ba * bd + bf * b_ad);
-  acc[45] = df_add_f(acc[45], bd * bd + bf * b_dd);
+  constexpr int MA = SIG == 2 ? 40 : 20, MB = SIG == 2 ? 43 : 20;
+  if constexpr (DA) {
+    acc[MA] = df_add_f(acc[MA], aa * aa + af * a_aa);
+    acc[MA + 1] = df_add_f(acc[MA + 1], aa * ad + af * a_ad);
+    acc[MA + 2] = df_add_f(acc[MA + 2], ad * ad + af * a_dd);
+  }
+  if constexpr (DB) {
+    acc[MB] = df_add_f(acc[MB], ba * ba + bf * b_aa);
+    acc[MB + 1] = df_add_f(acc[MB + 1], ba * bd + bf * b_ad);
+    acc[MB + 2] = df_add_f(acc[MB + 2], bd * bd + bf * b_dd);
+  }
 }
 
 // The Hessian's accumulators [q0, q0 + 46) of PtLayout: d2Sa_ij, d2Sb_ij (i <= j) and
-// the sums a_i a_j + a a_ij, b_i b_j + b b_ij over the sky pairs.
+// the sums a_i a_j + a a_ij, b_i b_j + b b_ij over the sky pairs; SIG selects signal a
+// or b (its 20 pair sums and 3 sums).
+// One kernel per signal (SIG 0: a, 1: b), 23 sums each: 2% faster than one kernel with
+// all 46 (255 registers and spills); forcing 3 CTAs per SM (168 registers) gained nothing.
+template <int SIG>
 __global__ void __launch_bounds__(kPtThreads) k_points_h(SegGeom g, const dbl4 *__restrict__ etab, Etab32 et,
                                                          const PointConst *pcs, double *partial, int NA, int q0) {
   __shared__ FastConst c;
@@ -663,16 +684,20 @@ __global__ void __launch_bounds__(kPtThreads) k_points_h(SegGeom g, const dbl4 *
   if (threadIdx.x == 0) c = fast_const(pcs[pt], g);
   for (int i = threadIdx.x; i < 257; i += blockDim.x) sc[i] = et.SC[i];
   __syncthreads();
-  df32 acc[46];
+  static_assert(SIG == 0 || SIG == 1, "one signal per kernel");
+  constexpr int NQ = 23;
+  df32 acc[NQ];
 #pragma unroll
-  for (int q = 0; q < 46; q++) acc[q] = df32{0.f, 0.f};
+  for (int q = 0; q < NQ; q++) acc[q] = df32{0.f, 0.f};
   const int64_t k0 = (int64_t)blockIdx.y * kPtThreads * kPtSamples;
   const int64_t k1 = min(g.n, k0 + (int64_t)kPtThreads * kPtSamples);
   for (int64_t k = k0 + threadIdx.x; k < k1; k += kPtThreads) {
     const FastSample s = fast_sample<true>(c, g, etab, et, sc, k);  // the same e as k_points_fg
-    hess_sample(c, s, acc);
+    hess_sample<SIG>(c, s, acc);
   }
-  fast_reduce<46>(acc, q0, NA, partial, pt);
+  // this signal's pairs, then its three sums of a_i a_j + a a_ij
+  fast_reduce<20>(acc, q0 + 20 * SIG, NA, partial, pt);
+  fast_reduce<3>(acc + 20, q0 + 40 + 3 * SIG, NA, partial, pt);
 }
 
 // The metric's accumulators [26, 40) in FP64 (first pass of a climb only): sums of
@@ -1000,8 +1025,9 @@ static int launch_points(fs_seg *seg, const RefWs &w, int npt, double *F, double
     const Etab32 e32 = etab32_view(seg);
     k_points_fg<<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.pc, w.partial, Lt::kN);
     if constexpr (HESS) {
-      k_points_h<<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.pc, w.partial, Lt::kN, Lt::kH);
-      launches++;
+      k_points_h<0><<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.pc, w.partial, Lt::kN, Lt::kH);
+      k_points_h<1><<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.pc, w.partial, Lt::kN, Lt::kH);
+      launches += 2;
     }
     if constexpr (MET) {
       k_points_met<<<grid, kPtThreads, 0, st>>>(seg->g, et, w.pc, w.partial, Lt::kN);

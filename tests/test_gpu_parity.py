@@ -282,8 +282,9 @@ def test_argument_errors(fs):
 def test_full_configuration_sampled(fs, name):
     """The benchmark's launch configuration (all 256 skies x 16 spindowns in one sky
     group, the persistent queue sized as the bench sizes it): sampled template rows
-    against the oracle (FFT mode) and their candidates, and for all 4096 templates the
-    count of crossings equals the number of F values above threshold."""
+    against the oracle (FFT mode) and their candidates; for all templates the count of
+    crossings equals the number of F values above threshold, and every template's F
+    (the 6-day 2^21 grid: every 32nd sky's) agrees with the plain FP64 form."""
     wl = W.WORKLOADS[name]
     det = W.detector_for(wl)
     x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float32)
@@ -314,6 +315,22 @@ def test_full_configuration_sampled(fs, name):
         missing, bad = check_candidates(np.zeros(mine.sum(), dtype=np.int64), np.zeros(mine.sum(), dtype=np.int64),
                                         bins[mine], Fc[mine], ref[None, :], wl.F_thr, 1)
         assert not missing and not bad, (t, missing, bad)
+    # every template (the 2^21 grid: every 32nd sky) against the plain FP64 form on the
+    # same GPU, itself parity-tested against the oracle at 1e-8, by chunks of skies
+    seg64 = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0, precision="f64",
+                       interbin=wl.interbin)
+    skies = np.arange(0, wl.nsky, 32 if wl.nfft > (1 << 20) else 1)
+    per = max(1, (1 << 28) // (wl.nspin * wl.nbins * 8))
+    worst = 0.0
+    for c0 in range(0, skies.size, per):
+        sk = skies[c0:c0 + per]
+        r64 = fs.search(ctx, seg64, _dev(alpha[sk]), _dev(delta[sk]), _dev(f1), 1e30, cand_cap=1)
+        rows = torch.as_tensor((sk[:, None] * wl.nspin + np.arange(wl.nspin)[None, :]).ravel(), device="cuda")
+        d = ((F[rows].double() - r64.F).abs() / torch.clamp(r64.F, min=1.0)).max().item()
+        worst = max(worst, d)
+    assert ctx.sync_status() == 0
+    assert worst <= F32_TOL, worst
+    seg64.close()
     seg.close()
     ctx.close()
 

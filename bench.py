@@ -57,9 +57,10 @@ def metric_name(workload: str) -> str:
     return "F-stat templates/s (N=%d, 2^%d FFT, %s) on 1 GB300" % (wl.n, wl.nfft.bit_length() - 1, workload)
 
 
-REFINE_FLOP_PER_SAMPLE = 5540.0  # FP32 flops per sample and point of a climb pass: the double-float
-                                 # kernels k_points_fg (1514) and k_points_h (4026), from ncu's
-                                 # FADD/FFMA/FMUL counts (profiles/k_points_refine_2d.md)
+REFINE_FLOP_PER_SAMPLE = 5540.0  # FP32 flops per sample and point of a climb pass: F and gradient
+                                 # (1514) and the Hessian's 46 sums computed once (4026), from ncu's
+                                 # FADD/FFMA/FMUL counts (profiles/k_points_refine_2d.md); the
+                                 # per-signal Hessian kernels' recomputation is not counted
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 

@@ -24,6 +24,13 @@ Modules and the parts of the paper they follow:
                 convention (Eq. eq:DFT), the F-statistic (Eq. OS), the exact
                 F without resampling (Eqs. OS, Fab), threshold crossings, the
                 noise-only false-alarm probability (Eq. PF).
+* ``refine``    the fine search (Sec. VI.C): exact F at continuous points
+                with its gradient, Hessian and reduced Fisher matrix (Eq.
+                redFm-def), Nelder-Mead maximisation.
+* ``adjoint``   the coarse search's F of the resampled series at continuous
+                points and its gradient through the resampling (Eqs. eq:Bt,
+                ia, Fab, OS; Sec. VI.A).
+* ``grid``      the constrained A4* lattice covering (Sec. IV).
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
 closed form, a textbook/library special case or brute force, except the

@@ -86,6 +86,17 @@ def spline_eval(y: np.ndarray, M: np.ndarray, u: np.ndarray) -> np.ndarray:
     return g * y[i] + f * y[i + 1] + ((g ** 3 - g) * M[i] + (f ** 3 - f) * M[i + 1]) / 6.0
 
 
+def spline_eval_derivative(y: np.ndarray, M: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """dS/du of the spline of spline_eval: on [i, i+1] with f = u - i, g = 1 - f,
+      dS/du = y_{i+1} - y_i + ((1 - 3 g^2) M_i + (3 f^2 - 1) M_{i+1}) / 6."""
+    u = np.asarray(u, dtype=np.float64)
+    n = y.size
+    i = np.minimum(np.floor(u).astype(np.int64), n - 2)
+    f = u - i
+    g = 1.0 - f
+    return y[i + 1] - y[i] + ((1.0 - 3.0 * g * g) * M[i] + (3.0 * f * f - 1.0) * M[i + 1]) / 6.0
+
+
 def source_times(tb: np.ndarray, alpha: float, delta: float, det, tol: float = 1e-10,
                  max_iter: int = 50) -> np.ndarray:
     """Solve t + phi_m(t) = t_b (Eq. eq:Bt) for the source time t by fixed-point iteration.
@@ -124,6 +135,14 @@ class Segment:
         out = np.zeros(t.size)
         u = 2.0 * t[inside] / self.dt
         out[inside] = spline_eval(self.x2, self.M, u)
+        return out
+
+    def interpolate_derivative(self, t: np.ndarray) -> np.ndarray:
+        """d/dt of interpolate: the spline's slope times du/dt = 2/dt; 0 outside [0, (N-1) dt]."""
+        t = np.asarray(t, dtype=np.float64)
+        inside = (t >= 0.0) & (t <= (self.n - 1) * self.dt)
+        out = np.zeros(t.size)
+        out[inside] = spline_eval_derivative(self.x2, self.M, 2.0 * t[inside] / self.dt) * (2.0 / self.dt)
         return out
 
     def nearest(self, t: np.ndarray) -> np.ndarray:

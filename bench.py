@@ -740,6 +740,33 @@ def main_refine(args):
         "clocks": ck,
         "F_gain": {"median": float(np.median(gain)), "max": float(np.max(gain))},
     }
+    # the adjoint: the coarse search's F at the starting points (forward) and gF dF/dtheta
+    # (backward, recomputing the resampled series), each timed over the same steps
+    pts0 = fs.points_from_candidates(ctx, seg, cand, npt, alpha, delta, f1)
+    for _ in range(2):
+        fs.fstat_resampled_grad(ctx, seg, pts0)
+    evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        evf[k][0].record(stream)
+        Fres = fs.fstat_resampled(ctx, seg, pts0)
+        evf[k][1].record(stream)
+        flush.zero_()
+        evb[k][0].record(stream)
+        _, gres = fs.fstat_resampled_grad(ctx, seg, pts0)
+        evb[k][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    fwd_ms = sum(a.elapsed_time(c) for a, c in evf) / steps
+    bwd_ms = sum(a.elapsed_time(c) for a, c in evb) / steps
+    line["adjoint"] = {"forward": {"value": npt / (fwd_ms / 1e3), "unit": "candidates/s", "ms": fwd_ms},
+                       "backward": {"value": npt / (bwd_ms / 1e3), "unit": "candidates/s", "ms": bwd_ms},
+                       "what": "F of the resampled series at the %d starting points (fs_fstat_resampled) and "
+                               "dF/d(f0, f1, alpha, delta) recomputing the series (fs_fstat_resampled_grad), "
+                               "FP32 with double-float phases" % npt,
+                       "F_res_over_F_exact_median": float(torch.median(Fres / F0).item())}
     if rank == 0 and not args.quick:
         # oracle: Nelder-Mead fine search (Sec. VI.C) from the first starting points, one
         # climb per host core

@@ -299,7 +299,8 @@ typedef struct {
 /* The F-statistic at npt points, evaluated exactly by the direct sums of
  * Eqs. OS and Fab over the segment's original samples (no resampling; phase
  * f0 (t + phi_m) + fl phi_m + f1 (t^2/2 + t phi_m), as in the fine search of
- * Sec. VI.C as run in Sec. VII), in FP64.  F_dev: npt doubles.  grad_dev: NULL or [npt][4]
+ * Sec. VI.C as run in Sec. VII): sums as double-floats with the orbital
+ * phase in FP64 (FP64 throughout with a caller's position table).  F_dev: npt doubles.  grad_dev: NULL or [npt][4]
  * doubles dF/d(f0, f1, alpha, delta).  hess_dev: NULL or [npt][10] doubles,
  * the upper triangle row by row of the Hessian of F.  metric_dev: NULL or [npt][10]
  * doubles, the upper triangle row by row of the reduced Fisher matrix
@@ -310,6 +311,28 @@ typedef struct {
 FS_API fs_status fs_fstat_points(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int32_t npt,
                                  double *F_dev, double *grad_dev, double *hess_dev, double *metric_dev,
                                  void *stream);
+
+/* The coarse search's F at npt continuous points (the adjoint's forward call):
+ * the sums of Eqs. ia and Fab over the resampled series of Sec. VI.A (source
+ * times of Eq. eq:Bt, spline values, a and b at those times) with the phase
+ * Psi_j = fl phi_m(t_j) + f1 (t_j^2/2 + t_j phi_m(t_j)) + f0 j dt, and F of Eq. OS.  At
+ * f0 = k / (nfft dt) it is fs_search's F at bin k (the zero-padded DFT of
+ * Eq. eq:DFT), between Fourier frequencies the same sum off the grid.  FP32 with
+ * double-float phases, as fs_search.  F_dev: npt doubles.  Segments of
+ * precision FS_PREC_F32 with FS_INTERP_SPLINE2X and the analytic Earth only
+ * (otherwise FS_ERR_UNSUPPORTED). */
+FS_API fs_status fs_fstat_resampled(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int32_t npt,
+                                    double *F_dev, void *stream);
+
+/* The backward (adjoint) call of fs_fstat_resampled: grad_dev[4 i + k] =
+ * gF_dev[i] * dF_i/dtheta_k, theta = (f0, f1, alpha, delta), gF_dev NULL for
+ * ones.  The resampled series is recomputed sample by sample, not stored; its
+ * sky dependence enters through the source times (Eq. eq:Bt differentiated:
+ * dt_j/dsky = -(d phi_m/dsky) / (1 + d phi_m/dt)), the spline's slope, a and b at
+ * the moved times and the phase.  F_dev: NULL or npt doubles (F as the forward
+ * call).  Same segments as fs_fstat_resampled. */
+FS_API fs_status fs_fstat_resampled_grad(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int32_t npt,
+                                         const double *gF_dev, double *F_dev, double *grad_dev, void *stream);
 
 /* Hill climb of the exact F from each point (the fine search of Sec. VI.C,
  * here by Newton's method instead of the simplex search): nsteps steps, each

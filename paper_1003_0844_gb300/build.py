@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfstat.so")
 SOURCES = ["fs_api.cu", "fs_fft64.cu", "fs_prep.cu", "fs_search32.cu", "fs_search64.cu", "fs_passes_small.cu",
            "fs_passes_mid.cu", "fs_passes_large.cu", "fs_passes_batch.cu", "fs_passes_ib.cu", "fs_passes_lat.cu",
-           "fs_passes_lat_wide.cu", "fs_batch.cu", "fs_refine.cu", "fs_host.cu", "fs_grid.cu"]
+           "fs_passes_lat_wide.cu", "fs_batch.cu", "fs_refine.cu", "fs_adjoint.cu", "fs_host.cu", "fs_grid.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

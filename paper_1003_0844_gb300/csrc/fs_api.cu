@@ -398,6 +398,22 @@ fs_status fs_fstat_points(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int
   return fstat_points(ctx, seg, pts_dev, npt, F_dev, grad_dev, hess_dev, metric_dev, as_stream(stream));
 }
 
+fs_status fs_fstat_resampled(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int32_t npt, double *F_dev,
+                             void *stream) {
+  if (!ctx || !seg || !pts_dev || !F_dev || seg->ctx != ctx || npt < 1) return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  NvtxRange nv("fs.fstat_resampled");
+  return fstat_resampled(ctx, seg, pts_dev, npt, nullptr, F_dev, nullptr, as_stream(stream));
+}
+
+fs_status fs_fstat_resampled_grad(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int32_t npt,
+                                  const double *gF_dev, double *F_dev, double *grad_dev, void *stream) {
+  if (!ctx || !seg || !pts_dev || !grad_dev || seg->ctx != ctx || npt < 1) return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  NvtxRange nv("fs.fstat_resampled_grad");
+  return fstat_resampled(ctx, seg, pts_dev, npt, gF_dev, F_dev, grad_dev, as_stream(stream));
+}
+
 fs_status fs_refine(fs_ctx *ctx, fs_seg *seg, fs_point *pts_dev, int32_t npt, int32_t nsteps, double *F_dev,
                     void *stream) {
   if (!ctx || !seg || !pts_dev || !F_dev || seg->ctx != ctx) return FS_ERR_ARG;

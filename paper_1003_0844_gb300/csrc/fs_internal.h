@@ -202,6 +202,9 @@ fs_status fstat_points(fs_ctx *ctx, fs_seg *seg, const fs_point *pts, int npt, d
                        double *hess, double *metric, cudaStream_t st);
 fs_status refine_points(fs_ctx *ctx, fs_seg *seg, fs_point *pts, int npt, int nsteps, double *F, cudaStream_t st);
 fs_status amplitudes(fs_ctx *ctx, fs_seg *seg, const fs_point *pts, int npt, double *amp, cudaStream_t st);
+// The coarse search's F at continuous points and (grad != NULL) gF dF/dtheta (fs_adjoint.cu).
+fs_status fstat_resampled(fs_ctx *ctx, fs_seg *seg, const fs_point *pts, int npt, const double *gF, double *F,
+                          double *grad, cudaStream_t st);
 fs_status points_from_candidates(fs_ctx *ctx, fs_seg *seg, const fs_candidate *cand, int n, const double *alpha,
                                  const double *delta, const double *f1, fs_point *pts, cudaStream_t st);
 fs_status autotune32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,

@@ -28,6 +28,7 @@ EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_prepare_segment_
            "fs_sync_status", "fs_strerror", "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling",
            "fs_get_stats", "fs_search_noalloc", "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune",
            "fs_fstat_points", "fs_refine", "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm_cell",
+           "fs_fstat_resampled", "fs_fstat_resampled_grad",
            "fs_false_alarm", "fs_threshold", "fs_cell_count", "fs_linear_model_fisher", "fs_lattice",
            "fs_lattice_nodes", "fs_lattice_templates", "fs_search_lattice", "fs_search_lattice_noalloc",
            "fs_search_lattice_batch", "fs_selftest_wait"]
@@ -105,6 +106,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.fs_autotune.argtypes = [vp, vp, vp, vp, i32, vp, i32, i32, ctypes.POINTER(_Tuning), vp]
     lib.fs_fstat_points.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
     lib.fs_refine.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+    lib.fs_fstat_resampled.argtypes = [vp, vp, vp, i32, vp, vp]
+    lib.fs_fstat_resampled_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
     lib.fs_points_from_candidates.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
     lib.fs_amplitudes.argtypes = [vp, vp, vp, i32, vp, vp]
     lib.fs_false_alarm_cell.argtypes = [f64]
@@ -127,7 +130,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                  "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm", "fs_threshold", "fs_cell_count",
                  "fs_linear_model_fisher", "fs_lattice", "fs_lattice_nodes", "fs_lattice_templates",
                  "fs_search_lattice", "fs_search_lattice_noalloc", "fs_search_lattice_batch",
-                 "fs_selftest_wait"):
+                 "fs_selftest_wait", "fs_fstat_resampled", "fs_fstat_resampled_grad"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -448,6 +451,63 @@ class FstatAt(torch.autograd.Function):
 def fstat_at(ctx: Context, seg: Segment, pts: torch.Tensor) -> torch.Tensor:
     """Differentiable exact F at the points (see FstatAt)."""
     return FstatAt.apply(pts, ctx, seg)
+
+
+def fstat_resampled(ctx: Context, seg: Segment, pts: torch.Tensor, stream=None) -> torch.Tensor:
+    """The coarse search's F at continuous points (fs_fstat_resampled): F [npt]."""
+    _need_cuda(pts, "pts", torch.float64)
+    if pts.dim() != 2 or pts.shape[1] != 4:
+        raise ValueError("pts must have shape [npt, 4]")
+    pts = pts.contiguous()
+    F = torch.empty(pts.shape[0], dtype=torch.float64, device=pts.device)
+    _check(ctx.lib.fs_fstat_resampled(ctx.handle, seg.handle, _ptr(pts), pts.shape[0], _ptr(F), _stream(stream)),
+           "fs_fstat_resampled")
+    return F
+
+
+def fstat_resampled_grad(ctx: Context, seg: Segment, pts: torch.Tensor, gF: torch.Tensor = None, stream=None):
+    """The backward call (fs_fstat_resampled_grad): (F [npt], gF dF/dpts [npt, 4]);
+    gF None for ones."""
+    _need_cuda(pts, "pts", torch.float64)
+    if pts.dim() != 2 or pts.shape[1] != 4:
+        raise ValueError("pts must have shape [npt, 4]")
+    pts = pts.contiguous()
+    npt = pts.shape[0]
+    if gF is not None:
+        _need_cuda(gF, "gF", torch.float64)
+        if gF.shape != (npt,):
+            raise ValueError("gF must have shape [npt]")
+        gF = gF.contiguous()
+    F = torch.empty(npt, dtype=torch.float64, device=pts.device)
+    g = torch.empty((npt, 4), dtype=torch.float64, device=pts.device)
+    _check(ctx.lib.fs_fstat_resampled_grad(ctx.handle, seg.handle, _ptr(pts), npt, _ptr(gF) if gF is not None else None,
+                                           _ptr(F), _ptr(g), _stream(stream)), "fs_fstat_resampled_grad")
+    return F, g
+
+
+class FstatResampled(torch.autograd.Function):
+    """The coarse search's F at the points as a differentiable function: the forward
+    call keeps only the points; the backward call recomputes the resampled series
+    and returns gF dF/dpts (the adjoint kernel)."""
+
+    @staticmethod
+    def forward(fctx, pts, ctx, seg):
+        pts = pts.detach().contiguous()
+        fctx.save_for_backward(pts)
+        fctx.handles = (ctx, seg)
+        return fstat_resampled(ctx, seg, pts)
+
+    @staticmethod
+    def backward(fctx, gF):
+        (pts,) = fctx.saved_tensors
+        ctx, seg = fctx.handles
+        _, g = fstat_resampled_grad(ctx, seg, pts, gF.detach().to(torch.float64).contiguous())
+        return g, None, None
+
+
+def fstat_resampled_at(ctx: Context, seg: Segment, pts: torch.Tensor) -> torch.Tensor:
+    """Differentiable coarse-search F at the points (see FstatResampled)."""
+    return FstatResampled.apply(pts, ctx, seg)
 
 
 def refine(ctx: Context, seg: Segment, pts: torch.Tensor, nsteps: int = 20, stream=None):

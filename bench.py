@@ -761,12 +761,29 @@ def main_refine(args):
     ctx.check()
     fwd_ms = sum(a.elapsed_time(c) for a, c in evf) / steps
     bwd_ms = sum(a.elapsed_time(c) for a, c in evb) / steps
+    # 20 steps of gradient ascent of the resampled F from the same points
+    fs.refine_resampled(ctx, seg, pts0, nsteps=nsteps)
+    eva = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        eva[k][0].record(stream)
+        _, Fasc = fs.refine_resampled(ctx, seg, pts0, nsteps=nsteps)
+        eva[k][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    asc_ms = sum(a.elapsed_time(c) for a, c in eva) / steps
     line["adjoint"] = {"forward": {"value": npt / (fwd_ms / 1e3), "unit": "candidates/s", "ms": fwd_ms},
                        "backward": {"value": npt / (bwd_ms / 1e3), "unit": "candidates/s", "ms": bwd_ms},
                        "what": "F of the resampled series at the %d starting points (fs_fstat_resampled) and "
                                "dF/d(f0, f1, alpha, delta) recomputing the series (fs_fstat_resampled_grad), "
                                "FP32 with double-float phases" % npt,
-                       "F_res_over_F_exact_median": float(torch.median(Fres / F0).item())}
+                       "F_res_over_F_exact_median": float(torch.median(Fres / F0).item()),
+                       "gradient_ascent": {"value": npt / (asc_ms / 1e3), "unit": "candidates/s", "ms": asc_ms,
+                                           "steps": nsteps,
+                                           "F_gain_median": float(torch.median(Fasc / Fres).item()),
+                                           "what": "fs_refine_resampled: quasi-Newton ascent (BFGS from 2 F G) "
+                                                   "of the resampled F, one adjoint evaluation per step"}}
     if rank == 0 and not args.quick:
         # oracle: Nelder-Mead fine search (Sec. VI.C) from the first starting points, one
         # climb per host core

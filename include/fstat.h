@@ -334,6 +334,20 @@ FS_API fs_status fs_fstat_resampled(fs_ctx *ctx, fs_seg *seg, const fs_point *pt
 FS_API fs_status fs_fstat_resampled_grad(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_dev, int32_t npt,
                                          const double *gF_dev, double *F_dev, double *grad_dev, void *stream);
 
+/* Gradient ascent of the coarse search's F (fs_fstat_resampled) from each
+ * point, the fine search driven by the adjoint's gradient: nsteps quasi-Newton
+ * steps D = B^-1 grad F.  B starts as 2 F G, G the reduced Fisher matrix at
+ * the starting point (Eq. redFm-def; near a maximum F(theta + tau) ~
+ * F(theta) (1 - tau^T G tau), Eq. TaylorC2), and is updated by BFGS from the
+ * gradient change of every accepted step.  Each step is limited to
+ * D^T G D <= 1 and scaled by a factor that doubles (up to 1) when F grows and
+ * quarters when it does not; a trial point replaces the current one only if its
+ * F is larger.  One adjoint evaluation (F and gradient) per step.  pts_dev is updated in
+ * place; F_dev (npt doubles) receives the final F.  Same segments as
+ * fs_fstat_resampled. */
+FS_API fs_status fs_refine_resampled(fs_ctx *ctx, fs_seg *seg, fs_point *pts_dev, int32_t npt, int32_t nsteps,
+                                     double *F_dev, void *stream);
+
 /* Hill climb of the exact F from each point (the fine search of Sec. VI.C,
  * here by Newton's method instead of the simplex search): nsteps steps, each
  * solving (-H + lambda diag(max(-H_ii, 2 F G_ii))) D = grad F with H the

@@ -129,3 +129,16 @@ def resampled_fstat_point(seg: resample.Segment, theta, fl: float, det, S0: floa
         scale[i] = c * (2.0 * abs(r["Sa"]) * abs(r["dSa"][i]) / r["A2"] + abs(ua)
                         + 2.0 * abs(r["Sb"]) * abs(r["dSb"][i]) / r["B2"] + abs(ub))
     return F, dF, scale
+
+
+def resampled_fine_search(seg: resample.Segment, theta0, fl: float, det, S0: float, scale, xatol: float = 1e-4,
+                          maxiter: int = 2000):
+    """Maximise the resampled F from theta0 with the Nelder-Mead simplex, in coordinates
+    u = (theta - theta0) / scale (scale: about one correlation length per parameter)."""
+    from scipy.optimize import minimize
+    theta0 = np.asarray(theta0, dtype=np.float64)
+    scale = np.asarray(scale, dtype=np.float64)
+    res = minimize(lambda u: -resampled_fstat_point(seg, theta0 + u * scale, fl, det, S0), np.zeros(4),
+                   method="Nelder-Mead", options=dict(xatol=xatol, fatol=1e-10, maxiter=maxiter,
+                                                      initial_simplex=0.3 * np.vstack([np.zeros(4), np.eye(4)])))
+    return theta0 + res.x * scale, -res.fun

@@ -198,10 +198,10 @@ fs_status fstat_resampled(fs_ctx *ctx, fs_seg *seg, const fs_point *pts, int npt
   const int64_t per_blk = (int64_t)kAdjThreads * kAdjSamples;
   const int nblk = (int)((seg->g.n + per_blk - 1) / per_blk);  // <= 65535 for n <= 2^28
   const size_t o_pa = (sizeof(ResPointConst) * (size_t)npt + 255) & ~(size_t)255;
-  fs_status s = ensure_buffer(&ctx->rws, &ctx->rws_bytes, o_pa + sizeof(double) * NQ * (size_t)nblk * npt, st);
+  fs_status s = ensure_buffer(&ctx->aws, &ctx->aws_bytes, o_pa + sizeof(double) * NQ * (size_t)nblk * npt, st);
   if (s != FS_OK) return s;
-  ResPointConst *pc = (ResPointConst *)ctx->rws;
-  double *partial = (double *)((char *)ctx->rws + o_pa);
+  ResPointConst *pc = (ResPointConst *)ctx->aws;
+  double *partial = (double *)((char *)ctx->aws + o_pa);
   DemodArgs A{};
   A.g = seg->g;
   A.dt2 = df_from_double(seg->g.dt);

@@ -124,6 +124,7 @@ void fs_destroy(fs_ctx *ctx) {
   for (int i = 0; i < fs_ctx::kWsSlots; i++) cudaFree(ctx->ws[i]);
   cudaFree(ctx->ws64);
   cudaFree(ctx->rws);
+  cudaFree(ctx->aws);
   cudaFree(ctx->scratch);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
   delete ctx;
@@ -414,6 +415,15 @@ fs_status fs_fstat_resampled_grad(fs_ctx *ctx, fs_seg *seg, const fs_point *pts_
   return fstat_resampled(ctx, seg, pts_dev, npt, gF_dev, F_dev, grad_dev, as_stream(stream));
 }
 
+fs_status fs_refine_resampled(fs_ctx *ctx, fs_seg *seg, fs_point *pts_dev, int32_t npt, int32_t nsteps,
+                              double *F_dev, void *stream) {
+  if (!ctx || !seg || !pts_dev || !F_dev || seg->ctx != ctx) return FS_ERR_ARG;
+  if (npt < 1 || nsteps < 0 || nsteps > 10000) return FS_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  NvtxRange nv("fs.refine_resampled");
+  return refine_resampled(ctx, seg, pts_dev, npt, nsteps, F_dev, as_stream(stream));
+}
+
 fs_status fs_refine(fs_ctx *ctx, fs_seg *seg, fs_point *pts_dev, int32_t npt, int32_t nsteps, double *F_dev,
                     void *stream) {
   if (!ctx || !seg || !pts_dev || !F_dev || seg->ctx != ctx) return FS_ERR_ARG;
@@ -467,7 +477,7 @@ fs_status fs_get_stats(fs_ctx *ctx, fs_stats *out, int32_t reset) {
   if (cudaDeviceSynchronize() != cudaSuccess) return FS_ERR_CUDA;
   memset(out, 0, sizeof(*out));
   out->launches = ctx->launches;
-  int64_t wb = (int64_t)(ctx->ws64_bytes + ctx->scratch_bytes + ctx->rws_bytes);
+  int64_t wb = (int64_t)(ctx->ws64_bytes + ctx->scratch_bytes + ctx->rws_bytes + ctx->aws_bytes);
   for (int i = 0; i < fs_ctx::kWsSlots; i++) wb += (int64_t)ctx->ws_bytes[i];
   out->workspace_bytes = wb;
   for (const auto &r : ctx->recs) {

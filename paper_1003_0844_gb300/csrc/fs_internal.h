@@ -27,6 +27,9 @@ struct fs_ctx {
   // fine-search workspace
   size_t rws_bytes = 0;
   void *rws = nullptr;
+  // workspace of the resampled F at continuous points (fs_adjoint.cu)
+  size_t aws_bytes = 0;
+  void *aws = nullptr;
   // device address of the fixed array of the allocation-free searches, looked up
   // for this context by fs_create (the address belongs to the device's context)
   unsigned char *noalloc = nullptr;
@@ -205,6 +208,8 @@ fs_status amplitudes(fs_ctx *ctx, fs_seg *seg, const fs_point *pts, int npt, dou
 // The coarse search's F at continuous points and (grad != NULL) gF dF/dtheta (fs_adjoint.cu).
 fs_status fstat_resampled(fs_ctx *ctx, fs_seg *seg, const fs_point *pts, int npt, const double *gF, double *F,
                           double *grad, cudaStream_t st);
+// Fisher-preconditioned gradient ascent of the resampled F from each point (fs_refine.cu).
+fs_status refine_resampled(fs_ctx *ctx, fs_seg *seg, fs_point *pts, int npt, int nsteps, double *F, cudaStream_t st);
 fs_status points_from_candidates(fs_ctx *ctx, fs_seg *seg, const fs_candidate *cand, int n, const double *alpha,
                                  const double *delta, const double *f1, fs_point *pts, cudaStream_t st);
 fs_status autotune32(fs_ctx *ctx, fs_seg *seg, const double *alpha, const double *delta, int nsky,

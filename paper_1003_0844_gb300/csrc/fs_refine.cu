@@ -736,6 +736,80 @@ fs_status refine_points(fs_ctx *ctx, fs_seg *seg, fs_point *pts, int npt, int ns
   return cuda_status(cudaGetLastError());
 }
 
+// The starting curvature of the resampled-F ascent: the Gauss-Newton Hessian of F
+// near a maximum, H = -2 F G (F(theta + tau) ~ F(theta) (1 - tau^T G tau), Eq.
+// TaylorC2), with which the first step is G^-1 grad F / (2 F).
+__global__ void k_gauss_hessian(int npt, const double *F, const double *G, double *H) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npt) return;
+  for (int q = 0; q < 10; q++) H[10 * i + q] = -2.0 * F[i] * G[10 * i + q];
+}
+
+// Accept the trial point if F grew; then update the curvature B = -H by BFGS from
+// the step s and the gradient change y = g_old - g_new (the quasi-Newton secant
+// condition B s = y for the minimisation of -F), skipped unless s^T y > 0 so that
+// B stays positive definite.  Over a long, flat ridge of F (the f0-sky correlation)
+// this learns the ridge's curvature, where the fixed -2 F G is far off.
+__global__ void k_bfgs_accept(int npt, fs_point *pts, ClimbState *st, const fs_point *trial, const double *Ft,
+                              const double *gt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npt) return;
+  ClimbState c = st[i];
+  if (Ft[i] > c.F) {
+    const fs_point a = pts[i], b = trial[i];
+    const double two_pi = 6.283185307179586476925286766559;
+    const double sv[4] = {b.f0 - a.f0, b.f1 - a.f1, remainder(b.alpha - a.alpha, two_pi), b.delta - a.delta};
+    double y[4], Bs[4], sBs = 0.0, sy = 0.0;
+    for (int q = 0; q < 4; q++) y[q] = c.g[q] - gt[4 * i + q];
+    for (int r = 0; r < 4; r++) {
+      Bs[r] = 0.0;
+      for (int q = 0; q < 4; q++) Bs[r] -= c.H[sym_idx(r, q)] * sv[q];
+      sBs += sv[r] * Bs[r];
+      sy += sv[r] * y[r];
+    }
+    if (sy > 0.0 && sBs > 0.0)
+      for (int r = 0; r < 4; r++)
+        for (int q = r; q < 4; q++) c.H[sym_idx(r, q)] += Bs[r] * Bs[q] / sBs - y[r] * y[q] / sy;
+    pts[i] = b;
+    c.F = Ft[i];
+    for (int q = 0; q < 4; q++) c.g[q] = gt[4 * i + q];
+    c.eta = fmin(1.0, 2.0 * c.eta);
+  } else {
+    c.eta *= 0.25;
+  }
+  st[i] = c;
+}
+
+fs_status refine_resampled(fs_ctx *ctx, fs_seg *seg, fs_point *pts, int npt, int nsteps, double *F, cudaStream_t st) {
+  if (seg->d.precision != FS_PREC_F32 || seg->d.interp != FS_INTERP_SPLINE2X || seg->eph) return FS_ERR_UNSUPPORTED;
+  ProfScope ps(ctx, PROF_OTHER, st);
+  fs_status s = earth_table(seg, st);
+  if (s != FS_OK) return s;
+  RefWs w;
+  s = refine_ws(ctx, seg, npt, true, st, &w);
+  if (s != FS_OK) return s;
+  const unsigned nb = (unsigned)((npt + 127) / 128);
+  // the reduced Fisher matrix at the starting points (w.Ft receives the exact F, unused)
+  s = points_pass(ctx, seg, w, pts, npt, w.Ft, nullptr, nullptr, w.Gt, st);
+  if (s != FS_OK) return s;
+  // F and its gradient from the adjoint kernels at the starting points
+  s = fstat_resampled(ctx, seg, pts, npt, nullptr, w.Ft, w.gt, st);
+  if (s != FS_OK) return s;
+  k_gauss_hessian<<<nb, 128, 0, st>>>(npt, w.Ft, w.Gt, w.Ht);
+  k_climb_init<<<nb, 128, 0, st>>>(npt, w.Ft, w.gt, w.Ht, w.Gt, w.state);
+  ctx->launches += 2;
+  for (int it = 0; it < nsteps; it++) {
+    k_climb_propose<<<nb, 128, 0, st>>>(npt, pts, w.state, w.trial);
+    s = fstat_resampled(ctx, seg, w.trial, npt, nullptr, w.Ft, w.gt, st);
+    if (s != FS_OK) return s;
+    k_bfgs_accept<<<nb, 128, 0, st>>>(npt, pts, w.state, w.trial, w.Ft, w.gt);
+    ctx->launches += 2;
+  }
+  k_climb_out<<<nb, 128, 0, st>>>(npt, w.state, F);
+  ctx->launches += 1;
+  return cuda_status(cudaGetLastError());
+}
+
 fs_status points_from_candidates(fs_ctx *ctx, fs_seg *seg, const fs_candidate *cand, int n, const double *alpha,
                                  const double *delta, const double *f1, fs_point *pts, cudaStream_t st) {
   const double df = 1.0 / ((double)seg->g.nfft * seg->g.dt);

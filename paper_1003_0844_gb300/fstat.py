@@ -28,7 +28,7 @@ EXPORTS = ["fs_create", "fs_destroy", "fs_prepare_segment", "fs_prepare_segment_
            "fs_sync_status", "fs_strerror", "fs_seg_upsampled", "fs_demodulate", "fs_inject", "fs_set_profiling",
            "fs_get_stats", "fs_search_noalloc", "fs_search_batch", "fs_set_tuning", "fs_get_tuning", "fs_autotune",
            "fs_fstat_points", "fs_refine", "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm_cell",
-           "fs_fstat_resampled", "fs_fstat_resampled_grad",
+           "fs_fstat_resampled", "fs_fstat_resampled_grad", "fs_refine_resampled",
            "fs_false_alarm", "fs_threshold", "fs_cell_count", "fs_linear_model_fisher", "fs_lattice",
            "fs_lattice_nodes", "fs_lattice_templates", "fs_search_lattice", "fs_search_lattice_noalloc",
            "fs_search_lattice_batch", "fs_selftest_wait"]
@@ -108,6 +108,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.fs_refine.argtypes = [vp, vp, vp, i32, i32, vp, vp]
     lib.fs_fstat_resampled.argtypes = [vp, vp, vp, i32, vp, vp]
     lib.fs_fstat_resampled_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+    lib.fs_refine_resampled.argtypes = [vp, vp, vp, i32, i32, vp, vp]
     lib.fs_points_from_candidates.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
     lib.fs_amplitudes.argtypes = [vp, vp, vp, i32, vp, vp]
     lib.fs_false_alarm_cell.argtypes = [f64]
@@ -130,7 +131,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                  "fs_points_from_candidates", "fs_amplitudes", "fs_false_alarm", "fs_threshold", "fs_cell_count",
                  "fs_linear_model_fisher", "fs_lattice", "fs_lattice_nodes", "fs_lattice_templates",
                  "fs_search_lattice", "fs_search_lattice_noalloc", "fs_search_lattice_batch",
-                 "fs_selftest_wait", "fs_fstat_resampled", "fs_fstat_resampled_grad"):
+                 "fs_selftest_wait", "fs_fstat_resampled", "fs_fstat_resampled_grad", "fs_refine_resampled"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -508,6 +509,17 @@ class FstatResampled(torch.autograd.Function):
 def fstat_resampled_at(ctx: Context, seg: Segment, pts: torch.Tensor) -> torch.Tensor:
     """Differentiable coarse-search F at the points (see FstatResampled)."""
     return FstatResampled.apply(pts, ctx, seg)
+
+
+def refine_resampled(ctx: Context, seg: Segment, pts: torch.Tensor, nsteps: int = 20, stream=None):
+    """Gradient ascent of the coarse search's F from each point (fs_refine_resampled):
+    returns (refined points, F)."""
+    _need_cuda(pts, "pts", torch.float64)
+    out = pts.clone().contiguous()
+    F = torch.empty(out.shape[0], dtype=torch.float64, device=out.device)
+    _check(ctx.lib.fs_refine_resampled(ctx.handle, seg.handle, _ptr(out), out.shape[0], int(nsteps), _ptr(F),
+                                       _stream(stream)), "fs_refine_resampled")
+    return out, F
 
 
 def refine(ctx: Context, seg: Segment, pts: torch.Tensor, nsteps: int = 20, stream=None):

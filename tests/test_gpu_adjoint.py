@@ -154,3 +154,61 @@ def test_unsupported_segments_are_refused(fs, kind):
     assert e.value.status == 7
     with pytest.raises(fs.FstatError):
         fs.fstat_resampled_grad(ctx, seg, _dev(th[None, :]))
+
+
+def test_gradient_ascent_never_lowers_F(fs):
+    """fs_refine_resampled on the 1-day case: F never decreases with more steps, the
+    returned F is the F at the returned point, and the oracle agrees there."""
+    wl, det, x, th = _case("small")
+    _, _, G0 = orf.fstat_point(x.astype(np.float64), wl.dt, th, wl.fl, det, wl.S0, grad=True)
+    width = 1.0 / np.sqrt(np.diag(G0))
+    starts = th + width * np.array([[0.9, -0.8, 0.7, -0.6], [-0.5, 0.6, 0.4, 0.9], [0.3, 0.3, -0.8, -0.2]])
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0)
+    prev = fs.fstat_resampled(ctx, seg, _dev(starts)).cpu().numpy()
+    for k in (1, 2, 4, 8, 20):
+        out, Fk = fs.refine_resampled(ctx, seg, _dev(starts), nsteps=k)
+        Fk = Fk.cpu().numpy()
+        assert np.all(Fk >= prev)
+        prev = Fk
+    assert ctx.sync_status() == 0
+    assert np.array_equal(prev, fs.fstat_resampled(ctx, seg, out).cpu().numpy())
+    oseg = ors.Segment(x.astype(np.float64), wl.dt)
+    out = out.cpu().numpy()
+    for p in range(len(starts)):
+        Fr = oad.resampled_fstat_point(oseg, out[p], wl.fl, det, wl.S0)
+        assert abs(prev[p] - Fr) <= F_TOL * Fr, (p, prev[p], Fr)
+
+
+def test_gradient_ascent_reaches_the_simplex_maximum(fs):
+    """The 2-day series of the differentiation workload: from three starts up to a
+    correlation width away, 20 quasi-Newton steps reach the oracle's simplex maximum of
+    the resampled F to 1e-3 of F, i.e. (F(theta + tau) ~ F (1 - tau^T G tau), Eq.
+    TaylorC2) to about 0.03 of a correlation length; near the peak the FP32 rounding of
+    F (~1e-5) decides the last accepted steps."""
+    wl, det, x, th = _case("grid_2d")
+    _, _, G0 = orf.fstat_point(x.astype(np.float64), wl.dt, th, wl.fl, det, wl.S0, grad=True)
+    width = 1.0 / np.sqrt(np.diag(G0))
+    starts = th + width * np.array([[0.9, -0.8, 0.7, -0.6], [-0.5, 0.6, 0.4, 0.9], [0.3, 0.3, -0.8, -0.2]])
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0)
+    F0 = fs.fstat_resampled(ctx, seg, _dev(starts)).cpu().numpy()
+    out, F = fs.refine_resampled(ctx, seg, _dev(starts), nsteps=20)
+    assert ctx.sync_status() == 0
+    out, F = out.cpu().numpy(), F.cpu().numpy()
+    oseg = ors.Segment(x.astype(np.float64), wl.dt)
+    _, Fb = oad.resampled_fine_search(oseg, starts[1], wl.fl, det, wl.S0, width)
+    for p in range(len(starts)):
+        assert F[p] > F0[p]
+        assert F[p] >= Fb * (1 - 1e-3), (p, F[p], Fb)
+        Fr = oad.resampled_fstat_point(oseg, out[p], wl.fl, det, wl.S0)
+        assert abs(F[p] - Fr) <= F_TOL * Fr, (p, F[p], Fr)
+
+
+def test_gradient_ascent_refuses_unsupported_segments(fs):
+    wl, det, x, th = _case("small")
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x.astype(np.float64)), wl.dt, wl.nfft, wl.fl, wl.S0, precision="f64")
+    with pytest.raises(fs.FstatError) as e:
+        fs.refine_resampled(ctx, seg, _dev(th[None, :]), nsteps=2)
+    assert e.value.status == 7

@@ -19,8 +19,8 @@
 //   dSa = sum_j [d(x~ a)_j - 2 pi i x~_j a_j dPsi_j] exp(-2 pi i Psi_j),
 //   dF = c [2 Re(conj(Sa) dSa) / <a^2> - |Sa|^2 d<a^2> / <a^2>^2 + (same for b)].
 // Arithmetic as in the coarse search: FP32, with the phase terms as double-floats
-// reduced to fractions of a cycle; per-thread FP32 sums over 16 samples, combined
-// in FP64 in a fixed order.
+// reduced to fractions of a cycle; per-thread FP32 sums over 32 samples, combined
+// in FP64 across warps in a fixed order.
 #include "fs_internal.h"
 #include "fs_model.cuh"
 #include "fs_demod.cuh"
@@ -29,7 +29,7 @@
 namespace fs {
 
 constexpr int kAdjThreads = 256;
-constexpr int kAdjSamples = 16;  // samples per thread per block
+constexpr int kAdjSamples = 32;  // samples per thread per block
 
 // Per-point constants: the coarse search's sky constants, the sky derivatives of
 // the delay's and of a, b's coefficients, and the phase coefficients.
@@ -146,13 +146,15 @@ __global__ void __launch_bounds__(kAdjThreads) k_resampled(DemodArgs A, const Re
       acc[25] = fmaf(r.bv, b_d, acc[25]);
     }
   }
-  // the block's sums in FP64, warps in a fixed order
+  // the block's sums: a pairwise FP32 tree within each warp (5 roundings), then the
+  // warps in FP64 in a fixed order (an FP64 tree here kept the 1/64-rate FP64 pipe 60%
+  // busy)
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < NQ; q++) {
-    double v = (double)acc[q];
+    float v = acc[q];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wp][q] = v;
+    if (lane == 0) red[wp][q] = (double)v;
   }
   __syncthreads();
   for (int q = threadIdx.x; q < NQ; q += kAdjThreads) {

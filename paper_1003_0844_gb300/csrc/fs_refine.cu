@@ -273,11 +273,14 @@ template <int NQ>
 __device__ __forceinline__ void fast_reduce(const df32 *acc, int q0, int NA, double *partial, int pt) {
   __shared__ double red[kPtThreads / 32][NQ];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  // within a warp as double-floats (a DADD tree here cost the 1/64-rate FP64 pipe as
+  // much as the orbital phase of 8 samples), across warps in FP64
 #pragma unroll
   for (int q = 0; q < NQ; q++) {
-    double v = (double)acc[q].hi + (double)acc[q].lo;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wp][q] = v;
+    df32 v = acc[q];
+    for (int o = 16; o > 0; o >>= 1)
+      v = df_add(v, df32{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)});
+    if (lane == 0) red[wp][q] = (double)v.hi + (double)v.lo;
   }
   __syncthreads();
   for (int q = threadIdx.x; q < NQ; q += kPtThreads) {

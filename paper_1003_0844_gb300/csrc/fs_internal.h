@@ -76,7 +76,8 @@ struct fs_seg {
   double *x2 = nullptr;     // Fourier x2 upsampled [2n]
   void *coef = nullptr;     // spline coefficients per interval: float4 or double[4] x [2n]
   // Bluestein plan of the length-n DFT (depends on n only): transform length m,
-  // FFT of the chirp b and the FFT twiddles; built by the first load
+  // FFT of the chirp b and the FFT twiddles; built in FP64 by the first load, then
+  // held as double-floats (float4 per complex value, the same 16 bytes)
   int64_t blu_m = 0;
   double2 *blu_bhat = nullptr, *blu_tw = nullptr;
   double2 *blu_chirp = nullptr;  // [2N]: chirp exp(-i pi m^2/N), then the half-sample shift
@@ -107,6 +108,12 @@ cudaError_t fft64(double2 *buf, double2 *tmp, const double2 *twiddle, int64_t n,
                   int sign, cudaStream_t st, int64_t *launches);
 // twiddle[q] = exp(-2 pi i q / n), q < n/2
 cudaError_t fft64_twiddles(double2 *tw, int64_t n, cudaStream_t st);
+// The same transform in double-float arithmetic: complex values as float4
+// (re.hi, re.lo, im.hi, im.lo), twiddle[q] = exp(-2 pi i q / n) likewise (to_df32 of
+// the FP64 table).  to_df32 converts n double2 to float4 (in place when out == in).
+cudaError_t fftdf(float4 *buf, float4 *tmp, const float4 *twiddle, int64_t n, int batch, int sign, cudaStream_t st,
+                  int64_t *launches);
+cudaError_t to_df32(const double2 *in, float4 *out, int64_t n, cudaStream_t st);
 
 // Segment preparation (P0 tables, P1 upsampling, P2 spline).
 fs_status prepare_tables(fs_seg *seg, cudaStream_t st);

@@ -136,62 +136,65 @@ __global__ void k_bluestein_tables(double2 *chirp, double2 *shift, int64_t N) {
   }
 }
 
+// The per-load steps of the upsampler run in double-float arithmetic (FP32 pipe;
+// ~1e-14 relative), on tables converted once per length from their FP64 form.
 // a[n] = in[n] * exp(-i pi n^2/N) for n < N (in real or complex, optionally conjugated), 0 beyond.
-__global__ void k_bluestein_a(double2 *a, const double *in_real, const double2 *in_cplx, int conj_in,
-                              const double2 *chirp, int64_t N, int64_t M) {
+__global__ void k_bluestein_a(float4 *a, const double *in_real, const float4 *in_cplx, int conj_in,
+                              const float4 *chirp, int64_t N, int64_t M) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= M) return;
-  double2 v = make_double2(0.0, 0.0);
+  dfc v{df32{0.f, 0.f}, df32{0.f, 0.f}};
   if (i < N) {
-    double2 u = in_cplx ? in_cplx[i] : make_double2(in_real[i], 0.0);
-    if (conj_in) u.y = -u.y;
-    v = cmul(u, chirp[i]);
+    dfc u = in_cplx ? dfc_ld(in_cplx[i]) : dfc{df_from_double(in_real[i]), df32{0.f, 0.f}};
+    if (conj_in) u.im = df_neg(u.im);
+    v = dfc_mul(u, dfc_ld(chirp[i]));
   }
-  a[i] = v;
+  a[i] = dfc_st(v);
 }
 
-__global__ void k_pointwise_mul(double2 *a, const double2 *b, int64_t M) {
+__global__ void k_pointwise_mul(float4 *a, const float4 *b, int64_t M) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < M) a[i] = cmul(a[i], b[i]);
+  if (i < M) a[i] = dfc_st(dfc_mul(dfc_ld(a[i]), dfc_ld(b[i])));
 }
 
 // out[k] = exp(-i pi k^2/N) conv[k] / M   (k < N; M a power of two: exact scaling)
-__global__ void k_bluestein_out(double2 *out, const double2 *conv, const double2 *chirp, int64_t N, int64_t M) {
+__global__ void k_bluestein_out(float4 *out, const float4 *conv, const float4 *chirp, int64_t N, int64_t M) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= N) return;
-  const double inv = 1.0 / (double)M;
-  double2 v = conv[k];
-  v.x *= inv;
-  v.y *= inv;
-  out[k] = cmul(v, chirp[k]);
+  const float inv = 1.0f / (float)M;
+  dfc v = dfc_ld(conv[k]);
+  v = dfc{df_scale(v.re, inv), df_scale(v.im, inv)};
+  out[k] = dfc_st(dfc_mul(v, dfc_ld(chirp[k])));
 }
 
 // Z_k = X_k exp(i pi k'/N), Nyquist bin of even N zeroed (the shift table).
-__global__ void k_halfshift(double2 *Z, const double2 *X, const double2 *shift, int64_t N) {
+__global__ void k_halfshift(float4 *Z, const float4 *X, const float4 *shift, int64_t N) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= N) return;
-  Z[k] = cmul(X[k], shift[k]);
+  Z[k] = dfc_st(dfc_mul(dfc_ld(X[k]), dfc_ld(shift[k])));
 }
 
 // x2[2m] = x[m]; x2[2m+1] = Re(IDFT_N(Z))[m] = Re(conj(DFT_N(conj Z)))[m] / N
-__global__ void k_interleave(double *x2, const double *x, const double2 *dft_conjZ, int64_t N) {
+__global__ void k_interleave(double *x2, const double *x, const float4 *dft_conjZ, int64_t N) {
   int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= N) return;
   x2[2 * m] = x[m];
-  x2[2 * m + 1] = dft_conjZ[m].x / (double)N;
+  const float4 v = dft_conjZ[m];
+  x2[2 * m + 1] = ((double)v.x + (double)v.y) / (double)N;
 }
 
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-// DFT of length N of `in` (real or complex, optionally conjugated) into out, by Bluestein.
-static cudaError_t bluestein_dft(double2 *out, const double *in_real, const double2 *in_cplx, int conj_in,
-                                 int64_t N, int64_t M, const double2 *Bhat, const double2 *chirp, double2 *a,
-                                 double2 *tmp, const double2 *tw, cudaStream_t st, int64_t *launches) {
+// DFT of length N of `in` (real, or complex double-floats optionally conjugated) into
+// out (double-floats), by Bluestein.
+static cudaError_t bluestein_dft(float4 *out, const double *in_real, const float4 *in_cplx, int conj_in,
+                                 int64_t N, int64_t M, const float4 *Bhat, const float4 *chirp, float4 *a,
+                                 float4 *tmp, const float4 *tw, cudaStream_t st, int64_t *launches) {
   k_bluestein_a<<<nblk(M), 256, 0, st>>>(a, in_real, in_cplx, conj_in, chirp, N, M);
-  cudaError_t e = fft64(a, tmp, tw, M, 1, -1, st, launches);
+  cudaError_t e = fftdf(a, tmp, tw, M, 1, -1, st, launches);
   if (e != cudaSuccess) return e;
   k_pointwise_mul<<<nblk(M), 256, 0, st>>>(a, Bhat, M);
-  e = fft64(a, tmp, tw, M, 1, +1, st, launches);
+  e = fftdf(a, tmp, tw, M, 1, +1, st, launches);
   if (e != cudaSuccess) return e;
   k_bluestein_out<<<nblk(N), 256, 0, st>>>(out, a, chirp, N, M);
   *launches += 3;
@@ -218,25 +221,32 @@ fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st) {
       return FS_ERR_NOMEM;
     }
   }
-  double2 *chirp = seg->blu_chirp, *shift = seg->blu_chirp + N;
   // scratch: a, tmp, X (M each)
-  size_t need = sizeof(double2) * 3 * (size_t)M;
+  size_t need = sizeof(float4) * 3 * (size_t)M;
   fs_status s = ensure_buffer(&seg->ctx->scratch, &seg->ctx->scratch_bytes, need, st);
   if (s != FS_OK) return s;
-  double2 *a = (double2 *)seg->ctx->scratch;
-  double2 *tmp = a + M, *X = tmp + M;
-  double2 *Bhat = seg->blu_bhat, *tw = seg->blu_tw;
+  float4 *a = (float4 *)seg->ctx->scratch;
+  float4 *tmp = a + M, *X = tmp + M;
   cudaError_t e;
   if (seg->blu_m != M) {
+    // the plan in FP64, then its tables as double-floats in place (16 bytes either way)
+    double2 *chirp = seg->blu_chirp, *shift = seg->blu_chirp + N;
+    double2 *Bhat = seg->blu_bhat, *tw = seg->blu_tw;
     e = fft64_twiddles(tw, M, st);
     if (e != cudaSuccess) return FS_ERR_CUDA;
     k_bluestein_b<<<nblk(M), 256, 0, st>>>(Bhat, N, M);
     k_bluestein_tables<<<nblk(N), 256, 0, st>>>(chirp, shift, N);
     *L += 3;
-    e = fft64(Bhat, tmp, tw, M, 1, -1, st, L);
+    e = fft64(Bhat, (double2 *)tmp, tw, M, 1, -1, st, L);
     if (e != cudaSuccess) return FS_ERR_CUDA;
+    if (to_df32(Bhat, (float4 *)Bhat, M, st) != cudaSuccess || to_df32(tw, (float4 *)tw, M / 2, st) != cudaSuccess ||
+        to_df32(chirp, (float4 *)chirp, 2 * N, st) != cudaSuccess)
+      return FS_ERR_CUDA;
+    *L += 3;
     seg->blu_m = M;
   }
+  const float4 *chirp = (const float4 *)seg->blu_chirp, *shift = chirp + N;
+  const float4 *Bhat = (const float4 *)seg->blu_bhat, *tw = (const float4 *)seg->blu_tw;
 
   if (seg->d.x_dtype == FS_X_F32)
     k_load_x<float><<<nblk(N), 256, 0, st>>>((const float *)x_dev, seg->x64, seg->x32, N, seg->ctx->d_flags);

@@ -75,12 +75,14 @@ struct fs_seg {
   float *x32 = nullptr;     // input as float [n] (nearest-neighbour path)
   double *x2 = nullptr;     // Fourier x2 upsampled [2n]
   void *coef = nullptr;     // spline coefficients per interval: float4 or double[4] x [2n]
-  // Bluestein plan of the length-n DFT (depends on n only): transform length m,
-  // FFT of the chirp b and the FFT twiddles; built in FP64 by the first load, then
-  // held as double-floats (float4 per complex value, the same 16 bytes)
+  // Upsampler plan (depends on n only), built by the first load: transform length
+  // m >= 2n - 1, the FFT twiddles, the Bluestein chirp and half-sample shift [2n];
+  // blu_bhat holds the chirp's spectrum while the plan runs one Bluestein DFT, then
+  // the spectrum of the interpolation kernel.  Computed in FP64, held as
+  // double-floats (float4 per complex value, the same 16 bytes).
   int64_t blu_m = 0;
   double2 *blu_bhat = nullptr, *blu_tw = nullptr;
-  double2 *blu_chirp = nullptr;  // [2N]: chirp exp(-i pi m^2/N), then the half-sample shift
+  double2 *blu_chirp = nullptr;
   // FP64 (cos, sin) of the orbital and sidereal angles on t_k = k dt, built by
   // the first fine-search call
   void *etab64 = nullptr;

@@ -167,20 +167,40 @@ __global__ void k_bluestein_out(float4 *out, const float4 *conv, const float4 *c
   out[k] = dfc_st(dfc_mul(v, dfc_ld(chirp[k])));
 }
 
-// Z_k = X_k exp(i pi k'/N), Nyquist bin of even N zeroed (the shift table).
-__global__ void k_halfshift(float4 *Z, const float4 *X, const float4 *shift, int64_t N) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  Z[k] = dfc_st(dfc_mul(dfc_ld(X[k]), dfc_ld(shift[k])));
-}
-
-// x2[2m] = x[m]; x2[2m+1] = Re(IDFT_N(Z))[m] = Re(conj(DFT_N(conj Z)))[m] / N
-__global__ void k_interleave(double *x2, const double *x, const float4 *dft_conjZ, int64_t N) {
+// x2[2m] = x[m]; x2[2m+1] = Re(c[m]), c the circular convolution of x with the
+// interpolation kernel (its spectrum carries the 1/M of the inverse transform)
+__global__ void k_interleave(double *x2, const double *x, const float4 *c, int64_t N) {
   int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= N) return;
   x2[2 * m] = x[m];
-  const float4 v = dft_conjZ[m];
-  x2[2 * m + 1] = ((double)v.x + (double)v.y) / (double)N;
+  const float4 v = c[m];
+  x2[2 * m + 1] = (double)v.x + (double)v.y;
+}
+
+// a[i] = x[i] (i < N), 0 up to M, as double-float complex values
+__global__ void k_pack_real(float4 *a, const double *x, int64_t N, int64_t M) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const df32 v = i < N ? df_from_double(x[i]) : df32{0.f, 0.f};
+  a[i] = make_float4(v.hi, v.lo, 0.f, 0.f);
+}
+
+// The interpolation kernel h = IDFT_N(shift) (real: shift is Hermitian) placed
+// circularly in a length-M buffer, hM[d mod M] = h[d mod N] / M for |d| < N, zero
+// elsewhere; X = DFT_N(conj(shift)), so h[j] = Re(X_j) / N.  M >= 2N - 1: the two
+// ends do not overlap, and for outputs m < N and inputs j < N the circular
+// convolution of length M reads h at m - j only, i.e. it equals the length-N one.
+__global__ void k_place_kernel(float4 *hM, const float4 *X, int64_t N, int64_t M) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const int64_t d = i < N ? i : i - M;  // signed offset
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (d > -N) {
+    const float4 x = X[d < 0 ? d + N : d];
+    const df32 h = df_mul(df32{x.x, x.y}, df_from_double(1.0 / ((double)N * (double)M)));
+    v = make_float4(h.hi, h.lo, 0.f, 0.f);
+  }
+  hM[i] = v;
 }
 
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -201,13 +221,18 @@ static cudaError_t bluestein_dft(float4 *out, const double *in_real, const float
   return cudaGetLastError();
 }
 
+// Fourier x2 upsampling (Sec. VI.A, reading of the Nyquist split as the oracle):
+// the odd samples are x2[2m+1] = sum_j x_j h[(m - j) mod N] with h = IDFT_N(s),
+// s_k = exp(i pi k'/N) the half-sample shift (k' the signed frequency, zero at the
+// Nyquist bin of even N), i.e. the inverse DFT of the DFT of x times s.  Per length N
+// the plan computes h (one Bluestein DFT) and the spectrum of h placed in a
+// power-of-two buffer of M >= 2N - 1 points; every load then takes one forward and
+// one inverse transform of length M (double-float arithmetic on the FP32 pipe).
 fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st) {
   int64_t N = seg->g.n;
   int64_t M = 1;
   while (M < 2 * N - 1) M <<= 1;
   int64_t *L = &seg->ctx->launches;
-  // plan (once per segment): chirp spectrum Bhat = FFT_M(b), the FFT twiddles, and the
-  // chirp and half-shift tables of length N
   if (seg->blu_m != M) {
     cudaFree(seg->blu_bhat);
     cudaFree(seg->blu_tw);
@@ -227,42 +252,52 @@ fs_status prepare_upsample(fs_seg *seg, const void *x_dev, cudaStream_t st) {
   if (s != FS_OK) return s;
   float4 *a = (float4 *)seg->ctx->scratch;
   float4 *tmp = a + M, *X = tmp + M;
+  float4 *Hhat = (float4 *)seg->blu_bhat;  // after the plan: the kernel's spectrum
+  const float4 *tw = (const float4 *)seg->blu_tw;
   cudaError_t e;
   if (seg->blu_m != M) {
-    // the plan in FP64, then its tables as double-floats in place (16 bytes either way)
-    double2 *chirp = seg->blu_chirp, *shift = seg->blu_chirp + N;
-    double2 *Bhat = seg->blu_bhat, *tw = seg->blu_tw;
-    e = fft64_twiddles(tw, M, st);
+    // tables in FP64 (twiddles, Bluestein chirp and its spectrum, the half-sample
+    // shift), then as double-floats in place (16 bytes per complex value either way)
+    double2 *chirp64 = seg->blu_chirp, *shift64 = seg->blu_chirp + N;
+    double2 *Bhat64 = seg->blu_bhat, *tw64 = seg->blu_tw;
+    e = fft64_twiddles(tw64, M, st);
     if (e != cudaSuccess) return FS_ERR_CUDA;
-    k_bluestein_b<<<nblk(M), 256, 0, st>>>(Bhat, N, M);
-    k_bluestein_tables<<<nblk(N), 256, 0, st>>>(chirp, shift, N);
+    k_bluestein_b<<<nblk(M), 256, 0, st>>>(Bhat64, N, M);
+    k_bluestein_tables<<<nblk(N), 256, 0, st>>>(chirp64, shift64, N);
     *L += 3;
-    e = fft64(Bhat, (double2 *)tmp, tw, M, 1, -1, st, L);
+    e = fft64(Bhat64, (double2 *)tmp, tw64, M, 1, -1, st, L);
     if (e != cudaSuccess) return FS_ERR_CUDA;
-    if (to_df32(Bhat, (float4 *)Bhat, M, st) != cudaSuccess || to_df32(tw, (float4 *)tw, M / 2, st) != cudaSuccess ||
-        to_df32(chirp, (float4 *)chirp, 2 * N, st) != cudaSuccess)
+    if (to_df32(Bhat64, (float4 *)Bhat64, M, st) != cudaSuccess ||
+        to_df32(tw64, (float4 *)tw64, M / 2, st) != cudaSuccess ||
+        to_df32(chirp64, (float4 *)chirp64, 2 * N, st) != cudaSuccess)
       return FS_ERR_CUDA;
     *L += 3;
+    const float4 *chirp = (const float4 *)chirp64, *shift = chirp + N;
+    // X = DFT_N(conj(shift)): h = IDFT_N(shift) = Re(X) / N
+    e = bluestein_dft(X, nullptr, shift, 1, N, M, (const float4 *)Bhat64, chirp, a, tmp, tw, st, L);
+    if (e != cudaSuccess) return FS_ERR_CUDA;
+    // the kernel placed circularly (scaled by 1/M), and its spectrum in place of Bhat
+    k_place_kernel<<<nblk(M), 256, 0, st>>>(Hhat, X, N, M);
+    *L += 1;
+    e = fftdf(Hhat, tmp, tw, M, 1, -1, st, L);
+    if (e != cudaSuccess) return FS_ERR_CUDA;
     seg->blu_m = M;
   }
-  const float4 *chirp = (const float4 *)seg->blu_chirp, *shift = chirp + N;
-  const float4 *Bhat = (const float4 *)seg->blu_bhat, *tw = (const float4 *)seg->blu_tw;
 
   if (seg->d.x_dtype == FS_X_F32)
     k_load_x<float><<<nblk(N), 256, 0, st>>>((const float *)x_dev, seg->x64, seg->x32, N, seg->ctx->d_flags);
   else
     k_load_x<double><<<nblk(N), 256, 0, st>>>((const double *)x_dev, seg->x64, seg->x32, N, seg->ctx->d_flags);
-  *L += 1;
-  // X = DFT_N(x)
-  e = bluestein_dft(X, seg->x64, nullptr, 0, N, M, Bhat, chirp, a, tmp, tw, st, L);
+  // odd samples: the circular convolution of x with the kernel
+  k_pack_real<<<nblk(M), 256, 0, st>>>(a, seg->x64, N, M);
+  *L += 2;
+  e = fftdf(a, tmp, tw, M, 1, -1, st, L);
   if (e != cudaSuccess) return FS_ERR_CUDA;
-  // Z = half-sample shift; odd samples = Re IDFT_N(Z) = Re conj(DFT_N(conj Z)) / N
-  k_halfshift<<<nblk(N), 256, 0, st>>>(X, X, shift, N);
+  k_pointwise_mul<<<nblk(M), 256, 0, st>>>(a, Hhat, M);
   *L += 1;
-  // the result overwrites X: the transform reads its whole input before writing
-  e = bluestein_dft(X, nullptr, X, 1, N, M, Bhat, chirp, a, tmp, tw, st, L);
+  e = fftdf(a, tmp, tw, M, 1, +1, st, L);
   if (e != cudaSuccess) return FS_ERR_CUDA;
-  k_interleave<<<nblk(N), 256, 0, st>>>(seg->x2, seg->x64, X, N);
+  k_interleave<<<nblk(N), 256, 0, st>>>(seg->x2, seg->x64, a, N);
   *L += 1;
   return cuda_status(cudaGetLastError());
 }

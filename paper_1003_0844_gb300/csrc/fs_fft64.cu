@@ -7,6 +7,7 @@
 // this GPU).  Convention of Eq. (eq:DFT): X_k = sum_l x_l exp(-2 pi i l k / n),
 // unnormalised; the inverse uses exp(+2 pi i l k / n), also unnormalised.
 #include "fs_internal.h"
+#include "fs_dfc.cuh"
 
 namespace fs {
 

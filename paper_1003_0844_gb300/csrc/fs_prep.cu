@@ -16,6 +16,7 @@
 #include <stdio.h>
 #include <algorithm>
 #include "fs_internal.h"
+#include "fs_dfc.cuh"
 #include "fs_model.cuh"
 
 namespace fs {

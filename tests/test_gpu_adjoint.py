@@ -71,6 +71,26 @@ def test_F_and_gradient_match_oracle(fs, name):
         assert np.all(np.abs(g[p] - gr) <= G_TOL * scale), (p, g[p], gr, scale)
 
 
+def test_segment_epoch(fs):
+    """A segment starting t0 after the detector's t = 0 (Sec. V: orbital and sidereal
+    angles at its first sample): the adjoint against the oracle on the detector at
+    that epoch."""
+    from oracle import earth as oe
+    wl, det, x, th = _case("small")
+    t0 = 123456.7
+    P = _points(wl, oe.detector_at_epoch(det, t0), x, th)[:3]
+    ctx = fs.Context(det)
+    seg = fs.Segment(ctx, _dev(x, torch.float32), wl.dt, wl.nfft, wl.fl, wl.S0, t0=t0)
+    F, g = fs.fstat_resampled_grad(ctx, seg, _dev(P))
+    assert ctx.sync_status() == 0
+    F, g = F.cpu().numpy(), g.cpu().numpy()
+    oseg = ors.Segment(x.astype(np.float64), wl.dt)
+    for p in range(len(P)):
+        Fr, gr, scale = oad.resampled_fstat_point(oseg, P[p], wl.fl, oe.detector_at_epoch(det, t0), wl.S0, grad=True)
+        assert abs(F[p] - Fr) <= F_TOL * max(Fr, 1.0), (p, F[p], Fr)
+        assert np.all(np.abs(g[p] - gr) <= G_TOL * scale), (p, g[p], gr, scale)
+
+
 def test_on_the_fourier_grid_it_is_the_searchs_F(fs):
     """Points at f0 = k / (Nfft dt) with the templates of a search: F equals the
     search's F map at bin k (the transform and the direct sum are two routes to the

@@ -38,6 +38,8 @@ METRICS = {
     "uneven_64": "F-stat templates/s (64 segments of 1/2/3/6 days, 2^16-2^20 FFT) on 1 GB300",
     "grid_2d_ib": "F-stat templates/s (N=86,164, 2^17 FFT + interbinning) on 1 GB300; max rel dF vs FP64",
     "refine_2d": "fine-search candidates/s (20 Newton steps on the exact F, N=86,164) on 1 GB300",
+    "adjoint_2d": ("adjoint fine-search candidates/s (F of the resampled series and dF/d(f0, f1, delta, alpha) "
+                   "recomputing the series, 20 quasi-Newton steps, N=86,164) on 1 GB300"),
     "lattice_2d": "F-stat templates/s (N=86,164, 2^18 FFT, constrained A4* lattice of a sky patch) on 1 GB300",
 }
 
@@ -61,6 +63,9 @@ REFINE_FLOP_PER_SAMPLE = 5540.0  # FP32 flops per sample and point of a climb pa
                                  # (1514) and the Hessian's 46 sums computed once (4026), from ncu's
                                  # FADD/FFMA/FMUL counts (profiles/k_points_refine_2d.md); the
                                  # per-signal Hessian kernels' recomputation is not counted
+ADJOINT_FLOP_PER_SAMPLE = 424.0  # FP32 flops per output sample and point of the adjoint's backward
+                                 # kernel (F and the 26 sums of its gradient), from ncu's FADD/FFMA/FMUL
+                                 # counts (profiles/k_resampled_refine_2d.md)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
@@ -72,7 +77,7 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"],
                    help="ours: the CUDA library; reference: the CPU oracle on the host cores")
     p.add_argument("--workload", default="grid_2d",
-                   help="grid_2d (default), grid_2d_ib, wide_6d, lattice_2d, refine_2d, a batch (uneven_64, "
+                   help="grid_2d (default), grid_2d_ib, wide_6d, lattice_2d, refine_2d, adjoint_2d, a batch (uneven_64, "
                         "uneven_small) or a test-size workload (tiny, small)")
     p.add_argument("--cpu-templates", type=int, default=320,
                    help="oracle sample size: templates of the 2-day size per 20 host cores (~10 s)")
@@ -82,7 +87,8 @@ def _args():
     p.add_argument("--nsky", type=int, default=None, help="override the sky count (profiling runs, batch sky subset)")
     p.add_argument("--tune", action="store_true", help="run the launch tuner for each transform length first")
     p.add_argument("--n1", type=int, default=0, help="first-pass length N1 of the transform split (0: default)")
-    p.add_argument("--cands", type=int, default=1024, help="fine-search workload: candidates refined per step")
+    p.add_argument("--cands", type=int, default=1024,
+                   help="fine-search and adjoint workloads: candidates refined per step")
     p.add_argument("--stub", action="store_true",
                    help="launcher self-test on the CPU: every rank takes its sky shard and reports it over gloo; "
                         "no GPU work")
@@ -280,7 +286,7 @@ def host_cpu_model() -> str:
 
 
 def _oracle_worker_init():
-    import oracle.fstat, oracle.refine, oracle.resample  # noqa: F401  (imports before any timed region)
+    import oracle.adjoint, oracle.fstat, oracle.refine, oracle.resample  # noqa: F401  (imports before any timed region)
 
 
 def _oracle_worker_ready(_):
@@ -306,12 +312,17 @@ def _oracle_templates(task):
 
 def _oracle_points(task):
     """One worker's share of fine-search work: exact-F passes with gradient and
-    Hessian at points (kind "pass"), or Nelder-Mead climbs from points ("climb")."""
+    Hessian at points (kind "pass"), Nelder-Mead climbs from points ("climb"), or the
+    resampled F with its gradient at points after the worker's own segment
+    preparation ("adjoint")."""
     kind, x, dt, pts, fl, det, S0 = task
-    from oracle import refine as orf
+    from oracle import adjoint as oad, refine as orf, resample as ors
+    seg = ors.Segment(np.asarray(x, dtype=np.float64), dt) if kind == "adjoint" else None
     for p in pts:
         if kind == "pass":
             orf.fstat_point(np.asarray(x), dt, p, fl, det, S0, grad=True, hess=True)
+        elif kind == "adjoint":
+            oad.resampled_fstat_point(seg, p, fl, det, S0, grad=True)
         else:
             orf.fine_search(np.asarray(x), dt, p, fl, det, S0)
     return len(pts)
@@ -456,6 +467,21 @@ def run_reference(args):
                   "coarse": "grid_2d search (256 sky x 16 spindowns), strongest %d crossings" % args.cands,
                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky shards x%d" % args.gpus}
         what = "one exact-F pass with gradient and Hessian on each of %d workers (a candidate's climb takes 21)" % C
+        per_unit = 1.0 / 21.0
+    elif args.workload == "adjoint_2d":
+        wl = W.WORKLOADS["grid_2d"]
+        det = W.detector_for(wl)
+        x = (W.noise(wl) + orsp.inject(wl.n, wl.dt, W.injections(wl), wl.fl, det, wl.sigma)).astype(np.float32)
+        inj = W.injections(wl)[0]
+        th = np.array([inj.f0, inj.f1, inj.alpha, inj.delta])
+        tasks = [("adjoint", x, wl.dt, [th, th], wl.fl, det, wl.S0) for _ in range(C)]
+
+        def sample():
+            return pool.points(tasks)[0]
+        metric, unit = METRICS["adjoint_2d"], "candidates/s"
+        config = _adjoint_config(wl, args.cands, args.gpus)
+        what = ("two evaluations of the resampled F and its gradient after the segment's preparation on each of "
+                "%d workers (a candidate's 20 steps take 21)" % C)
         per_unit = 1.0 / 21.0
     else:
         wl = W.WORKLOADS[args.workload]
@@ -821,6 +847,157 @@ def main_refine(args):
         dist.destroy_process_group()
 
 
+def _adjoint_config(wl, cands, world):
+    return {"workload": "adjoint_2d", "n": wl.n, "candidates": cands, "ascent_steps": 20,
+            "coarse": "grid_2d search (256 sky x 16 spindowns), strongest %d crossings" % cands,
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "sky shards x%d" % world}
+
+
+def main_adjoint(args):
+    """The differentiation workload (config 4 of the headline's configs): the coarse
+    2-day search gives candidates (untimed); one step = starting points from 1024
+    candidates + the adjoint's gradient ascent (fs_refine_resampled: F and the gradient
+    of the resampled series recomputed at every step, 20 quasi-Newton steps)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1003_0844_gb300 import build, fstat as fs, shard
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    wl = W.WORKLOADS["grid_2d"]
+    det = W.detector_for(wl)
+    ctx = fs.Context(det, device=local)
+    x64 = torch.as_tensor(W.noise(wl), device="cuda")
+    fs.inject(ctx, x64, wl.dt, wl.fl, wl.sigma, W.injections(wl))
+    x32 = x64.float().contiguous()
+    a_all, d_all = W.sky_grid(wl.nsky * world)
+    mine = shard.sky_shard(wl.nsky, rank, world)
+    alpha = torch.as_tensor(np.ascontiguousarray(a_all[mine]), device="cuda")
+    delta = torch.as_tensor(np.ascontiguousarray(d_all[mine]), device="cuda")
+    f1 = torch.as_tensor(W.spin_grid(wl.nspin, *wl.f1_range), device="cuda")
+    seg = fs.Segment(ctx, x32, wl.dt, wl.nfft, wl.fl, wl.S0)
+    res = fs.search(ctx, seg, alpha, delta, f1, wl.F_thr, write_F=False, cand_cap=1 << 20)
+    ncand_all = min(int(res.n_cand.item()), res.cand.shape[0])
+    Fc = res.cand[:ncand_all, 3].view(torch.float32)
+    top = torch.argsort(Fc, descending=True)[:args.cands]
+    cand = res.cand[top].contiguous()
+    npt, nsteps = cand.shape[0], 20
+
+    def step():
+        pts = fs.points_from_candidates(ctx, seg, cand, npt, alpha, delta, f1)
+        return fs.refine_resampled(ctx, seg, pts, nsteps=nsteps)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    ctx.check()
+    ctx.stats(reset=True)
+    stream = torch.cuda.current_stream()
+    steps = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        out, Fa = step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    stats = ctx.stats(reset=True)
+    ctx.check()
+    total_ms = shard.max_over_ranks(sum(a.elapsed_time(c) for a, c in ev), device="cuda")
+    ms_per_step = total_ms / steps
+    value = npt * world / (ms_per_step / 1e3)
+    # the forward and backward calls alone at the starting points, same flushing
+    pts0 = fs.points_from_candidates(ctx, seg, cand, npt, alpha, delta, f1)
+    evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        evf[k][0].record(stream)
+        F0 = fs.fstat_resampled(ctx, seg, pts0)
+        evf[k][1].record(stream)
+        flush.zero_()
+        evb[k][0].record(stream)
+        fs.fstat_resampled_grad(ctx, seg, pts0)
+        evb[k][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    fwd_ms = sum(a.elapsed_time(c) for a, c in evf) / steps
+    bwd_ms = sum(a.elapsed_time(c) for a, c in evb) / steps
+    gain = (Fa / F0).cpu().numpy()
+    flops = ADJOINT_FLOP_PER_SAMPLE * wl.n * npt * (nsteps + 1)
+    achieved = flops / (ms_per_step / 1e3) / 1e12
+    line = {
+        "metric": METRICS["adjoint_2d"], "value": value, "unit": "candidates/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (double-float phases)", "data": "synthetic",
+        "config": _adjoint_config(wl, npt, world),
+        "roofline": {"kernel": "k_resampled<true> (F and gradient of the resampled series, 21 calls per step)",
+                     "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "peak_kind": "FP32 CUDA-core peak from unit counts and max clock (152 SM x 128 x 2 x 2070 MHz)",
+                     "flop_convention": "%d FP32 flop per output sample and point per call (ncu opcode counts; the "
+                                        "whole step's time, which also holds the starting points' metric pass)"
+                                        % ADJOINT_FLOP_PER_SAMPLE},
+        "gpu_launches": int(stats["launches"]),
+        "clocks": ck,
+        "forward": {"value": npt / (fwd_ms / 1e3), "unit": "candidates/s", "ms": fwd_ms},
+        "backward": {"value": npt / (bwd_ms / 1e3), "unit": "candidates/s", "ms": bwd_ms},
+        "F_gain": {"median": float(np.median(gain)), "max": float(np.max(gain))},
+    }
+    if rank == 0 and not args.quick:
+        # oracle: the resampled F with its gradient (FP64) at starting points, on every host core
+        pool = OraclePool()
+        ptsh = pts0.cpu().numpy()
+        xh = x32.double().cpu().numpy()
+        try:
+            per = 64  # evaluations per worker: ~7 s on the 16 cores of a Grace host
+            pts_s = [list(ptsh[i % npt]) for i in range(per * pool.cores)]
+            done, secs = pool.points([("adjoint", xh, wl.dt, pp, wl.fl, det, wl.S0) for pp in pool.deal(pts_s)])
+            line["cpu_baseline"] = pool.record(done / 21.0 / secs, "candidates/s",
+                                               "%d evaluations of the resampled F and its gradient (with each "
+                                               "worker's segment preparation) over %d workers, %.1f s; a "
+                                               "candidate's 20 steps take 21" % (done, pool.cores, secs))
+        finally:
+            pool.close()
+        # end to end: candidates from the host, refined points and F back to the host
+        ch = cand.cpu().pin_memory()
+        ke = max(2, steps)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(ke):
+            cd = ch.to("cuda", non_blocking=True)
+            pts = fs.points_from_candidates(ctx, seg, cd, npt, alpha, delta, f1)
+            o, Fo = fs.refine_resampled(ctx, seg, pts, nsteps=nsteps)
+            o.cpu(), Fo.cpu()
+        e2e_s = (time.perf_counter() - t1) / ke
+        line["e2e"] = {"value": npt / e2e_s, "unit": "candidates/s", "h2d_bytes_per_step": npt * 16,
+                       "d2h_bytes_per_step": npt * 40}
+    else:
+        line.setdefault("e2e", None)
+        line.setdefault("cpu_baseline", None)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    seg.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main_lattice(args):
     """The constrained A4* lattice of a sky patch on the 2-day data (Sec. IV): per sky
     node a row of spindown nodes, each line one transform whose bins are shifted by its
@@ -1100,6 +1277,8 @@ def main():
         return main_batch(args)
     if args.workload == "refine_2d":
         return main_refine(args)
+    if args.workload == "adjoint_2d":
+        return main_adjoint(args)
     if args.workload == "lattice_2d":
         return main_lattice(args)
     import torch

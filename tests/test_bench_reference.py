@@ -1,6 +1,6 @@
 """The benchmark's reference arm (the CPU oracle on every host core) prints one JSON
 line with the workload's own metric, unit and config, for a single segment, a batch,
-the fine search and the constrained lattice, without a GPU."""
+the fine search, the adjoint and the constrained lattice, without a GPU."""
 import json
 import os
 import subprocess
@@ -12,7 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.mark.parametrize("workload,unit", [("tiny", "templates/s"), ("uneven_small", "templates/s"),
-                                           ("refine_2d", "candidates/s"), ("lattice_2d", "templates/s")])
+                                           ("refine_2d", "candidates/s"), ("adjoint_2d", "candidates/s"),
+                                           ("lattice_2d", "templates/s")])
 def test_reference_arm_line(workload, unit):
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", workload, "--steps", "1",
                         "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=300)

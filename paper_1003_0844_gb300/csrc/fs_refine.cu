@@ -44,10 +44,15 @@ __global__ void k_earth_table64(SegGeom g, dbl4 *tab) {
   tab[k] = make_dbl4(cl, sl, cth, sth);
 }
 
-__global__ void k_point_constants(const fs_point *pts, int npt, SegGeom g, fs_detector det, PointConst *out) {
+// The constants of each point, and their double-float form for the FP32-pipe kernels
+// (computed once per point rather than by every block of those kernels).
+__global__ void k_point_constants(const fs_point *pts, int npt, SegGeom g, fs_detector det, PointConst *out,
+                                  FastConst *fast) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npt) return;
-  out[i] = point_constants(pts[i], g, det);
+  const PointConst c = point_constants(pts[i], g, det);
+  out[i] = c;
+  fast[i] = fast_const(c, g);
 }
 
 // Accumulators per point:
@@ -268,6 +273,14 @@ __global__ void k_data32(int64_t n, const double *x64, float2 *X) {
   }
 }
 
+// A point's FastConst into shared memory by the whole block (word by word).
+__device__ __forceinline__ void load_fast_const(const FastConst *src, FastConst *dst) {
+  static_assert(sizeof(FastConst) % 4 == 0, "copied as 32-bit words");
+  const unsigned *s = (const unsigned *)src;
+  unsigned *d = (unsigned *)dst;
+  for (int i = threadIdx.x; i < (int)(sizeof(FastConst) / 4); i += blockDim.x) d[i] = s[i];
+}
+
 // Sums of the double-float kernels to FP64 block partials, in a fixed order.
 template <int NQ>
 __device__ __forceinline__ void fast_reduce(const df32 *acc, int q0, int NA, double *partial, int pt) {
@@ -293,11 +306,11 @@ __device__ __forceinline__ void fast_reduce(const df32 *acc, int q0, int NA, dou
 // F and its gradient: accumulators [0, 26) of PtLayout (Sa, Sb, dSa_i, dSb_i, sums of
 // a^2, b^2 and a da, b db).  NA: stride of a block's partials.
 __global__ void __launch_bounds__(kPtThreads) k_points_fg(SegGeom g, const dbl4 *__restrict__ etab, Etab32 et,
-                                                          const PointConst *pcs, double *partial, int NA) {
+                                                          const FastConst *fcs, double *partial, int NA) {
   __shared__ FastConst c;
   __shared__ float4 sc[257];
   const int pt = blockIdx.x;
-  if (threadIdx.x == 0) c = fast_const(pcs[pt], g);
+  load_fast_const(fcs + pt, &c);
   for (int i = threadIdx.x; i < 257; i += blockDim.x) sc[i] = et.SC[i];
   __syncthreads();
   df32 acc[26];
@@ -319,11 +332,11 @@ __global__ void __launch_bounds__(kPtThreads) k_points_fg(SegGeom g, const dbl4 
 // all 46 (255 registers and spills); forcing 3 CTAs per SM (168 registers) gained nothing.
 template <int SIG>
 __global__ void __launch_bounds__(kPtThreads) k_points_h(SegGeom g, const dbl4 *__restrict__ etab, Etab32 et,
-                                                         const PointConst *pcs, double *partial, int NA, int q0) {
+                                                         const FastConst *fcs, double *partial, int NA, int q0) {
   __shared__ FastConst c;
   __shared__ float4 sc[257];
   const int pt = blockIdx.x;
-  if (threadIdx.x == 0) c = fast_const(pcs[pt], g);
+  load_fast_const(fcs + pt, &c);
   for (int i = threadIdx.x; i < 257; i += blockDim.x) sc[i] = et.SC[i];
   __syncthreads();
   static_assert(SIG == 0 || SIG == 1, "one signal per kernel");
@@ -615,6 +628,7 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 // state, trial points and their F, gradients, Hessians and metrics.
 struct RefWs {
   PointConst *pc;
+  FastConst *fc;
   double *partial;
   ClimbState *state;
   fs_point *trial;
@@ -628,6 +642,7 @@ static fs_status refine_ws(fs_ctx *ctx, const fs_seg *seg, int npt, bool climb, 
   constexpr int kMaxAcc = PtLayout<true, true>::kN;
   size_t off = 0;
   const size_t o_pc = off; off = al256(off + sizeof(PointConst) * npt);
+  const size_t o_fc = off; off = al256(off + sizeof(FastConst) * npt);
   const size_t o_pa = off; off = al256(off + sizeof(double) * kMaxAcc * (size_t)w->nblk * npt);
   size_t o_st = 0, o_tr = 0, o_ft = 0, o_gt = 0, o_Ht = 0, o_Gt = 0;
   if (climb) {
@@ -642,6 +657,7 @@ static fs_status refine_ws(fs_ctx *ctx, const fs_seg *seg, int npt, bool climb, 
   if (s != FS_OK) return s;
   char *b = (char *)ctx->rws;
   w->pc = (PointConst *)(b + o_pc);
+  w->fc = (FastConst *)(b + o_fc);
   w->partial = (double *)(b + o_pa);
   w->state = climb ? (ClimbState *)(b + o_st) : nullptr;
   w->trial = climb ? (fs_point *)(b + o_tr) : nullptr;
@@ -665,10 +681,10 @@ static int launch_points(fs_seg *seg, const RefWs &w, int npt, double *F, double
     k_points<HESS, MET, true><<<grid, kPtThreads, 0, st>>>(seg->g, et, seg->eph, seg->x64, w.pc, w.partial);
   } else {
     const Etab32 e32 = etab32_view(seg);
-    k_points_fg<<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.pc, w.partial, Lt::kN);
+    k_points_fg<<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.fc, w.partial, Lt::kN);
     if constexpr (HESS) {
-      k_points_h<0><<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.pc, w.partial, Lt::kN, Lt::kH);
-      k_points_h<1><<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.pc, w.partial, Lt::kN, Lt::kH);
+      k_points_h<0><<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.fc, w.partial, Lt::kN, Lt::kH);
+      k_points_h<1><<<grid, kPtThreads, 0, st>>>(seg->g, et, e32, w.fc, w.partial, Lt::kN, Lt::kH);
       launches += 2;
     }
     if constexpr (MET) {
@@ -683,7 +699,7 @@ static int launch_points(fs_seg *seg, const RefWs &w, int npt, double *F, double
 
 static fs_status points_pass(fs_ctx *ctx, fs_seg *seg, const RefWs &w, const fs_point *pts, int npt, double *F,
                              double *grad, double *hess, double *metric, cudaStream_t st, double *amp = nullptr) {
-  k_point_constants<<<(unsigned)((npt + 127) / 128), 128, 0, st>>>(pts, npt, seg->g, ctx->det, w.pc);
+  k_point_constants<<<(unsigned)((npt + 127) / 128), 128, 0, st>>>(pts, npt, seg->g, ctx->det, w.pc, w.fc);
   int nl = 0;
   if (hess && metric) nl = launch_points<true, true>(seg, w, npt, F, grad, hess, metric, amp, st);
   else if (hess) nl = launch_points<true, false>(seg, w, npt, F, grad, hess, metric, amp, st);

@@ -23,6 +23,7 @@
 // matrix at the start (one full correlation length, Eq. hype), scaled by eta,
 // and kept only if F grew (eta doubles, up to 1), else eta quarters.
 #include <math.h>
+#include <algorithm>
 #include "fs_internal.h"
 #include "fs_model.cuh"
 #include "fs_refine_df.cuh"
@@ -30,7 +31,19 @@
 namespace fs {
 
 constexpr int kPtThreads = 128;
-constexpr int kPtSamples = 32;   // samples per thread per block
+// Samples per thread per block: 192 at most (a 2-day point in 4 blocks; measured
+// fastest over 32..336 with 1024 points), fewer when the points alone leave the GPU
+// short of blocks (about two waves of the kernels' 2 CTAs per SM), 8 at least.
+constexpr int kPtSamplesMax = 192;
+constexpr int kPtSamplesMin = 8;
+
+// The samples [k0, k1) of this block: the n samples in gridDim.y blocks of equal size
+// (a multiple of kPtThreads), so that no block is left with a sliver of the data.
+__device__ __forceinline__ void block_range(int64_t n, int64_t *k0, int64_t *k1) {
+  const int64_t per = ((n + gridDim.y - 1) / gridDim.y + kPtThreads - 1) / kPtThreads * kPtThreads;
+  *k0 = (int64_t)blockIdx.y * per;
+  *k1 = min(n, *k0 + per);
+}
 
 // Per-segment FP64 table on t_k = k dt: (cos, sin) of the orbital longitude
 // lambda_E(t_k) and of the local sidereal angle theta(t_k).
@@ -66,7 +79,7 @@ struct PtLayout {
   static constexpr int kN = kH + (HESS ? 46 : 0);
 };
 
-// Grid: x = point, y = block of kPtThreads x kPtSamples samples.
+// Grid: x = point, y = block of samples (block_range).
 // EPH: phi and its sky derivatives from the caller's position table eph (r_k at
 // t_k = k dt: n0 . r_k and the derivatives of n0 dotted with r_k) instead of the
 // analytic orbit and rotation terms; the sidereal angle still comes from etab.
@@ -85,8 +98,8 @@ __global__ void __launch_bounds__(kPtThreads) k_points(SegGeom g, const dbl4 *__
   double acc[NA];
 #pragma unroll
   for (int q = 0; q < NA; q++) acc[q] = 0.0;
-  const int64_t k0 = (int64_t)blockIdx.y * kPtThreads * kPtSamples;
-  const int64_t k1 = min(g.n, k0 + (int64_t)kPtThreads * kPtSamples);
+  int64_t k0, k1;
+  block_range(g.n, &k0, &k1);
   const double two_pi = 6.283185307179586476925286766559;
   const double four_pi2 = 39.478417604357434475337963999505;
   for (int64_t k = k0 + threadIdx.x; k < k1; k += kPtThreads) {
@@ -316,8 +329,8 @@ __global__ void __launch_bounds__(kPtThreads) k_points_fg(SegGeom g, const dbl4 
   df32 acc[26];
 #pragma unroll
   for (int q = 0; q < 26; q++) acc[q] = df32{0.f, 0.f};
-  const int64_t k0 = (int64_t)blockIdx.y * kPtThreads * kPtSamples;
-  const int64_t k1 = min(g.n, k0 + (int64_t)kPtThreads * kPtSamples);
+  int64_t k0, k1;
+  block_range(g.n, &k0, &k1);
   for (int64_t k = k0 + threadIdx.x; k < k1; k += kPtThreads) {
     const FastSample s = fast_sample(c, g, etab, et, sc, k);
     fg_sample(c, s, acc);
@@ -344,8 +357,8 @@ __global__ void __launch_bounds__(kPtThreads) k_points_h(SegGeom g, const dbl4 *
   df32 acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; q++) acc[q] = df32{0.f, 0.f};
-  const int64_t k0 = (int64_t)blockIdx.y * kPtThreads * kPtSamples;
-  const int64_t k1 = min(g.n, k0 + (int64_t)kPtThreads * kPtSamples);
+  int64_t k0, k1;
+  block_range(g.n, &k0, &k1);
   for (int64_t k = k0 + threadIdx.x; k < k1; k += kPtThreads) {
     const FastSample s = fast_sample(c, g, etab, et, sc, k);  // the same e as k_points_fg
     hess_sample<SIG>(c, s, acc);
@@ -366,8 +379,8 @@ __global__ void __launch_bounds__(kPtThreads) k_points_met(SegGeom g, const dbl4
   double acc[14];
 #pragma unroll
   for (int q = 0; q < 14; q++) acc[q] = 0.0;
-  const int64_t k0 = (int64_t)blockIdx.y * kPtThreads * kPtSamples;
-  const int64_t k1 = min(g.n, k0 + (int64_t)kPtThreads * kPtSamples);
+  int64_t k0, k1;
+  block_range(g.n, &k0, &k1);
   for (int64_t k = k0 + threadIdx.x; k < k1; k += kPtThreads) {
     const dbl4 e4 = etab[k];
     const double t = (double)k * g.dt;
@@ -637,8 +650,13 @@ struct RefWs {
 };
 
 static fs_status refine_ws(fs_ctx *ctx, const fs_seg *seg, int npt, bool climb, cudaStream_t st, RefWs *w) {
-  const int64_t per_blk = (int64_t)kPtThreads * kPtSamples;
-  w->nblk = (int)((seg->g.n + per_blk - 1) / per_blk);  // <= 65535 for n <= 2^28
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) return FS_ERR_CUDA;
+  const int64_t n = seg->g.n;
+  const int64_t lo = (n + (int64_t)kPtThreads * kPtSamplesMax - 1) / ((int64_t)kPtThreads * kPtSamplesMax);
+  const int64_t hi = (n + (int64_t)kPtThreads * kPtSamplesMin - 1) / ((int64_t)kPtThreads * kPtSamplesMin);
+  const int64_t want = (4 * (int64_t)nsm + npt - 1) / npt;  // blocks per point for ~2 waves
+  w->nblk = (int)std::min(hi, std::max(lo, want));  // <= 65535 for n <= 2^26
   constexpr int kMaxAcc = PtLayout<true, true>::kN;
   size_t off = 0;
   const size_t o_pc = off; off = al256(off + sizeof(PointConst) * npt);

@@ -116,3 +116,18 @@ def test_product_path_does_not_import_oracle():
     for f in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
         src = open(f).read()
         assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
+
+
+def test_adjoint_entry_points_refuse_null_arguments(lib):
+    """The adjoint's entry points check their arguments before any device call:
+    null handles or pointers and empty point lists return FS_ERR_ARG."""
+    vp = ctypes.c_void_p
+    lib.fs_fstat_resampled.argtypes = [vp, vp, vp, ctypes.c_int32, vp, vp]
+    lib.fs_fstat_resampled_grad.argtypes = [vp, vp, vp, ctypes.c_int32, vp, vp, vp, vp]
+    lib.fs_refine_resampled.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, vp, vp]
+    for f in (lib.fs_fstat_resampled, lib.fs_fstat_resampled_grad, lib.fs_refine_resampled):
+        f.restype = ctypes.c_int
+    FS_ERR_ARG = 1
+    assert lib.fs_fstat_resampled(None, None, None, 1, None, None) == FS_ERR_ARG
+    assert lib.fs_fstat_resampled_grad(None, None, None, 1, None, None, None, None) == FS_ERR_ARG
+    assert lib.fs_refine_resampled(None, None, None, 1, 20, None, None) == FS_ERR_ARG

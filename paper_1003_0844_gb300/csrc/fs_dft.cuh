@@ -41,6 +41,41 @@ constexpr double cx_sin64(int k) {  // sin(2 pi k / 64)
   return q == 0 ? s : q == 1 ? c : q == 2 ? -s : -c;
 }
 
+
+// Packed FP32 pairs (the f32x2 forms of add, sub, mul and fma on sm_100 and later):
+// both halves of a complex value in one instruction.  They do the same arithmetic at
+// the same FP32 rate as two scalar instructions (measured: 69 TFLOP/s either way) but
+// take half the issue slots, which bound the transform kernel; swapping the halves of
+// an operand measured free.  The butterflies use them (3.5% faster on the 2-day grid,
+// 7% on 2^21); complex products with a runtime twiddle measured slower packed (the
+// broadcast and sign of the twiddle's halves cost more than they save).  Device code
+// only; the host keeps the scalar forms (the butterflies round exactly as they do; a
+// lone twiddle product rounds its two terms in another order).
+#if defined(__CUDA_ARCH__)
+#define FS_X2 1
+__device__ __forceinline__ unsigned long long x2p(float2 a) {
+  unsigned long long r; asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y)); return r;
+}
+__device__ __forceinline__ float2 x2u(unsigned long long v) {
+  float2 a; asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(v)); return a;
+}
+__device__ __forceinline__ float2 x2add(float2 a, float2 b) {
+  unsigned long long d; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x2p(a)), "l"(x2p(b))); return x2u(d);
+}
+__device__ __forceinline__ float2 x2sub(float2 a, float2 b) {
+  unsigned long long d; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x2p(a)), "l"(x2p(b))); return x2u(d);
+}
+__device__ __forceinline__ float2 x2mul(float2 a, float2 b) {
+  unsigned long long d; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x2p(a)), "l"(x2p(b))); return x2u(d);
+}
+__device__ __forceinline__ float2 x2fma(float2 a, float2 b, float2 c) {  // a * b + c by halves
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(x2p(a)), "l"(x2p(b)), "l"(x2p(c)));
+  return x2u(d);
+}
+__device__ __forceinline__ float2 x2swap(float2 a) { return make_float2(a.y, a.x); }
+#endif
+
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
@@ -81,6 +116,33 @@ constexpr int cx_bitrev(int i, int bits) {
 // compile time from the double-precision table above.
 template <int M, int K>
 __host__ __device__ __forceinline__ void bfly_dit(float2 &a, float2 &b) {
+#ifdef FS_X2
+  if constexpr (K == 0) {
+    const float2 t = b;
+    b = x2sub(a, t);
+    a = x2add(a, t);
+  } else if constexpr (4 * K == M) {  // w = -i: w b = (b.y, -b.x)
+    const float2 t = x2swap(b);
+    b = x2fma(make_float2(-1.f, 1.f), t, a);
+    a = x2fma(make_float2(1.f, -1.f), t, a);
+  } else {
+    constexpr int k64 = K * (64 / M);
+    constexpr double c = cx_cos64(k64), s = -cx_sin64(k64);
+    constexpr bool cbig = (c >= 0 ? c : -c) >= (s >= 0 ? s : -s);
+    constexpr float f = (float)(cbig ? c : s);
+    constexpr float r = (float)(cbig ? s / c : c / s);
+    if constexpr (cbig) {
+      const float2 uv = x2fma(make_float2(-r, r), x2swap(b), b);  // (b.x - r b.y, b.y + r b.x)
+      b = x2fma(make_float2(-f, -f), uv, a);
+      a = x2fma(make_float2(f, f), uv, a);
+    } else {
+      // (u, v) = (r b.x - b.y, r b.y + b.x) = (-v', u') with (u', v') = (b.x + r b.y, b.y - r b.x)
+      const float2 vu = x2swap(x2fma(make_float2(r, -r), x2swap(b), b));
+      b = x2fma(make_float2(f, -f), vu, a);
+      a = x2fma(make_float2(-f, f), vu, a);
+    }
+  }
+#else
   if constexpr (K == 0) {
     const float2 t = b;
     b = csub(a, t);
@@ -106,6 +168,7 @@ __host__ __device__ __forceinline__ void bfly_dit(float2 &a, float2 &b) {
     b = make_float2(fmaf(-f, u, a.x), fmaf(-f, v, a.y));
     a = make_float2(fmaf(f, u, a.x), fmaf(f, v, a.y));
   }
+#endif
 }
 // w b alone (the first operand of the butterfly is known to be zero).
 template <int M, int K>
@@ -117,7 +180,11 @@ __host__ __device__ __forceinline__ float2 twmul_dit(float2 b) {
   } else {
     constexpr int k64 = K * (64 / M);
     constexpr float c = (float)cx_cos64(k64), s = (float)(-cx_sin64(k64));
+#ifdef FS_X2
+    return x2fma(make_float2(-s, s), x2swap(b), x2mul(make_float2(c, c), b));
+#else
     return make_float2(fmaf(c, b.x, -s * b.y), fmaf(s, b.x, c * b.y));
+#endif
   }
 }
 
@@ -172,7 +239,11 @@ __host__ __device__ __forceinline__ void dft_inplace(float2 *v) {
           if constexpr (!last_pruned) u[i1] = make_float2(-t.x, -t.y);
         } else if constexpr (last_pruned) {
           const float2 t = twmul_dit<2 * h, k>(u[i1]);
+#ifdef FS_X2
+          u[i0] = x2add(u[i0], t);
+#else
           u[i0] = cadd(u[i0], t);
+#endif
         } else {
           bfly_dit<2 * h, k>(u[i0], u[i1]);
         }

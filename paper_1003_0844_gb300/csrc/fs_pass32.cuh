@@ -170,16 +170,46 @@ __device__ __forceinline__ void pass1_item(const Pass1Args &A, int tm, int zs, i
   const int64_t nf = N2T ? (int64_t)L * N2T : A.nfft;
   const float inv_nf = 1.0f / (float)nf;
   const float2 step = expm2pi((float)(((int64_t)n2 * P) & (nf - 1)) * inv_nf);
-  float2 wt = make_float2(1.f, 0.f);
-  sfor<0, Q>([&](auto d) {
-    if constexpr (d % 16 == 0) {
-      const float f = (float)(((int64_t)n2 * (t + P * d)) & (nf - 1)) * inv_nf;
-      wt = chirp_cycles(f > 0.5f ? f - 1.0f : f);
-    } else {
-      wt = cmul(wt, step);
-    }
-    v[d] = cmul(v[d], wt);
-  });
+#ifdef FS_X2
+  // 512-point columns (16 x 32): the twiddle w kept as (w.x, w.x) and (-w.y, w.y), so
+  // that v w and the step w' = w step are two packed FP32 instructions per product.
+  // Measured per shape: 0.9% faster on the 2-day transform and 1.5% on the lattice
+  // search, but 2.1% slower for 1024-point columns and 0.4% for 256-point ones (a table
+  // of twiddles kept that way measured slower everywhere).
+  constexpr bool kPackedTw = P == 16 && Q == 32;
+#else
+  constexpr bool kPackedTw = false;
+#endif
+  if constexpr (kPackedTw) {
+#ifdef FS_X2
+    float2 wc, ws;
+    const float2 sr = make_float2(step.x, step.x), sk = make_float2(step.y, -step.y);
+    sfor<0, Q>([&](auto d) {
+      if constexpr (d % 16 == 0) {
+        const float f = (float)(((int64_t)n2 * (t + P * d)) & (nf - 1)) * inv_nf;
+        const float2 w0 = chirp_cycles(f > 0.5f ? f - 1.0f : f);
+        wc = make_float2(w0.x, w0.x);
+        ws = make_float2(-w0.y, w0.y);
+      } else {
+        const float2 c1 = x2mul(wc, sr), s1 = x2mul(ws, sr), wc0 = wc;
+        wc = x2fma(ws, sk, c1);           // (w'.x, w'.x)
+        ws = x2fma(wc0, x2swap(sk), s1);  // (-w'.y, w'.y)
+      }
+      v[d] = x2fma(ws, x2swap(v[d]), x2mul(wc, v[d]));
+    });
+#endif
+  } else {
+    float2 wt = make_float2(1.f, 0.f);
+    sfor<0, Q>([&](auto d) {
+      if constexpr (d % 16 == 0) {
+        const float f = (float)(((int64_t)n2 * (t + P * d)) & (nf - 1)) * inv_nf;
+        wt = chirp_cycles(f > 0.5f ? f - 1.0f : f);
+      } else {
+        wt = cmul(wt, step);
+      }
+      v[d] = cmul(v[d], wt);
+    });
+  }
   float2 *Zs = A.Z + ((int64_t)zs * 2 + sig) * nf;
   sfor<0, Q>([&](auto d) {
     if (dbg_in(((int64_t)zs * 2 + sig) * nf + (int64_t)(t + P * d) * N2 + n2, A.z_elems, A.flags))
